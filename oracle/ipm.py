@@ -1,0 +1,715 @@
+"""Plain FP64 interior-point iteration, one problem at a time (oracle side).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+This follows the paper's review of IPOPT (Sec. IV) step by step:
+
+* barrier objective phi_mu (Eq. 3) with IPOPT's linear damping term for
+  variables bounded on one side only (the footnote of Sec. IV points to
+  IPOPT's handling of one-sided bounds);
+* Lagrangian and iterate (x, y_c, z_L, z_U) (Eq. 4);
+* optimality conditions (Eq. 5) measured by IPOPT's scaled error E_mu;
+* Newton system (Eq. 6) reduced to the augmented system (Eq. 7) by
+  eliminating the bound-multiplier steps (text after Eq. 6), solved by a
+  symmetric indefinite LDL^T whose inertia is checked and corrected by the
+  regularisation delta_x I (text after Eq. 7; IPOPT's Algorithm IC);
+* the branches of Table I: (1) backtracking filter line search,
+  (2) second-order correction, (4) tiny step, (6) hard feasibility
+  restoration (a nested interior-point solve of the l1 restoration problem;
+  a restoration inside restoration is reported as a failure), and
+  (7) the monotone barrier update.  The watchdog (3), soft restoration (5) and
+  the adaptive barrier rule are not part of this method.
+
+Every constant is IPOPT's published default as listed in ``Options``.
+One call of ``step`` is one iteration; the complete state between iterations
+is ``SolverState`` (the state-injection test of Sec. VI, Eq. 8, loads it).
+"""
+
+from __future__ import annotations
+
+import copy
+import dataclasses
+import math
+
+import numpy as np
+from scipy.linalg import eigvalsh_tridiagonal, ldl, solve_triangular
+
+# status codes (shared meaning with the library, not shared code)
+RUNNING, CONVERGED, MAX_ITER, RESTO_FAILED, EVAL_ERROR, TINY_STEP = 0, 1, 2, 3, 4, 5
+NORMAL, RESTO = 0, 1
+EPS_MACH = np.finfo(np.float64).eps
+
+
+@dataclasses.dataclass
+class Options:
+    tol: float = 1e-6
+    max_iter: int = 500
+    mu_init: float = 0.1
+    s_max: float = 100.0
+    kappa_eps: float = 10.0
+    kappa_mu: float = 0.2
+    theta_mu: float = 1.5
+    tau_min: float = 0.99
+    kappa_sigma: float = 1e10
+    gamma_theta: float = 1e-5
+    gamma_phi: float = 1e-8
+    delta: float = 1.0
+    s_theta: float = 1.1
+    s_phi: float = 2.3
+    eta_phi: float = 1e-8
+    gamma_alpha: float = 0.05
+    kappa_soc: float = 0.99
+    p_max: int = 4
+    kappa_d: float = 1e-4
+    dw_init: float = 1e-4
+    dw_min: float = 1e-20
+    dw_max: float = 1e40
+    kappa_w_minus: float = 1.0 / 3.0
+    kappa_w_plus: float = 8.0
+    kappa_w_plus_bar: float = 100.0
+    bound_push: float = 1e-2
+    bound_frac: float = 1e-2
+    y_max: float = 1e3
+    z_init: float = 1.0
+    rho: float = 1000.0
+    kappa_resto: float = 0.9
+    filter_cap: int = 64
+    ls_max_trials: int = 60
+
+
+@dataclasses.dataclass
+class Phase:
+    """Iterate and line-search memory of one barrier solve (original or restoration)."""
+
+    x: np.ndarray
+    y: np.ndarray
+    zl: np.ndarray
+    zu: np.ndarray
+    mu: float
+    filt: list
+    theta_max: float = 0.0
+    theta_min: float = 0.0
+    dw_last: float = 0.0
+    tiny: bool = False
+
+
+@dataclasses.dataclass
+class SolverState:
+    normal: Phase
+    mode: int = NORMAL
+    resto: Phase | None = None
+    x_ref: np.ndarray | None = None      # x_R, the point where restoration started
+    zeta: float = 0.0
+    need_init: bool = True               # theta_max/theta_min and y still to be set
+    need_y_ls: bool = True               # least-squares y at the next evaluation
+    iter: int = 0
+    status: int = RUNNING
+    # counters (reported, not part of the algorithm)
+    n_soc: int = 0
+    n_resto_iter: int = 0
+    n_inertia_corr: int = 0
+    n_tiny: int = 0
+
+
+# ---------------------------------------------------------------- helpers --
+
+def bound_sets(nlp):
+    has_l = np.isfinite(nlp.xl)
+    has_u = np.isfinite(nlp.xu)
+    return has_l, has_u
+
+
+def slacks(nlp, x):
+    """s_L = x - x_L and s_U = x_U - x on the bounded components (0 elsewhere)."""
+    has_l, has_u = bound_sets(nlp)
+    sl = np.where(has_l, x - np.where(has_l, nlp.xl, 0.0), 0.0)
+    su = np.where(has_u, np.where(has_u, nlp.xu, 0.0) - x, 0.0)
+    return sl, su
+
+
+def barrier_phi(nlp, x, f, mu, opt):
+    """phi_mu (Eq. 3) plus kappa_d * mu * (distance to the only bound) per one-sided variable."""
+    has_l, has_u = bound_sets(nlp)
+    sl, su = slacks(nlp, x)
+    if np.any(sl[has_l] <= 0) or np.any(su[has_u] <= 0):
+        return np.inf
+    val = f - mu * np.sum(np.log(sl[has_l])) - mu * np.sum(np.log(su[has_u]))
+    only_l = has_l & ~has_u
+    only_u = has_u & ~has_l
+    val += opt.kappa_d * mu * (np.sum(sl[only_l]) + np.sum(su[only_u]))
+    return val
+
+
+def barrier_grad(nlp, x, g, mu, opt):
+    """Gradient of barrier_phi: grad f - mu S_L^{-1} e + mu S_U^{-1} e (+ damping)."""
+    has_l, has_u = bound_sets(nlp)
+    sl, su = slacks(nlp, x)
+    out = g.copy()
+    out[has_l] -= mu / sl[has_l]
+    out[has_u] += mu / su[has_u]
+    only_l = has_l & ~has_u
+    only_u = has_u & ~has_l
+    out[only_l] += opt.kappa_d * mu
+    out[only_u] -= opt.kappa_d * mu
+    return out
+
+
+def theta_of(c):
+    """Constraint violation used by the filter: l1 norm of c."""
+    return float(np.sum(np.abs(c)))
+
+
+def opt_error(nlp, x, y, zl, zu, g, J, c, mu, opt):
+    """IPOPT's scaled optimality error E_mu of the conditions Eq. 5."""
+    has_l, has_u = bound_sets(nlp)
+    sl, su = slacks(nlp, x)
+    grad_lag = g + J.T @ y - zl + zu
+    nb = int(has_l.sum() + has_u.sum())
+    z1 = float(np.sum(np.abs(zl[has_l])) + np.sum(np.abs(zu[has_u])))
+    s_d = max(opt.s_max, (float(np.sum(np.abs(y))) + z1) / max(1, nlp.m + nb)) / opt.s_max
+    s_c = max(opt.s_max, z1 / max(1, nb)) / opt.s_max
+    e_dual = float(np.max(np.abs(grad_lag))) / s_d if grad_lag.size else 0.0
+    e_prim = float(np.max(np.abs(c))) if c.size else 0.0
+    comp = 0.0
+    if has_l.any():
+        comp = max(comp, float(np.max(np.abs(sl[has_l] * zl[has_l] - mu))))
+    if has_u.any():
+        comp = max(comp, float(np.max(np.abs(su[has_u] * zu[has_u] - mu))))
+    return max(e_dual, e_prim, comp / s_c)
+
+
+def frac_to_boundary(v, dv, tau):
+    """Largest alpha in (0, 1] with v + alpha dv >= (1 - tau) v, over components with dv < 0."""
+    neg = dv < 0
+    if not np.any(neg):
+        return 1.0
+    return float(min(1.0, np.min(-tau * v[neg] / dv[neg])))
+
+
+# ------------------------------------------------------------ linear algebra --
+
+class KKTFactor:
+    """Bunch-Kaufman LDL^T of the augmented matrix of Eq. 7 with its inertia."""
+
+    def __init__(self, K):
+        self.K = K
+        lu, d, perm = ldl(K, lower=True)
+        self.L = lu[perm]
+        self.perm = perm
+        self.d = d
+        diag = np.diag(d).copy()
+        off = np.diag(d, -1).copy()
+        ev = eigvalsh_tridiagonal(diag, off) if K.shape[0] > 1 else diag
+        self.n_pos = int(np.sum(ev > 0))
+        self.n_neg = int(np.sum(ev < 0))
+        self.n_zero = int(np.sum(ev == 0))
+
+    def solve(self, rhs):
+        b = rhs[self.perm]
+        w = solve_triangular(self.L, b, lower=True, unit_diagonal=True)
+        n = self.d.shape[0]
+        ab = np.zeros((3, n))
+        ab[0, 1:] = np.diag(self.d, 1)
+        ab[1, :] = np.diag(self.d)
+        ab[2, :-1] = np.diag(self.d, -1)
+        from scipy.linalg import solve_banded
+        v = solve_banded((1, 1), ab, w)
+        u = solve_triangular(self.L.T, v, lower=False, unit_diagonal=True)
+        out = np.empty_like(u)
+        out[self.perm] = u
+        return out
+
+
+def augmented_matrix(Wsig, J, dw):
+    n = Wsig.shape[0]
+    m = J.shape[0]
+    K = np.zeros((n + m, n + m))
+    K[:n, :n] = Wsig + dw * np.eye(n)
+    K[n:, :n] = J
+    K[:n, n:] = J.T
+    return K
+
+
+# ------------------------------------------------------- restoration NLP --
+
+class RestoNLP:
+    """The l1 feasibility-restoration problem of IPOPT, built on an NLP.
+
+    min rho * sum(p + n) + zeta/2 * |D_R (x - x_R)|^2
+    s.t. c(x) - p + n = 0,  x_L <= x <= x_U,  p, n >= 0,
+    with D_R = diag(min(1, 1/|x_R|)) and zeta = sqrt(mu) at the start of the phase.
+    Variables are stacked as w = (x, p, n).
+    """
+
+    def __init__(self, nlp, x_ref, zeta, rho):
+        self.inner = nlp
+        self.x_ref = x_ref.copy()
+        self.zeta = zeta
+        self.rho = rho
+        nx, m = nlp.n, nlp.m
+        self.nx0 = nx
+        self.n = nx + 2 * m
+        self.m = m
+        self.dr = np.minimum(1.0, 1.0 / np.maximum(np.abs(x_ref), 1e-300))
+        self.xl = np.concatenate([nlp.xl, np.zeros(2 * m)])
+        self.xu = np.concatenate([nlp.xu, np.full(2 * m, np.inf)])
+
+    def parts(self, w):
+        nx, m = self.nx0, self.m
+        return w[:nx], w[nx:nx + m], w[nx + m:]
+
+    def f(self, w):
+        x, p, n = self.parts(w)
+        return self.rho * float(np.sum(p) + np.sum(n)) + \
+            0.5 * self.zeta * float(np.sum((self.dr * (x - self.x_ref)) ** 2))
+
+    def c(self, w):
+        x, p, n = self.parts(w)
+        return self.inner.c(x) - p + n
+
+    def grad_f(self, w):
+        x, _, _ = self.parts(w)
+        gx = self.zeta * self.dr ** 2 * (x - self.x_ref)
+        return np.concatenate([gx, np.full(2 * self.m, self.rho)])
+
+    def jac_c(self, w):
+        x, _, _ = self.parts(w)
+        Jx = self.inner.jac_c(x)
+        return np.hstack([Jx, -np.eye(self.m), np.eye(self.m)])
+
+    def hess_lag(self, w, y, obj_factor=1.0):
+        x, _, _ = self.parts(w)
+        H = np.zeros((self.n, self.n))
+        H[:self.nx0, :self.nx0] = self.inner.hess_lag(x, y, obj_factor=0.0) + \
+            obj_factor * np.diag(self.zeta * self.dr ** 2)
+        return H
+
+
+# ------------------------------------------------------------- the solver --
+
+def initial_state(nlp, x0, opt: Options) -> SolverState:
+    """Starting point: x pushed inside its bounds, z = 1, y set at the first iteration."""
+    x = np.asarray(x0, dtype=np.float64).copy()
+    has_l, has_u = bound_sets(nlp)
+    k1, k2 = opt.bound_push, opt.bound_frac
+    for i in range(nlp.n):
+        if has_l[i] and has_u[i]:
+            width = nlp.xu[i] - nlp.xl[i]
+            pl = min(k1 * max(1.0, abs(nlp.xl[i])), k2 * width)
+            pu = min(k1 * max(1.0, abs(nlp.xu[i])), k2 * width)
+            x[i] = min(max(x[i], nlp.xl[i] + pl), nlp.xu[i] - pu)
+        elif has_l[i]:
+            x[i] = max(x[i], nlp.xl[i] + k1 * max(1.0, abs(nlp.xl[i])))
+        elif has_u[i]:
+            x[i] = min(x[i], nlp.xu[i] - k1 * max(1.0, abs(nlp.xu[i])))
+    zl = np.where(has_l, opt.z_init, 0.0)
+    zu = np.where(has_u, opt.z_init, 0.0)
+    ph = Phase(x=x, y=np.zeros(nlp.m), zl=zl, zu=zu, mu=opt.mu_init, filt=[])
+    return SolverState(normal=ph)
+
+
+def least_squares_y(nlp, g, J, zl, zu, opt):
+    """y minimising |grad f - z_L + z_U + J^T y| via [[I, J^T], [J, 0]]; 0 if too large."""
+    n, m = nlp.n, nlp.m
+    K = augmented_matrix(np.zeros((n, n)), J, 1.0)
+    rhs = np.concatenate([-(g - zl + zu), np.zeros(m)])
+    try:
+        sol = np.linalg.solve(K, rhs)
+    except np.linalg.LinAlgError:
+        return np.zeros(m)  # rank-deficient constraint Jacobian: no estimate
+    y = sol[n:]
+    if m and np.max(np.abs(y)) > opt.y_max:
+        y = np.zeros(m)
+    return y
+
+
+def filter_add(ph: Phase, theta, phi, opt):
+    """Add (theta, phi) to the filter, dropping entries it dominates; oldest goes when full."""
+    ph.filt = [(t, p) for (t, p) in ph.filt if not (t >= theta and p >= phi)]
+    ph.filt.append((theta, phi))
+    if len(ph.filt) > opt.filter_cap:
+        ph.filt.pop(0)
+
+
+def in_filter(ph: Phase, theta, phi):
+    if not (theta < ph.theta_max):
+        return True
+    return any(theta >= t and phi >= p for (t, p) in ph.filt)
+
+
+def kappa_sigma_reset(nlp, x, zl, zu, mu, opt):
+    """z <- max(min(z, kappa_Sigma mu / s), mu / (kappa_Sigma s)) componentwise."""
+    has_l, has_u = bound_sets(nlp)
+    sl, su = slacks(nlp, x)
+    zl = zl.copy()
+    zu = zu.copy()
+    ks = opt.kappa_sigma
+    zl[has_l] = np.maximum(np.minimum(zl[has_l], ks * mu / sl[has_l]), mu / (ks * sl[has_l]))
+    zu[has_u] = np.maximum(np.minimum(zu[has_u], ks * mu / su[has_u]), mu / (ks * su[has_u]))
+    return zl, zu
+
+
+class _Outcome:
+    ACCEPTED, CONVERGED, LS_FAILED, EVAL_ERROR, TINY_STALL = range(5)
+
+
+def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
+                    y_ls=False):
+    """One iteration of the barrier method on `nlp` from phase state `ph`.
+
+    Returns an _Outcome; on ACCEPTED, `ph` holds the next iterate.
+    """
+    x, y, zl, zu = ph.x, ph.y, ph.zl, ph.zu
+    has_l, has_u = bound_sets(nlp)
+    f = nlp.f(x)
+    c = nlp.c(x)
+    g = nlp.grad_f(x)
+    J = nlp.jac_c(x)
+    if not (np.isfinite(f) and np.all(np.isfinite(c)) and np.all(np.isfinite(g))
+            and np.all(np.isfinite(J))):
+        return _Outcome.EVAL_ERROR
+    if y_ls:
+        y = least_squares_y(nlp, g, J, zl, zu, opt)
+        ph.y = y
+    theta = theta_of(c)
+    if init_theta:
+        ph.theta_max = 1e4 * max(1.0, theta)
+        ph.theta_min = 1e-4 * max(1.0, theta)
+
+    # overall convergence (Eq. 5 with mu = 0)
+    if opt_error(nlp, x, y, zl, zu, g, J, c, 0.0, opt) <= opt.tol:
+        return _Outcome.CONVERGED
+
+    # monotone barrier update (Table I row 7), repeated while the subproblem is solved
+    mu_floor = opt.tol / 10.0
+    first = True
+    while True:
+        e_mu = opt_error(nlp, x, y, zl, zu, g, J, c, ph.mu, opt)
+        if (e_mu <= opt.kappa_eps * ph.mu) or (first and ph.tiny):
+            if ph.mu <= mu_floor:
+                if first and ph.tiny:
+                    return _Outcome.TINY_STALL
+                break
+            ph.mu = max(mu_floor, min(opt.kappa_mu * ph.mu, ph.mu ** opt.theta_mu))
+            ph.filt = []
+            first = False
+            ph.tiny = False
+            continue
+        break
+    mu = ph.mu
+    tau = max(opt.tau_min, 1.0 - mu)
+
+    # augmented system (Eq. 7)
+    sl, su = slacks(nlp, x)
+    sigma = np.zeros(nlp.n)
+    sigma[has_l] += zl[has_l] / sl[has_l]
+    sigma[has_u] += zu[has_u] / su[has_u]
+    W = nlp.hess_lag(x, y, 1.0)
+    Wsig = W + np.diag(sigma)
+    gphi = barrier_grad(nlp, x, g, mu, opt)
+    rhs = -np.concatenate([gphi + J.T @ y, c])
+
+    # inertia correction (IPOPT Algorithm IC); delta_c is never used
+    def factor(dw):
+        fac = KKTFactor(augmented_matrix(Wsig, J, dw))
+        ok = (fac.n_pos == nlp.n and fac.n_neg == nlp.m and fac.n_zero == 0)
+        return fac, ok
+
+    fac, ok = factor(0.0)
+    dw = 0.0
+    if not ok:
+        dw = opt.dw_init if ph.dw_last == 0.0 else max(opt.dw_min, opt.kappa_w_minus * ph.dw_last)
+        while True:
+            trace["n_inertia_corr"] = trace.get("n_inertia_corr", 0) + 1
+            fac, ok = factor(dw)
+            if ok:
+                break
+            dw *= opt.kappa_w_plus_bar if ph.dw_last == 0.0 else opt.kappa_w_plus
+            if dw > opt.dw_max:
+                trace["ic_failed"] = True
+                return _Outcome.LS_FAILED
+        ph.dw_last = dw
+    trace["delta_w"] = dw
+
+    def solve(rhs_vec):
+        sol = fac.solve(rhs_vec)
+        return sol[:nlp.n], sol[nlp.n:]
+
+    def z_step(dx):
+        dzl = np.zeros(nlp.n)
+        dzu = np.zeros(nlp.n)
+        dzl[has_l] = mu / sl[has_l] - zl[has_l] - zl[has_l] / sl[has_l] * dx[has_l]
+        dzu[has_u] = mu / su[has_u] - zu[has_u] + zu[has_u] / su[has_u] * dx[has_u]
+        return dzl, dzu
+
+    def alpha_primal_max(dx):
+        return min(frac_to_boundary(sl[has_l], dx[has_l], tau),
+                   frac_to_boundary(su[has_u], -dx[has_u], tau))
+
+    def alpha_dual_max(dzl, dzu):
+        return min(frac_to_boundary(zl[has_l], dzl[has_l], tau),
+                   frac_to_boundary(zu[has_u], dzu[has_u], tau))
+
+    dx, dy = solve(rhs)
+    dzl, dzu = z_step(dx)
+    a_max = alpha_primal_max(dx)
+
+    def accept(alpha, dx_, dy_, dzl_, dzu_, augment, theta0, phi0):
+        x_new = x + alpha * dx_
+        y_new = y + alpha * dy_
+        az = alpha_dual_max(dzl_, dzu_)
+        zl_new = zl + az * dzl_
+        zu_new = zu + az * dzu_
+        zl_new, zu_new = kappa_sigma_reset(nlp, x_new, zl_new, zu_new, mu, opt)
+        if augment:
+            filter_add(ph, (1.0 - opt.gamma_theta) * theta0, phi0 - opt.gamma_phi * theta0, opt)
+        ph.x, ph.y, ph.zl, ph.zu = x_new, y_new, zl_new, zu_new
+        trace["alpha"] = alpha
+        trace["alpha_z"] = az
+
+    # tiny step (Table I row 4)
+    if np.max(np.abs(dx) / (1.0 + np.abs(x))) < 10.0 * EPS_MACH:
+        trace["tiny"] = True
+        accept(a_max, dx, dy, dzl, dzu, False, 0.0, 0.0)
+        ph.tiny = True
+        return _Outcome.ACCEPTED
+    ph.tiny = False
+
+    # backtracking filter line search (Table I row 1) with SOC (row 2)
+    phi0 = barrier_phi(nlp, x, f, mu, opt)
+    gdx = float(gphi @ dx)
+    if gdx < 0 and theta <= ph.theta_min:
+        a_min = opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta / (-gdx),
+                                      opt.delta * theta ** opt.s_theta / (-gdx) ** opt.s_phi)
+    elif gdx < 0:
+        a_min = opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta / (-gdx))
+    else:
+        a_min = opt.gamma_alpha * opt.gamma_theta
+
+    def switching(alpha):
+        return gdx < 0 and alpha * (-gdx) ** opt.s_phi > opt.delta * theta ** opt.s_theta
+
+    def trial_values(xt):
+        ft = nlp.f(xt)
+        ct = nlp.c(xt)
+        if not (np.isfinite(ft) and np.all(np.isfinite(ct))):
+            return None
+        return theta_of(ct), barrier_phi(nlp, xt, ft, mu, opt), ct
+
+    def acceptable(theta_t, phi_t, alpha):
+        """Filter test (A.5.3) and sufficient decrease (A.5.4); returns (ok, f_type)."""
+        if not np.isfinite(phi_t) or in_filter(ph, theta_t, phi_t):
+            return False, False
+        if switching(alpha) and theta <= ph.theta_min:
+            return phi_t <= phi0 + opt.eta_phi * alpha * gdx, True
+        ok = theta_t <= (1.0 - opt.gamma_theta) * theta or phi_t <= phi0 - opt.gamma_phi * theta
+        return ok, False
+
+    def needs_augment(alpha, phi_t):
+        return not (switching(alpha) and phi_t <= phi0 + opt.eta_phi * alpha * gdx)
+
+    alpha = a_max
+    n_trial = 0
+    while True:
+        n_trial += 1
+        xt = x + alpha * dx
+        tv = trial_values(xt)
+        if tv is not None:
+            theta_t, phi_t, c_t = tv
+            ok, _ = acceptable(theta_t, phi_t, alpha)
+            if ok:
+                accept(alpha, dx, dy, dzl, dzu, needs_augment(alpha, phi_t), theta, phi0)
+                trace["ls_trials"] = n_trial
+                return _Outcome.ACCEPTED
+            # second-order correction on the first trial when theta did not decrease
+            if n_trial == 1 and not (theta_t < theta):
+                c_soc = alpha * c + c_t
+                theta_old = theta
+                for p in range(1, opt.p_max + 1):
+                    trace["n_soc"] = trace.get("n_soc", 0) + 1
+                    dx_s, dy_s = solve(-np.concatenate([gphi + J.T @ y, c_soc]))
+                    a_soc = alpha_primal_max(dx_s)
+                    xs = x + a_soc * dx_s
+                    sv = trial_values(xs)
+                    if sv is None:
+                        break
+                    theta_s, phi_s, c_s = sv
+                    ok, _ = acceptable(theta_s, phi_s, alpha)
+                    if ok:
+                        dzl_s, dzu_s = z_step(dx_s)
+                        accept(a_soc, dx_s, dy_s, dzl_s, dzu_s, needs_augment(alpha, phi_s),
+                               theta, phi0)
+                        trace["soc_accepted"] = True
+                        trace["ls_trials"] = n_trial
+                        return _Outcome.ACCEPTED
+                    if p == opt.p_max or theta_s > opt.kappa_soc * theta_old:
+                        break
+                    c_soc = a_soc * c_soc + c_s
+                    theta_old = theta_s
+        alpha *= 0.5
+        if alpha < a_min or n_trial >= opt.ls_max_trials:
+            trace["ls_trials"] = n_trial
+            return _Outcome.LS_FAILED
+
+
+def resto_start(nlp, st: SolverState, opt: Options):
+    """Enter restoration from the current original iterate (IPOPT Sec. 3.3 reading)."""
+    ph = st.normal
+    x = ph.x
+    c = nlp.c(x)
+    f = nlp.f(x)
+    theta = theta_of(c)
+    phi = barrier_phi(nlp, x, f, ph.mu, opt)
+    filter_add(ph, (1.0 - opt.gamma_theta) * theta, phi - opt.gamma_phi * theta, opt)
+    zeta = math.sqrt(ph.mu)
+    rnlp = RestoNLP(nlp, x, zeta, opt.rho)
+    mu_r = max(ph.mu, float(np.max(np.abs(c))) if c.size else 0.0)
+    rho = opt.rho
+    a = (mu_r - rho * c) / (2.0 * rho)
+    nn = a + np.sqrt(a * a + mu_r * c / (2.0 * rho))
+    pp = c + nn
+    w = np.concatenate([x, pp, nn])
+    has_l, has_u = bound_sets(nlp)
+    zl = np.concatenate([np.where(has_l, np.minimum(rho, ph.zl), 0.0), mu_r / pp, mu_r / nn])
+    zu = np.concatenate([np.where(has_u, np.minimum(rho, ph.zu), 0.0), np.zeros(2 * nlp.m)])
+    rph = Phase(x=w, y=np.zeros(nlp.m), zl=zl, zu=zu, mu=mu_r, filt=[])
+    theta_r = theta_of(rnlp.c(w))
+    rph.theta_max = 1e4 * max(1.0, theta_r)
+    rph.theta_min = 1e-4 * max(1.0, theta_r)
+    st.resto = rph
+    st.x_ref = x.copy()
+    st.zeta = zeta
+    st.mode = RESTO
+    return rnlp
+
+
+def make_resto_nlp(nlp, st: SolverState, opt: Options):
+    return RestoNLP(nlp, st.x_ref, st.zeta, opt.rho)
+
+
+def step(nlp, st: SolverState, opt: Options) -> dict:
+    """Advance `st` by one iteration in place; returns a trace of what happened."""
+    trace = {"mode": st.mode}
+    if st.status != RUNNING:
+        return trace
+    if st.mode == NORMAL:
+        ph = st.normal
+        out = phase_iteration(nlp, ph, opt, trace, init_theta=st.need_init,
+                              y_ls=st.need_y_ls) if st.iter < opt.max_iter else None
+        if out is None:
+            # the iteration cap is tested after the convergence test of the same point
+            out = _check_only(nlp, ph, opt, st)
+            if out == _Outcome.CONVERGED:
+                st.status = CONVERGED
+            elif out == _Outcome.EVAL_ERROR:
+                st.status = EVAL_ERROR
+            else:
+                st.status = MAX_ITER
+            return trace
+        st.need_init = False
+        st.need_y_ls = False
+        if out == _Outcome.CONVERGED:
+            st.status = CONVERGED
+        elif out == _Outcome.EVAL_ERROR:
+            st.status = EVAL_ERROR
+        elif out == _Outcome.TINY_STALL:
+            st.status = TINY_STEP
+        elif out == _Outcome.ACCEPTED:
+            st.iter += 1
+            if trace.get("tiny"):
+                st.n_tiny += 1
+        elif out == _Outcome.LS_FAILED:
+            c = nlp.c(ph.x)
+            if theta_of(c) <= opt.tol:
+                st.status = RESTO_FAILED
+            else:
+                resto_start(nlp, st, opt)
+                trace["entered_resto"] = True
+                st.iter += 1
+        st.n_soc += trace.get("n_soc", 0)
+        st.n_inertia_corr += trace.get("n_inertia_corr", 0)
+        return trace
+
+    # restoration mode
+    rnlp = make_resto_nlp(nlp, st, opt)
+    rph = st.resto
+    if st.iter >= opt.max_iter:
+        st.status = MAX_ITER
+        return trace
+    out = phase_iteration(rnlp, rph, opt, trace)
+    st.n_soc += trace.get("n_soc", 0)
+    st.n_inertia_corr += trace.get("n_inertia_corr", 0)
+    if out in (_Outcome.CONVERGED, _Outcome.LS_FAILED, _Outcome.TINY_STALL):
+        st.status = RESTO_FAILED
+        return trace
+    if out == _Outcome.EVAL_ERROR:
+        st.status = EVAL_ERROR
+        return trace
+    st.iter += 1
+    st.n_resto_iter += 1
+    # return test: enough reduction of the original infeasibility and acceptable
+    # to the original filter at the original barrier parameter
+    x = rph.x[:nlp.n]
+    c = nlp.c(x)
+    f = nlp.f(x)
+    th = theta_of(c)
+    ph = st.normal
+    phi = barrier_phi(nlp, x, f, ph.mu, opt)
+    th_ref = theta_of(nlp.c(st.x_ref))
+    if np.isfinite(phi) and th <= opt.kappa_resto * th_ref and not in_filter(ph, th, phi):
+        zl, zu = kappa_sigma_reset(nlp, x, rph.zl[:nlp.n], rph.zu[:nlp.n], ph.mu, opt)
+        ph.x, ph.zl, ph.zu = x.copy(), zl, zu
+        ph.y = rph.y.copy()
+        st.need_y_ls = True
+        st.mode = NORMAL
+        st.resto = None
+        trace["left_resto"] = True
+    return trace
+
+
+def _check_only(nlp, ph, opt, st):
+    """Convergence test alone (used when the iteration cap is reached)."""
+    x = ph.x
+    f = nlp.f(x)
+    c = nlp.c(x)
+    g = nlp.grad_f(x)
+    J = nlp.jac_c(x)
+    if not (np.isfinite(f) and np.all(np.isfinite(c))):
+        return _Outcome.EVAL_ERROR
+    y = ph.y
+    if st.need_y_ls:
+        y = least_squares_y(nlp, g, J, ph.zl, ph.zu, opt)
+    if opt_error(nlp, x, y, ph.zl, ph.zu, g, J, c, 0.0, opt) <= opt.tol:
+        return _Outcome.CONVERGED
+    return None
+
+
+def solve(nlp, x0=None, opt: Options | None = None, record=False):
+    """Run to termination from x0 (default: the NLP's default start)."""
+    opt = opt or Options()
+    st = initial_state(nlp, nlp.default_start() if x0 is None else x0, opt)
+    history = []
+    while st.status == RUNNING:
+        if record:
+            history.append(copy.deepcopy(st))
+        tr = step(nlp, st, opt)
+        if record:
+            history[-1] = (history[-1], tr)
+    if record:
+        history.append((copy.deepcopy(st), {}))
+    return st, history
+
+
+def final_metrics(nlp, st: SolverState, opt: Options | None = None):
+    """Objective, scaled KKT error E_0 and infeasibility at the final original iterate."""
+    opt = opt or Options()
+    ph = st.normal
+    x = ph.x
+    g = nlp.grad_f(x)
+    J = nlp.jac_c(x)
+    c = nlp.c(x)
+    return {
+        "obj": nlp.f(x),
+        "kkt": opt_error(nlp, x, ph.y, ph.zl, ph.zu, g, J, c, 0.0, opt),
+        "inf": float(np.max(np.abs(c))) if c.size else 0.0,
+    }

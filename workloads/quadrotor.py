@@ -1,0 +1,239 @@
+"""Random problem parameters for the quadrotor NMPC workloads.
+
+The paper evaluates on quadrotor NMPC scenarios it describes only in words
+(Sec. VI: navigation past obstacles, reference tracking with obstacles,
+multi-quadrotor swaps).  No dataset exists, so the workloads below stand in for
+them with seeded synthetic draws of the same shape.
+
+Parameter vector theta of one problem (float64), in this order:
+    xbar    12*nq   initial state of every quadrotor (p, v, eta, omega)
+    ref      6*nq   per quadrotor reference circle (cx, cy, cz, radius, rate, phase);
+                    radius 0 means a fixed goal at (cx, cy, cz)
+    spheres  4*n_sph  (cx, cy, cz, r) of every spherical obstacle
+    cyls     3*n_cyl  (cx, cy, r) of every vertical cylinder
+Shared (not per problem): nq, horizon N, dt, n_sph, n_cyl and the pairwise
+minimum distance d (0 disables the pairwise constraints).
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """Counter-based SplitMix64 stream (Steele, Lea & Flood 2014)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / 9007199254740992.0))
+
+    def randint(self, lo: int, hi: int) -> int:
+        """Integer uniform in [lo, hi] inclusive."""
+        return lo + int(self.uniform() * (hi - lo + 1)) % (hi - lo + 1)
+
+
+def problem_stream(seed: int, problem_id: int) -> SplitMix64:
+    """Independent stream for problem `problem_id` of workload `seed`."""
+    mix = SplitMix64(seed * 0x1000003 + 0x51ED2701)
+    base = mix.next_u64()
+    return SplitMix64(base ^ ((problem_id * 0xD1342543DE82EF95) & MASK64))
+
+
+@dataclasses.dataclass(frozen=True)
+class ProblemDesc:
+    """Shared structure of one batch of problems (identical f, c and bounds)."""
+
+    nq: int = 1
+    horizon: int = 10
+    dt: float = 0.05
+    n_sph: int = 0
+    n_cyl: int = 0
+    pair_dist: float = 0.0
+
+    @property
+    def nx(self) -> int:
+        return 12 * self.nq
+
+    @property
+    def nu(self) -> int:
+        return 4 * self.nq
+
+    @property
+    def n_pairs(self) -> int:
+        return self.nq * (self.nq - 1) // 2 if self.pair_dist > 0 else 0
+
+    @property
+    def ni(self) -> int:
+        return self.nq * self.n_sph + self.nq * self.n_cyl + self.n_pairs
+
+    @property
+    def n(self) -> int:
+        return self.nx * (self.horizon + 1) + (self.nu + self.ni) * self.horizon
+
+    @property
+    def m(self) -> int:
+        return self.nx * (self.horizon + 1) + self.ni * self.horizon
+
+
+def theta_layout(desc: ProblemDesc) -> dict:
+    """Offsets of the parameter groups inside theta."""
+    o_x = 0
+    o_ref = o_x + 12 * desc.nq
+    o_sph = o_ref + 6 * desc.nq
+    o_cyl = o_sph + 4 * desc.n_sph
+    end = o_cyl + 3 * desc.n_cyl
+    return {"xbar": o_x, "ref": o_ref, "sph": o_sph, "cyl": o_cyl, "end": end}
+
+
+def n_theta(desc: ProblemDesc) -> int:
+    return theta_layout(desc)["end"]
+
+
+# ---------------------------------------------------------------- workloads --
+# Seeds follow 1000 + workload number.
+
+def _nav1(rng: SplitMix64, desc: ProblemDesc) -> np.ndarray:
+    """Single quadrotor flying to the origin past one sphere of radius 0.5."""
+    th = np.zeros(n_theta(desc))
+    lay = theta_layout(desc)
+    r = 0.5
+    while True:
+        p0 = np.array([rng.uniform(-3, 3) for _ in range(3)])
+        c = 0.5 * p0 + np.array([rng.uniform(-0.25, 0.25) for _ in range(3)])
+        if np.linalg.norm(p0 - c) >= r + 0.2 and np.linalg.norm(c) >= r + 0.2:
+            break
+    th[lay["xbar"]:lay["xbar"] + 3] = p0
+    th[lay["ref"]:lay["ref"] + 6] = 0.0
+    th[lay["sph"]:lay["sph"] + 4] = [c[0], c[1], c[2], r]
+    return th
+
+
+def _circle_point(ref, t):
+    cx, cy, cz, rad, rate, ph = ref
+    a = rate * t + ph
+    p = np.array([cx + rad * math.cos(a), cy + rad * math.sin(a), cz])
+    v = np.array([-rad * rate * math.sin(a), rad * rate * math.cos(a), 0.0])
+    return p, v
+
+
+def _track(rng: SplitMix64, desc: ProblemDesc) -> np.ndarray:
+    """Tracking a random circular reference at 1-2 m/s past spheres near the path."""
+    th = np.zeros(n_theta(desc))
+    lay = theta_layout(desc)
+    cx, cy, cz = rng.uniform(-2, 2), rng.uniform(-2, 2), rng.uniform(1, 2)
+    rad = rng.uniform(1.5, 3.0)
+    speed = rng.uniform(1.0, 2.0)
+    ref = (cx, cy, cz, rad, speed / rad, rng.uniform(0, 2 * math.pi))
+    p_ref0, v_ref0 = _circle_point(ref, 0.0)
+    p0 = p_ref0 + np.array([rng.uniform(-0.5, 0.5) for _ in range(3)])
+    th[lay["xbar"]:lay["xbar"] + 3] = p0
+    th[lay["xbar"] + 3:lay["xbar"] + 6] = v_ref0
+    th[lay["ref"]:lay["ref"] + 6] = ref
+    t_end = desc.horizon * desc.dt
+    for j in range(desc.n_sph):
+        while True:
+            r = rng.uniform(0.3, 0.8)
+            pj, _ = _circle_point(ref, rng.uniform(0, t_end))
+            c = pj + np.array([rng.uniform(-0.4, 0.4) for _ in range(3)])
+            if np.linalg.norm(p0 - c) >= r + 0.1:
+                break
+        th[lay["sph"] + 4 * j:lay["sph"] + 4 * j + 4] = [c[0], c[1], c[2], r]
+    return th
+
+
+def _spread_points(rng: SplitMix64, count: int, lo, hi, min_gap: float):
+    pts = []
+    while len(pts) < count:
+        q = np.array([rng.uniform(lo[i], hi[i]) for i in range(3)])
+        if all(np.linalg.norm(q - o) >= min_gap for o in pts):
+            pts.append(q)
+    return pts
+
+
+def _multi(rng: SplitMix64, desc: ProblemDesc) -> np.ndarray:
+    """nq quadrotors flying from random starts to random goals in a 10 m cube."""
+    th = np.zeros(n_theta(desc))
+    lay = theta_layout(desc)
+    starts = _spread_points(rng, desc.nq, (0, 0, 0), (10, 10, 10), 1.0)
+    goals = _spread_points(rng, desc.nq, (0, 0, 0), (10, 10, 10), 1.0)
+    for i in range(desc.nq):
+        th[lay["xbar"] + 12 * i:lay["xbar"] + 12 * i + 3] = starts[i]
+        th[lay["ref"] + 6 * i:lay["ref"] + 6 * i + 3] = goals[i]
+    for j in range(desc.n_sph):
+        # one obstacle between the first start and its goal (single-quad case)
+        while True:
+            c = 0.5 * (starts[0] + goals[0]) + np.array([rng.uniform(-0.25, 0.25) for _ in range(3)])
+            if all(np.linalg.norm(s - c) >= 0.7 for s in starts) and all(
+                np.linalg.norm(g - c) >= 0.7 for g in goals
+            ):
+                break
+            goals = _spread_points(rng, desc.nq, (0, 0, 0), (10, 10, 10), 1.0)
+            for i in range(desc.nq):
+                th[lay["ref"] + 6 * i:lay["ref"] + 6 * i + 3] = goals[i]
+        th[lay["sph"] + 4 * j:lay["sph"] + 4 * j + 4] = [c[0], c[1], c[2], 0.5]
+    return th
+
+
+def _cyl(rng: SplitMix64, desc: ProblemDesc) -> np.ndarray:
+    """Single quadrotor to (0, 0, 1) through 20-50 cylinders in a 20 m x 20 m area.
+
+    Problems with fewer than desc.n_cyl cylinders are padded with far-away
+    cylinders (centre 1000 m out, radius 0.2), which never become active.
+    """
+    th = np.zeros(n_theta(desc))
+    lay = theta_layout(desc)
+    n_real = rng.randint(20, min(50, desc.n_cyl)) if desc.n_cyl >= 20 else desc.n_cyl
+    cyl = []
+    while len(cyl) < n_real:
+        c = (rng.uniform(-10, 10), rng.uniform(-10, 10), rng.uniform(0.2, 0.6))
+        if math.hypot(c[0], c[1]) >= c[2] + 0.3:
+            cyl.append(c)
+    while True:
+        p0 = (rng.uniform(-10, 10), rng.uniform(-10, 10), rng.uniform(0.5, 2.0))
+        if all(math.hypot(p0[0] - c[0], p0[1] - c[1]) >= c[2] + 0.3 for c in cyl):
+            break
+    th[lay["xbar"]:lay["xbar"] + 3] = p0
+    th[lay["ref"]:lay["ref"] + 6] = [0.0, 0.0, 1.0, 0.0, 0.0, 0.0]
+    for j in range(desc.n_cyl):
+        c = cyl[j] if j < n_real else (1000.0 + 10.0 * j, 1000.0, 0.2)
+        th[lay["cyl"] + 3 * j:lay["cyl"] + 3 * j + 3] = c
+    return th
+
+
+WORKLOADS = {
+    # name: (seed, desc, drawer, default batch)
+    "nav1": (1001, ProblemDesc(nq=1, horizon=10, dt=0.05, n_sph=1), _nav1, 64),
+    "track": (1002, ProblemDesc(nq=1, horizon=30, dt=0.05, n_sph=3), _track, 4096),
+    "multi4": (1003, ProblemDesc(nq=4, horizon=25, dt=0.05, pair_dist=0.4), _multi, 1024),
+    "cyl": (1005, ProblemDesc(nq=1, horizon=40, dt=0.05, n_cyl=50), _cyl, 16384),
+}
+
+
+def make_batch(name: str, count: int | None = None, first_id: int = 0,
+               desc: ProblemDesc | None = None):
+    """Draw `count` problems of workload `name` starting at problem id `first_id`.
+
+    Returns (desc, theta) with theta of shape (count, n_theta(desc)).
+    `desc` may override the workload's structure (e.g. a shorter horizon for
+    quick tests); the drawing rules stay those of the named workload.
+    """
+    seed, base_desc, drawer, default_count = WORKLOADS[name]
+    desc = desc or base_desc
+    count = default_count if count is None else count
+    th = np.stack([drawer(problem_stream(seed, first_id + j), desc) for j in range(count)]) \
+        if count > 0 else np.zeros((0, n_theta(desc)))
+    return desc, np.ascontiguousarray(th, dtype=np.float64)
