@@ -1,0 +1,422 @@
+"""Benchmark: converged NLP solves/sec at KKT tolerance 1e-6 on one GB300.
+
+Workload (default): reference tracking with three random spherical obstacles,
+one quadrotor, RK4 horizon N = 30, batch of 4096 problems ("track").  One
+step = one full batched solve (every problem iterated to termination by the
+fused iteration kernel).  The headline `value` is the chosen form: FP32
+factorisation with FP64 iterative refinement; the plain FP64 form is reported
+beside it (`fp64`).
+
+python bench.py --gpus N --steps K --warmup W [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from workloads import make_batch  # noqa: E402
+
+WORKLOAD = "track"
+BATCH = 4096
+METRIC = "converged NLP solves/sec at KKT tol 1e-6 on 1 GB300 (plain FP64 vs chosen form)"
+UNIT = "solves/s"
+FP64_PEAK_NOMINAL = 152 * 2 * 2 * 2.07e9  # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
+FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh)
+    return None
+
+
+# ------------------------------------------------------------- flop model
+# Operation counts of the model routines, from the host instantiation of the
+# device templates with a counting scalar (paper_2606_26341_gb300/csrc/opcount.cpp;
+# tests/test_flop_model.py recompiles it and checks these numbers).
+RK4_VALUE_FLOPS = 152 + 200 + 4            # one RK4 step of one quadrotor, value only
+RK4_ADJOINT_FLOPS = 403 + 620 + 4          # value + reverse sweep (gradient of lam^T F)
+RK4_DUAL_FLOPS = 1122 + 1596 + 8           # forward-over-reverse, one direction
+
+
+def unit_flops(desc):
+    """Algorithmic FLOPs of the units the kernel counts, for one problem."""
+    N, nq, ni = desc.horizon, desc.nq, desc.ni
+    nx, nu = 12 * nq, 4 * nq
+    n, m = desc.n, desc.m
+    pos = 3 * nq
+    # one Riccati factorisation: PA, Q^ (24 nx^2 each), PB, S^ (24 nx nu each),
+    # R^ (24 nu^2), K (2 nx nu^2), P (2 nx^2 nu), Cholesky (nu^3/3), condensation
+    fact_stage = 48 * nx * nx + 48 * nx * nu + 24 * nu * nu + 2 * nx * nu * nu \
+        + 2 * nx * nx * nu + nu ** 3 / 3 + 4 * pos * pos * ni
+    fact = N * fact_stage + 4 * pos * pos * ni
+    # one solve: backward (P~d, B^T t, k, A^T t, K^T g) and forward (K dx, A dx + B du, P~ xi)
+    solve_stage = 4 * nx * nx + 56 * nx + 4 * nx * nu + 24 * nu + 2 * nu * nu + 20 * ni
+    solve = N * solve_stage
+    # KKT mat-vec of one refinement step: dynamics blocks, Hessian, diagonal, inequality rows
+    matvec = N * nq * (2 * 144 * 2 + 2 * 48 * 2 + 100 * 2) + 4 * n + N * ni * 12
+    values = N * nq * RK4_VALUE_FLOPS + N * ni * 12 + 3 * n       # c(x), f(x)
+    trial = values + 4 * n                                        # plus barrier objective
+    derivs = N * nq * 10 * RK4_DUAL_FLOPS                         # A, B, lambda-Hessian
+    jty = N * nq * RK4_ADJOINT_FLOPS + N * ni * pos * 4
+    iter_fixed = values + jty + derivs + 30 * n                   # + vector updates/norms
+    return {"fact": fact, "solve": solve, "matvec": matvec, "trial": trial,
+            "derivs": derivs, "iter_fixed": iter_fixed, "values": values}
+
+
+def step_flops(desc, stats, precision):
+    """(FP64 flops, FP32 flops) of one batched solve from the per-problem counters."""
+    u = unit_flops(desc)
+    it = float(np.sum(stats["iters"]))
+    fact = float(np.sum(stats["factorizations"]))
+    solves = float(np.sum(stats["solves"]))
+    trials = float(np.sum(stats["trials"]))
+    ir = float(np.sum(stats["ir_steps"]))
+    esc = float(np.sum(stats["fp64_escalations"]))
+    # evaluation, residuals, trials and refinement mat-vecs always run in FP64
+    f64 = it * (u["iter_fixed"] - u["derivs"]) + trials * u["trial"] + (ir + solves) * u["matvec"] * (precision == 1)
+    lowp = it * u["derivs"] + fact * u["fact"] + solves * u["solve"]
+    if precision == 0:
+        return f64 + lowp, 0.0
+    # escalated factorisations are redone in FP64
+    return f64 + esc * (u["fact"] + u["solve"]), lowp
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    from paper_2606_26341_gb300 import bipm
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    BATCH = args.batch
+    desc, theta = make_batch(WORKLOAD, BATCH, first_id=rank * BATCH)
+    theta_dev = torch.as_tensor(theta, device=dev)
+    theta_host = torch.as_tensor(theta).pin_memory()
+    n, m = desc.n, desc.m
+
+    def timed_solves(precision, steps, warmup):
+        b = bipm.Batch(desc, BATCH, bipm.Options(precision=precision), stream=stream)
+        for _ in range(warmup):
+            b.set_problems(theta_dev)
+            b.solve()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        k_ms = []
+        clocks = ClockSampler(local)
+        clocks.start()
+        e0.record(stream)
+        for _ in range(steps):
+            b.set_problems(theta_dev)
+            k0 = torch.cuda.Event(enable_timing=True)
+            k1 = torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            b.solve()
+            k1.record(stream)
+            k1.synchronize()
+            k_ms.append(k0.elapsed_time(k1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        st = b.get_stats()
+        b.close()
+        return ms, k_ms, st, clk
+
+    # chosen form and plain FP64 form
+    ms_mixed, kms_mixed, st_mixed, clk = timed_solves(1, args.steps, args.warmup)
+    if args.only_mixed:
+        ms_fp64, kms_fp64, st_fp64 = ms_mixed, kms_mixed, st_mixed
+    else:
+        ms_fp64, kms_fp64, st_fp64, _ = timed_solves(0, args.steps, args.warmup)
+
+    conv_mixed = int(np.sum(st_mixed["status"] == bipm.CONVERGED))
+    conv_fp64 = int(np.sum(st_fp64["status"] == bipm.CONVERGED))
+    t_mixed = ms_mixed / 1e3
+    steps_fp64 = args.steps
+    t_fp64 = ms_fp64 / 1e3
+
+    # end to end through the public API: host parameters in, host solutions out
+    b = bipm.Batch(desc, BATCH, bipm.Options(precision=1), stream=stream)
+    x_host = torch.empty((BATCH, n), dtype=torch.float64).pin_memory()
+    y_host = torch.empty((BATCH, m), dtype=torch.float64).pin_memory()
+    b.set_problems(theta_host.numpy())
+    b.solve()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e_steps = max(1, args.steps // 2)
+    e2e_conv = 0
+    for _ in range(e_steps):
+        b.set_problems(theta_host.numpy())
+        b.solve()
+        b.get_solution(out=(x_host, y_host, None, None))
+        e2e_conv += int(np.sum(b.get_stats()["status"] == bipm.CONVERGED))
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    b.close()
+
+    def max_over_ranks(v):
+        if ws == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v):
+        if ws == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    t_mixed_max = max_over_ranks(t_mixed)
+    t_fp64_max = max_over_ranks(t_fp64)
+    t_e2e_max = max_over_ranks(t_e2e)
+    tot_conv_mixed = sum_over_ranks(conv_mixed * args.steps)
+    tot_conv_fp64 = sum_over_ranks(conv_fp64 * steps_fp64)
+    tot_e2e = sum_over_ranks(e2e_conv)
+
+    # roofline of the iteration kernel (the only kernel of any weight in a step)
+    f64_m, f32_m = step_flops(desc, st_mixed, 1)
+    f64_d, _ = step_flops(desc, st_fp64, 0)
+    k_mixed = statistics.median(kms_mixed) / 1e3
+    k_fp64 = statistics.median(kms_fp64) / 1e3
+    t_bound_mixed = f64_m / FP64_PEAK_NOMINAL + f32_m / FP32_PEAK_NOMINAL
+    roof = {
+        "bound": "alu", "unit": "TFLOP/s",
+        "achieved": (f64_m + f32_m) / k_mixed / 1e12,
+        "peak": (f64_m + f32_m) / t_bound_mixed / 1e12,
+        "frac": t_bound_mixed / k_mixed,
+        "traffic": None,
+        "kernel": "ipm_kernel<float,float> (FP32 factorisation, FP64 refinement)",
+        "flops_fp64_per_launch": f64_m, "flops_fp32_per_launch": f32_m,
+        "peak_source": "nominal FP64 152 SMs x 2 FMA/clk x 2 x 2.07 GHz = 1.26 TFLOP/s; "
+                       "FP32 x 128 FMA/clk = 80.5 TFLOP/s (ALU-bound kernel; mixed peak = "
+                       "flops / (f64/peak64 + f32/peak32))",
+        "fp64_form": {"achieved": f64_d / k_fp64 / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
+                      "frac": f64_d / k_fp64 / FP64_PEAK_NOMINAL},
+    }
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": tot_conv_mixed / t_mixed_max, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_mixed_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 factor + f64 refine",
+            "data": "synthetic (seeded SplitMix64 tracking problems; no public dataset exists)",
+            "config": {"workload": f"{WORKLOAD}: 1 quadrotor, RK4 N=30, 3 spheres, batch {BATCH}",
+                       "global_batch": BATCH * ws, "parallelism": f"replicas x{ws}",
+                       "l2": "per-step working set (~0.7 GB of slot workspaces) exceeds the 129 MB L2"},
+            "fp64": {"value": tot_conv_fp64 / t_fp64_max, "unit": UNIT,
+                     "ms_per_step": t_fp64_max * 1e3 / steps_fp64, "dtype": "f64"},
+            "converged_frac": conv_mixed / BATCH,
+            "iters_mean": float(np.mean(st_mixed["iters"])),
+            "e2e": {"value": tot_e2e / t_e2e_max, "unit": UNIT,
+                    "h2d_bytes_per_step": BATCH * desc_theta_len(desc) * 8,
+                    "d2h_bytes_per_step": BATCH * (n + m) * 8 + BATCH * stats_record_bytes()},
+            "roofline": roof,
+            "clocks": clk,
+            "gpu_launches": 2 * args.steps,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(desc, theta, budget_s=args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def stats_record_bytes():
+    import ctypes
+
+    from paper_2606_26341_gb300 import bipm
+    return ctypes.sizeof(bipm.StatsC)
+
+
+def desc_theta_len(desc):
+    from workloads import n_theta
+    return n_theta(desc)
+
+
+# ------------------------------------------------------------ CPU oracle
+def _oracle_one(args):
+    desc, theta = args
+    sys.path.insert(0, ROOT)
+    from oracle import ipm
+    from oracle.quadrotor import QuadNLP
+    t0 = time.perf_counter()
+    st, _ = ipm.solve(QuadNLP(desc, theta))
+    return st.status == ipm.CONVERGED, time.perf_counter() - t0
+
+
+def oracle_rate(desc, theta, n_problems, processes):
+    ctx = mp.get_context("spawn")
+    jobs = [(desc, theta[j]) for j in range(n_problems)]
+    with ctx.Pool(processes=processes) as pool:
+        pool.map(_oracle_one, jobs[:processes])  # warm the workers (imports)
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_one, jobs)
+        wall = time.perf_counter() - t0
+    conv = sum(1 for ok, _ in res if ok)
+    return conv, wall
+
+
+def cpu_baseline(desc, theta, budget_s=20.0):
+    cores = min(os.cpu_count() or 1, 16)
+    n_prob = cores  # one problem per core (~10 s of CPU work per problem)
+    conv, wall = oracle_rate(desc, theta, n_prob, cores)
+    return {"value": conv / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_prob} problems of the {WORKLOAD} workload, one per process, "
+                      f"{wall:.1f} s wall"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    desc, theta = make_batch(WORKLOAD, 64)
+    cores = min(os.cpu_count() or 1, 16)
+    ctx = mp.get_context("spawn")
+    per_step = cores
+    times, convs = [], []
+    with ctx.Pool(processes=cores) as pool:
+        for s in range(args.warmup + args.steps):
+            jobs = [(desc, theta[(s * per_step + j) % theta.shape[0]]) for j in range(per_step)]
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_one, jobs)
+            dt = time.perf_counter() - t0
+            if s >= args.warmup:
+                times.append(dt)
+                convs.append(sum(1 for ok, _ in res if ok))
+    total = sum(times)
+    val = sum(convs) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"{WORKLOAD}: 1 quadrotor, RK4 N=30, 3 spheres",
+                                        "per_step_sample": per_step},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} problems per step, one per process"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--batch", type=int, default=BATCH, help="problems per GPU (profiling runs only)")
+    ap.add_argument("--only-mixed", action="store_true", help="skip the FP64 form (profiling runs only)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * bipm — batched primal-dual interior-point solver for many small NLPs on one
+ * GB300 (sm_103a).  C ABI.
+ *
+ * The problem class is the parametric NLP of Sec. III, Eq. 1 of "Scaling
+ * Nonlinear Optimization: Many Problems One GPU":
+ *     min_x f(x, theta)  s.t.  c(x, theta) = 0,  x_L <= x <= x_U,
+ * batched as in Eq. 2: a batch holds many instances that share f, c and the
+ * bounds and differ only in their parameter vector theta_i.  Each call below
+ * advances or reads every instance ("slot") of one batch.
+ *
+ * The built-in problem family is quadrotor NMPC (Sec. VI): nq rigid-body
+ * quadrotors (12 states, 4 rotor thrusts each), RK4 multiple shooting over N
+ * intervals, a quadratic tracking cost, thrust bounds, and squared-distance
+ * inequalities written with slacks (spheres, vertical cylinders, pairwise
+ * separation).
+ *
+ * Layouts (one problem; double precision):
+ *   theta : xbar (12 nq) | reference circles (6 nq: cx, cy, cz, radius, rate,
+ *           phase; radius 0 = fixed goal) | spheres (4 n_spheres: cx, cy, cz, r) |
+ *           cylinders (3 n_cylinders: cx, cy, r)
+ *   x     : for k = 0..N: x_k (12 nq), then u_k (4 nq) if k < N, then s_k (ni)
+ *           if k >= 1; n = 12nq(N+1) + (4nq + ni) N
+ *   y     : x_0 - xbar (12 nq), then for k = 0..N-1: dynamics rows
+ *           x_{k+1} - F(x_k, u_k) (12 nq), then stage-(k+1) inequality rows
+ *           (ni); m = 12nq(N+1) + ni N
+ *   ni    : nq * n_spheres + nq * n_cylinders + (pair_dist > 0 ? nq(nq-1)/2 : 0)
+ *
+ * Ownership: the batch owns all device memory it uses; caller buffers are
+ * only read or written during the call.  `on_device` = 1 means the pointer is
+ * a device pointer valid on the batch's stream, 0 a host pointer.
+ *
+ * Errors: every int-returning call returns 0 on success or a negative code
+ * (BIPM_EINVAL bad argument or size, BIPM_ENOMEM allocation failure,
+ * BIPM_ECUDA CUDA error, BIPM_ESTATE call not valid in this state);
+ * bipm_last_error() returns a thread-local message for the last failure.
+ * Per-problem outcomes (converged, iteration cap, ...) are data, reported in
+ * bipm_stats.status, never as a call error.
+ */
+#ifndef BIPM_H
+#define BIPM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BIPM_EINVAL (-22)
+#define BIPM_ENOMEM (-12)
+#define BIPM_ECUDA (-100)
+#define BIPM_ESTATE (-101)
+
+/* per-problem status */
+#define BIPM_RUNNING 0
+#define BIPM_CONVERGED 1
+#define BIPM_MAX_ITER 2
+#define BIPM_RESTO_FAILED 3
+#define BIPM_EVAL_ERROR 4
+#define BIPM_TINY_STEP 5
+#define BIPM_EMPTY 6 /* slot holds no problem */
+
+#define BIPM_FILTER_CAP 64
+
+typedef struct bipm_batch bipm_batch;
+
+/* Shared structure of one batch (Eq. 2: identical f, c and bounds). */
+typedef struct {
+  int n_quads;        /* quadrotors per problem, 1..8 */
+  int horizon;        /* N, number of RK4 intervals, >= 1 */
+  double dt;          /* interval length [s] */
+  int n_spheres;      /* spherical obstacles (applied to every quadrotor) */
+  int n_cylinders;    /* vertical cylinders (applied to every quadrotor) */
+  double pair_dist;   /* minimum pairwise distance; 0 disables the pair rows */
+} bipm_problem_desc;
+
+typedef struct {
+  double tol;         /* scaled KKT tolerance E_0 (default 1e-6) */
+  int max_iter;       /* iteration cap, restoration iterations included (500) */
+  double mu_init;     /* initial barrier parameter (0.1) */
+  int precision;      /* 0: FP64 factorisation; 1: FP32 factorisation with FP64
+                         iterative refinement of the Newton step */
+} bipm_options;
+
+/* Per-slot outcome and counters. */
+typedef struct {
+  int status;
+  int iters;            /* iterations taken (restoration included) */
+  int resto_iters;
+  int soc;              /* second-order-correction solves */
+  int inertia_corr;     /* factorisations with delta_x > 0 */
+  int ir_steps;         /* iterative-refinement correction solves */
+  int fp64_escalations; /* FP32 factorisations redone in FP64 */
+  int tiny_steps;
+  int factorizations;   /* Riccati factorisations (inertia retries and FP64 redo included) */
+  int solves;           /* triangular solve sweeps (steps, SOC, refinement) */
+  int trials;           /* line-search trial-point evaluations */
+  int reserved;
+  double obj;           /* f at the final iterate */
+  double kkt_err;       /* scaled optimality error E_0 at the final iterate */
+  double primal_inf;    /* max |c| at the final iterate */
+  double mu;            /* final barrier parameter */
+} bipm_stats;
+
+/* Complete solver state of one slot (state injection, Sec. VI "Correctness").
+ * Vector members point to caller-owned host arrays of the stated length; a
+ * NULL vector member is skipped.  Restoration members are meaningful only in
+ * restoration mode (mode == 1) and read back as zeros otherwise. */
+typedef struct {
+  double* x;        /* n   primal (in restoration: the original variables) */
+  double* y;        /* m   equality multipliers (restoration: of c - p + n = 0) */
+  double* zl;       /* n   lower-bound multipliers (0 where no lower bound) */
+  double* zu;       /* n   upper-bound multipliers */
+  double* p;        /* m   restoration elastic variables p, n and their */
+  double* nn;       /* m   bound multipliers */
+  double* zp;       /* m */
+  double* zn;       /* m */
+  double* x_ref;    /* n   point where restoration started (x_R) */
+  double* filter;   /* 2*BIPM_FILTER_CAP (theta, phi) pairs, original problem */
+  double* filter_r; /* 2*BIPM_FILTER_CAP pairs, restoration problem */
+  int mode;         /* 0 original problem, 1 restoration */
+  int status;
+  int iter;
+  int need_init;    /* theta_max/theta_min and least-squares y pending */
+  int need_y_ls;    /* least-squares y at the next evaluation */
+  int tiny;         /* last step was a tiny step (original / restoration) */
+  int tiny_r;
+  int n_filter;
+  int n_filter_r;
+  double mu, dw_last, theta_max, theta_min;
+  double mu_r, dw_last_r, theta_max_r, theta_min_r, zeta, theta_ref;
+} bipm_iterate;
+
+/* Creates a batch of `capacity` slots for problems of structure `desc`.
+ * `cuda_stream` is a cudaStream_t (NULL = default stream) used by every call. */
+int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_options* opt,
+                      void* cuda_stream, bipm_batch** out);
+
+/* Sizes of one problem: primal n, equalities m, parameters n_theta. */
+int bipm_dims(const bipm_batch* b, int* n, int* m, int* n_theta);
+
+/* Loads `count` parameter vectors (count x n_theta, row-major) into slots
+ * first_slot.. and resets those slots to the default starting point (states
+ * at xbar, hover thrust, slacks at the inequality values), pushed inside the
+ * bounds as in IPOPT's initialisation; z = 1; y from least squares at the
+ * first iteration. */
+int bipm_set_problems(bipm_batch* b, const double* theta, int first_slot, int count,
+                      int on_device);
+
+/* Replaces the primal starting point (count x n) of slots first_slot.. (after
+ * bipm_set_problems); y (count x m) may be NULL (least squares). */
+int bipm_set_initial_guess(bipm_batch* b, const double* x, const double* y, int first_slot,
+                           int count, int on_device);
+
+/* Runs every loaded slot to termination (persistent kernel; a warp that
+ * finishes its problem takes the next unfinished one). */
+int bipm_solve(bipm_batch* b);
+
+/* Runs exactly `n_iterations` iterations on every running slot. */
+int bipm_step(bipm_batch* b, int n_iterations);
+
+/* Copies the final original-problem iterate of slots first_slot..; any output
+ * pointer may be NULL.  Shapes count x n (x, zl, zu) and count x m (y). */
+int bipm_get_solution(const bipm_batch* b, double* x, double* y, double* zl, double* zu,
+                      int first_slot, int count, int on_device);
+
+/* Per-slot status and counters (host array of `count` records). */
+int bipm_get_stats(const bipm_batch* b, bipm_stats* out, int first_slot, int count);
+
+/* Reads / writes the complete state of one slot (host arrays). */
+int bipm_get_iterate(const bipm_batch* b, int slot, bipm_iterate* out);
+int bipm_set_iterate(bipm_batch* b, int slot, const bipm_iterate* in);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char* bipm_last_error(void);
+
+/* Frees the batch and all its device memory. */
+void bipm_destroy(bipm_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIPM_H */

@@ -1,0 +1,259 @@
+"""Python binding of the bipm C ABI (include/bipm.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts numpy
+arrays / torch tensors to pointers and back.  It fails loudly when the
+library cannot be built or loaded: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RUNNING, CONVERGED, MAX_ITER, RESTO_FAILED, EVAL_ERROR, TINY_STEP, EMPTY = range(7)
+STATUS_NAMES = {RUNNING: "running", CONVERGED: "converged", MAX_ITER: "max_iter",
+                RESTO_FAILED: "resto_failed", EVAL_ERROR: "eval_error", TINY_STEP: "tiny_step",
+                EMPTY: "empty"}
+FILTER_CAP = 64
+
+
+class ProblemDescC(ctypes.Structure):
+    _fields_ = [("n_quads", ctypes.c_int), ("horizon", ctypes.c_int), ("dt", ctypes.c_double),
+                ("n_spheres", ctypes.c_int), ("n_cylinders", ctypes.c_int),
+                ("pair_dist", ctypes.c_double)]
+
+
+class OptionsC(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mu_init", ctypes.c_double),
+                ("precision", ctypes.c_int)]
+
+
+class StatsC(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("resto_iters", ctypes.c_int),
+                ("soc", ctypes.c_int), ("inertia_corr", ctypes.c_int), ("ir_steps", ctypes.c_int),
+                ("fp64_escalations", ctypes.c_int), ("tiny_steps", ctypes.c_int),
+                ("factorizations", ctypes.c_int), ("solves", ctypes.c_int),
+                ("trials", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("obj", ctypes.c_double), ("kkt_err", ctypes.c_double),
+                ("primal_inf", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class IterateC(ctypes.Structure):
+    _fields_ = [("x", _DP), ("y", _DP), ("zl", _DP), ("zu", _DP), ("p", _DP), ("nn", _DP),
+                ("zp", _DP), ("zn", _DP), ("x_ref", _DP), ("filter", _DP), ("filter_r", _DP),
+                ("mode", ctypes.c_int), ("status", ctypes.c_int), ("iter", ctypes.c_int),
+                ("need_init", ctypes.c_int), ("need_y_ls", ctypes.c_int), ("tiny", ctypes.c_int),
+                ("tiny_r", ctypes.c_int), ("n_filter", ctypes.c_int), ("n_filter_r", ctypes.c_int),
+                ("mu", ctypes.c_double), ("dw_last", ctypes.c_double),
+                ("theta_max", ctypes.c_double), ("theta_min", ctypes.c_double),
+                ("mu_r", ctypes.c_double), ("dw_last_r", ctypes.c_double),
+                ("theta_max_r", ctypes.c_double), ("theta_min_r", ctypes.c_double),
+                ("zeta", ctypes.c_double), ("theta_ref", ctypes.c_double)]
+
+
+EXPORTS = ["bipm_create_batch", "bipm_dims", "bipm_set_problems", "bipm_set_initial_guess",
+           "bipm_solve", "bipm_step", "bipm_get_solution", "bipm_get_stats", "bipm_get_iterate",
+           "bipm_set_iterate", "bipm_last_error", "bipm_destroy"]
+
+_LIB = None
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libbipm.so (building it first if needed)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.lib_path()
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbipm.so not found at {path}; build it with "
+                           "paper_2606_26341_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    i = ctypes.c_int
+    lib.bipm_create_batch.argtypes = [ctypes.POINTER(ProblemDescC), i, ctypes.POINTER(OptionsC), vp,
+                                      ctypes.POINTER(vp)]
+    lib.bipm_dims.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.bipm_set_problems.argtypes = [vp, vp, i, i, i]
+    lib.bipm_set_initial_guess.argtypes = [vp, vp, vp, i, i, i]
+    lib.bipm_solve.argtypes = [vp]
+    lib.bipm_step.argtypes = [vp, i]
+    lib.bipm_get_solution.argtypes = [vp, vp, vp, vp, vp, i, i, i]
+    lib.bipm_get_stats.argtypes = [vp, ctypes.POINTER(StatsC), i, i]
+    lib.bipm_get_iterate.argtypes = [vp, i, ctypes.POINTER(IterateC)]
+    lib.bipm_set_iterate.argtypes = [vp, i, ctypes.POINTER(IterateC)]
+    lib.bipm_last_error.restype = ctypes.c_char_p
+    lib.bipm_destroy.argtypes = [vp]
+    lib.bipm_destroy.restype = None
+    for name in EXPORTS:
+        if name != "bipm_last_error" and name != "bipm_destroy":
+            getattr(lib, name).restype = ctypes.c_int
+    _LIB = lib
+    return lib
+
+
+class BipmError(RuntimeError):
+    pass
+
+
+def _check(rc):
+    if rc != 0:
+        msg = load_library(False).bipm_last_error().decode()
+        raise BipmError(f"bipm error {rc}: {msg}")
+
+
+def _ptr(arr):
+    """(pointer, on_device) of a contiguous float64 numpy array or torch tensor."""
+    if arr is None:
+        return None, 0
+    if hasattr(arr, "data_ptr"):  # torch tensor
+        import torch
+        if arr.dtype != torch.float64 or not arr.is_contiguous():
+            raise ValueError("tensor must be contiguous float64")
+        return ctypes.c_void_p(arr.data_ptr()), int(arr.is_cuda)
+    if arr.dtype != np.float64 or not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous float64")
+    return arr.ctypes.data_as(ctypes.c_void_p), 0
+
+
+@dataclasses.dataclass
+class Options:
+    tol: float = 1e-6
+    max_iter: int = 500
+    mu_init: float = 0.1
+    precision: int = 0  # 0 FP64 factorisation, 1 FP32 factorisation + FP64 refinement
+
+
+class Batch:
+    """A batch of `capacity` quadrotor NMPC problems sharing one structure."""
+
+    def __init__(self, desc, capacity: int, options: Options | None = None, stream=None):
+        self.lib = load_library()
+        d = ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist)
+        o = options or Options()
+        oc = OptionsC(o.tol, o.max_iter, o.mu_init, o.precision)
+        h = ctypes.c_void_p()
+        sp = None
+        if stream is not None:
+            sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        _check(self.lib.bipm_create_batch(ctypes.byref(d), capacity, ctypes.byref(oc), sp,
+                                          ctypes.byref(h)))
+        self.h = h
+        self.capacity = capacity
+        self.desc = desc
+        self.options = o
+        n, m, nt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.bipm_dims(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(nt)))
+        self.n, self.m, self.n_theta = n.value, m.value, nt.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bipm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------- inputs
+    def set_problems(self, theta, first_slot: int = 0):
+        count = theta.shape[0]
+        p, dev = _ptr(theta)
+        _check(self.lib.bipm_set_problems(self.h, p, first_slot, count, dev))
+
+    def set_initial_guess(self, x, y=None, first_slot: int = 0):
+        px, dev = _ptr(x)
+        py, _ = _ptr(y)
+        _check(self.lib.bipm_set_initial_guess(self.h, px, py, first_slot, x.shape[0], dev))
+
+    # ---------------------------------------------------------- iterations
+    def solve(self):
+        _check(self.lib.bipm_solve(self.h))
+
+    def step(self, n_iterations: int = 1):
+        _check(self.lib.bipm_step(self.h, n_iterations))
+
+    # -------------------------------------------------------------- outputs
+    def get_solution(self, first_slot: int = 0, count: int | None = None, out=None):
+        """Returns (x, y, zl, zu) as numpy arrays (or fills the torch tensors in `out`)."""
+        count = self.capacity - first_slot if count is None else count
+        if out is None:
+            x = np.empty((count, self.n))
+            y = np.empty((count, self.m))
+            zl = np.empty((count, self.n))
+            zu = np.empty((count, self.n))
+        else:
+            x, y, zl, zu = out
+        ptrs = [_ptr(a) for a in (x, y, zl, zu)]
+        dev = max(pd for (_, pd) in ptrs)
+        _check(self.lib.bipm_get_solution(self.h, *[p for (p, _) in ptrs], first_slot, count, dev))
+        return x, y, zl, zu
+
+    def get_stats(self, first_slot: int = 0, count: int | None = None):
+        count = self.capacity - first_slot if count is None else count
+        arr = (StatsC * max(count, 1))()
+        _check(self.lib.bipm_get_stats(self.h, arr, first_slot, count))
+        fields = [f for f, _ in StatsC._fields_]
+        return {f: np.array([getattr(arr[i], f) for i in range(count)]) for f in fields}
+
+    def get_iterate(self, slot: int) -> dict:
+        n, m = self.n, self.m
+        bufs = {k: np.zeros(n) for k in ("x", "zl", "zu", "x_ref")}
+        bufs.update({k: np.zeros(m) for k in ("y", "p", "nn", "zp", "zn")})
+        bufs["filter"] = np.zeros(2 * FILTER_CAP)
+        bufs["filter_r"] = np.zeros(2 * FILTER_CAP)
+        it = IterateC()
+        for k, v in bufs.items():
+            setattr(it, k, v.ctypes.data_as(_DP))
+        _check(self.lib.bipm_get_iterate(self.h, slot, ctypes.byref(it)))
+        out = dict(bufs)
+        for f, _ in IterateC._fields_:
+            if f not in bufs:
+                out[f] = getattr(it, f)
+        out["filter"] = out["filter"][: 2 * out["n_filter"]].reshape(-1, 2)
+        out["filter_r"] = out["filter_r"][: 2 * out["n_filter_r"]].reshape(-1, 2)
+        return out
+
+    def set_iterate(self, slot: int, state: dict):
+        it = IterateC()
+        keep = []
+        n, m = self.n, self.m
+        sizes = {"x": n, "zl": n, "zu": n, "x_ref": n, "y": m, "p": m, "nn": m, "zp": m, "zn": m}
+        for k, ln in sizes.items():
+            v = state.get(k)
+            if v is None:
+                v = np.zeros(ln)
+            v = np.ascontiguousarray(v, dtype=np.float64)
+            if v.shape != (ln,):
+                raise ValueError(f"{k} must have length {ln}")
+            keep.append(v)
+            setattr(it, k, v.ctypes.data_as(_DP))
+        for k, nk in (("filter", "n_filter"), ("filter_r", "n_filter_r")):
+            f = np.zeros(2 * FILTER_CAP)
+            src = np.asarray(state.get(k, np.zeros((0, 2))), dtype=np.float64).reshape(-1)
+            f[: src.size] = src
+            keep.append(f)
+            setattr(it, k, f.ctypes.data_as(_DP))
+            setattr(it, nk, int(src.size // 2))
+        for f, _ in IterateC._fields_:
+            if f in sizes or f in ("filter", "filter_r", "n_filter", "n_filter_r"):
+                continue
+            setattr(it, f, state.get(f, 0))
+        _check(self.lib.bipm_set_iterate(self.h, slot, ctypes.byref(it)))

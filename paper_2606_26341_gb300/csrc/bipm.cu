@@ -1,0 +1,523 @@
+// C-ABI library: batch management, the persistent iteration kernel and the
+// copies in and out of the per-slot workspaces.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bipm.h"
+#include "kernels.cuh"
+
+using namespace bipm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                               \
+  do {                                                                               \
+    cudaError_t e_ = (expr);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(BIPM_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+}  // namespace
+
+struct bipm_batch {
+  bipm_problem_desc desc;
+  Dims d;
+  Layout L;
+  Options opt;
+  int capacity;
+  cudaStream_t stream;
+  double* f64 = nullptr;
+  void* tb = nullptr;
+  void* tf = nullptr;
+  double* theta = nullptr;
+  SlotState* st = nullptr;
+  int* counter = nullptr;
+  Params* dparams = nullptr;
+  double* stage = nullptr;  // staging buffer for gathers / scatters
+  size_t stage_bytes = 0;
+  int smem_per_warp = 0;
+  int blocks = 0;
+  int loaded = 0;
+};
+
+namespace {
+
+__global__ void gather_kernel(const Params* __restrict__ P, int first, int count, long long off,
+                              int len, double* __restrict__ out) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)count * len) return;
+  int j = (int)(t / len), i = (int)(t - (t / len) * len);
+  out[t] = P->f64[(long long)(first + j) * P->L.slot_f64 + off + i];
+}
+
+// ------------------------------------------------------------- host helpers
+void* iter_kernel_ptr(int precision) { return precision ? iter_kernel_f32() : iter_kernel_f64(); }
+void* init_kernel_ptr(int precision) { return precision ? init_kernel_f32() : init_kernel_f64(); }
+
+Layout make_layout(const Dims& d, int precision) {
+  Layout L;
+  std::memset(&L, 0, sizeof(L));
+  const long long n = d.n, m = d.m, N = d.N, nx = d.nx, nu = d.nu;
+  L.nw = n + 2 * m;
+  L.nk = L.nw + m;
+  long long o = 0;
+  auto take = [&](long long len) {
+    long long at = o;
+    o += (len + 3) & ~3LL;  // 32-byte aligned arrays
+    return at;
+  };
+  L.x = take(L.nw);
+  L.zl = take(L.nw);
+  L.zu = take(L.nw);
+  L.y = take(m);
+  L.xt = take(L.nw);
+  L.c = take(m);
+  L.ct = take(m);
+  L.csoc = take(m);
+  L.gf = take(L.nw);
+  L.jty = take(L.nw);
+  L.gphi = take(L.nw);
+  L.xr = take(n);
+  L.dsv = take(N * d.ni);
+  L.ev = take(N * d.ni);
+  L.ipv = take(m);
+  L.inv = take(m);
+  L.dv = take(m);
+  L.rhs = take(L.nk);
+  L.sol = take(L.nk);
+  L.rhs2 = take(L.nk);
+  L.sol2 = take(L.nk);
+  L.res = take(L.nk);
+  L.corr = take(L.nk);
+  L.rct = take(m);
+  L.filt = take(2 * (kFilterCap + 1));  // one spare entry: a full filter appends before dropping
+  L.filt_r = take(2 * (kFilterCap + 1));
+  // factor region layout (element offsets)
+  long long fo = 0;
+  auto ftake = [&](long long len) {
+    long long at = fo;
+    fo += (len + 7) & ~7LL;
+    return at;
+  };
+  L.Pt = ftake((N + 1) * nx * nx);
+  L.K = ftake(N * nu * nx);
+  L.Lr = ftake(N * nu * nu);
+  L.LM = ftake((N + 1) * nx * nx);
+  L.Yr = ftake((N + 1) * nx * nx);
+  L.kff = ftake(N * nu);
+  L.ptv = ftake((N + 1) * nx);
+  L.fac_size = fo;
+  L.f64_fac = precision ? take(L.fac_size) : 0;
+  L.slot_f64 = o;
+  long long bo = 0;
+  L.A = bo;
+  bo += ((N * d.nq * 144) + 7) & ~7LL;
+  L.B = bo;
+  bo += ((N * d.nq * 48) + 7) & ~7LL;
+  L.H = bo;
+  bo += ((N * d.nq * 100) + 7) & ~7LL;
+  L.slot_tb = bo;
+  return L;
+}
+
+int check_slots(const bipm_batch* b, int first, int count) {
+  if (!b) return fail(BIPM_EINVAL, "null batch");
+  if (first < 0 || count < 0 || first + count > b->capacity)
+    return fail(BIPM_EINVAL, "slot range [" + std::to_string(first) + ", " +
+                                 std::to_string(first + count) + ") outside capacity " +
+                                 std::to_string(b->capacity));
+  return 0;
+}
+
+int ensure_stage(bipm_batch* b, size_t bytes) {
+  if (bytes <= b->stage_bytes) return 0;
+  if (b->stage) cudaFree(b->stage);
+  b->stage = nullptr;
+  b->stage_bytes = 0;
+  if (cudaMalloc(&b->stage, bytes) != cudaSuccess) return fail(BIPM_ENOMEM, "staging buffer");
+  b->stage_bytes = bytes;
+  return 0;
+}
+
+int run_iterations(bipm_batch* b, int n_iter) {
+  if (!b->loaded) return fail(BIPM_ESTATE, "no problems loaded");
+  CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
+  void* args[] = {&b->dparams, &n_iter};
+  CUDA_TRY(cudaLaunchKernel(iter_kernel_ptr(b->opt.precision), dim3(b->blocks),
+                            dim3(32 * kWarpsPerBlock), args,
+                            (size_t)b->smem_per_warp * kWarpsPerBlock, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return 0;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+const char* bipm_last_error(void) { return g_err.c_str(); }
+
+int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_options* opt,
+                      void* cuda_stream, bipm_batch** out) {
+  if (!desc || !out) return fail(BIPM_EINVAL, "null argument");
+  *out = nullptr;
+  if (desc->n_quads < 1 || desc->n_quads > 8) return fail(BIPM_EINVAL, "n_quads must be 1..8");
+  if (desc->horizon < 1 || desc->horizon > 1000) return fail(BIPM_EINVAL, "horizon must be 1..1000");
+  if (!(desc->dt > 0.0) || !std::isfinite(desc->dt)) return fail(BIPM_EINVAL, "dt must be > 0");
+  if (desc->n_spheres < 0 || desc->n_cylinders < 0 || desc->n_spheres > 256 || desc->n_cylinders > 256)
+    return fail(BIPM_EINVAL, "obstacle counts must be 0..256");
+  if (!(desc->pair_dist >= 0.0)) return fail(BIPM_EINVAL, "pair_dist must be >= 0");
+  if (capacity < 0) return fail(BIPM_EINVAL, "capacity must be >= 0");
+  bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0};
+  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || (o.precision != 0 && o.precision != 1))
+    return fail(BIPM_EINVAL, "bad options");
+
+  bipm_batch* b = new bipm_batch();
+  b->desc = *desc;
+  Dims& d = b->d;
+  d.nq = desc->n_quads;
+  d.N = desc->horizon;
+  d.nx = 12 * d.nq;
+  d.nu = 4 * d.nq;
+  d.n_sph = desc->n_spheres;
+  d.n_cyl = desc->n_cylinders;
+  d.n_pairs = desc->pair_dist > 0.0 ? d.nq * (d.nq - 1) / 2 : 0;
+  d.ni = d.nq * d.n_sph + d.nq * d.n_cyl + d.n_pairs;
+  d.n = d.nx * (d.N + 1) + (d.nu + d.ni) * d.N;
+  d.m = d.nx * (d.N + 1) + d.ni * d.N;
+  d.dt = desc->dt;
+  d.pair_d = desc->pair_dist;
+  d.th_x = 0;
+  d.th_ref = 12 * d.nq;
+  d.th_sph = d.th_ref + 6 * d.nq;
+  d.th_cyl = d.th_sph + 4 * d.n_sph;
+  d.n_theta = d.th_cyl + 3 * d.n_cyl;
+  b->opt.tol = o.tol;
+  b->opt.max_iter = o.max_iter;
+  b->opt.mu_init = o.mu_init;
+  b->opt.precision = o.precision;
+  b->capacity = capacity;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->L = make_layout(d, o.precision);
+  b->smem_per_warp = (int)scratch_bytes(d.nq, d.nx, d.nu);
+
+  auto cleanup = [&](int code, const std::string& msg) {
+    bipm_destroy(b);
+    return fail(code, msg);
+  };
+  size_t cap = (size_t)std::max(capacity, 1);
+  size_t tsz = o.precision ? sizeof(float) : sizeof(double);
+  if (cudaMalloc(&b->f64, cap * b->L.slot_f64 * sizeof(double)) != cudaSuccess)
+    return cleanup(BIPM_ENOMEM, "workspace (FP64 vectors)");
+  if (cudaMalloc(&b->tb, cap * b->L.slot_tb * tsz) != cudaSuccess)
+    return cleanup(BIPM_ENOMEM, "workspace (derivative blocks)");
+  if (cudaMalloc(&b->tf, cap * b->L.fac_size * tsz) != cudaSuccess)
+    return cleanup(BIPM_ENOMEM, "workspace (factors)");
+  if (cudaMalloc(&b->theta, cap * d.n_theta * sizeof(double) + 8) != cudaSuccess)
+    return cleanup(BIPM_ENOMEM, "parameters");
+  if (cudaMalloc(&b->st, cap * sizeof(SlotState)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "states");
+  if (cudaMalloc(&b->counter, sizeof(int)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "counter");
+  if (cudaMalloc(&b->dparams, sizeof(Params)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "params");
+  if (cudaMemset(b->f64, 0, cap * b->L.slot_f64 * sizeof(double)) != cudaSuccess)
+    return cleanup(BIPM_ECUDA, "memset");
+  {
+    std::vector<SlotState> empty(cap);
+    std::memset(empty.data(), 0, cap * sizeof(SlotState));
+    for (auto& s : empty) s.status = BIPM_EMPTY;
+    if (cudaMemcpy(b->st, empty.data(), cap * sizeof(SlotState), cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup(BIPM_ECUDA, "state init");
+  }
+  Params P;
+  std::memset(&P, 0, sizeof(P));
+  P.d = d;
+  P.L = b->L;
+  P.opt = b->opt;
+  P.n_slots = capacity;
+  P.f64 = b->f64;
+  P.tb = b->tb;
+  P.tf = b->tf;
+  P.theta = b->theta;
+  P.st = b->st;
+  P.work_counter = b->counter;
+  P.smem_per_warp = b->smem_per_warp;
+  if (cudaMemcpy(b->dparams, &P, sizeof(P), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cleanup(BIPM_ECUDA, "params copy");
+
+  // persistent grid: as many resident blocks as fit, capped by the work
+  void* kfn = iter_kernel_ptr(o.precision);
+  size_t smem = (size_t)b->smem_per_warp * kWarpsPerBlock;
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return cleanup(BIPM_ECUDA, "shared memory attribute");
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * kWarpsPerBlock, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return cleanup(BIPM_ECUDA, "kernel does not fit on an SM (shared memory " + std::to_string(smem) + " B)");
+  int need = (int)((cap + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  b->blocks = std::max(1, std::min(need, sms * per_sm));
+  *out = b;
+  g_err.clear();
+  return 0;
+}
+
+int bipm_dims(const bipm_batch* b, int* n, int* m, int* n_theta) {
+  if (!b) return fail(BIPM_EINVAL, "null batch");
+  if (n) *n = b->d.n;
+  if (m) *m = b->d.m;
+  if (n_theta) *n_theta = b->d.n_theta;
+  return 0;
+}
+
+int bipm_set_problems(bipm_batch* b, const double* theta, int first_slot, int count, int on_device) {
+  int rc = check_slots(b, first_slot, count);
+  if (rc) return rc;
+  if (count == 0) return 0;
+  if (!theta) return fail(BIPM_EINVAL, "null theta");
+  size_t bytes = (size_t)count * b->d.n_theta * sizeof(double);
+  if (bytes)
+    CUDA_TRY(cudaMemcpyAsync(b->theta + (size_t)first_slot * b->d.n_theta, theta, bytes,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+  const double* none = nullptr;
+  void* args[] = {&b->dparams, &first_slot, &count, &none, &none};
+  int threads = 128;
+  int blocks = (count * 32 + threads - 1) / threads;
+  CUDA_TRY(cudaLaunchKernel(init_kernel_ptr(b->opt.precision), dim3(blocks), dim3(threads), args, 0,
+                            b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  b->loaded = 1;
+  return 0;
+}
+
+int bipm_set_initial_guess(bipm_batch* b, const double* x, const double* y, int first_slot, int count,
+                           int on_device) {
+  int rc = check_slots(b, first_slot, count);
+  if (rc) return rc;
+  if (count == 0) return 0;
+  if (!x) return fail(BIPM_EINVAL, "null x");
+  size_t xb = (size_t)count * b->d.n * sizeof(double);
+  size_t yb = y ? (size_t)count * b->d.m * sizeof(double) : 0;
+  if ((rc = ensure_stage(b, xb + yb))) return rc;
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_TRY(cudaMemcpyAsync(b->stage, x, xb, kind, b->stream));
+  double* ys = nullptr;
+  if (y) {
+    ys = b->stage + (size_t)count * b->d.n;
+    CUDA_TRY(cudaMemcpyAsync(ys, y, yb, kind, b->stream));
+  }
+  double* xs = b->stage;
+  void* args[] = {&b->dparams, &first_slot, &count, &xs, &ys};
+  int threads = 128;
+  int blocks = (count * 32 + threads - 1) / threads;
+  CUDA_TRY(cudaLaunchKernel(init_kernel_ptr(b->opt.precision), dim3(blocks), dim3(threads), args, 0,
+                            b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return 0;
+}
+
+int bipm_solve(bipm_batch* b) {
+  if (!b) return fail(BIPM_EINVAL, "null batch");
+  if (b->capacity == 0) return 0;
+  return run_iterations(b, 0);
+}
+
+int bipm_step(bipm_batch* b, int n_iterations) {
+  if (!b) return fail(BIPM_EINVAL, "null batch");
+  if (n_iterations < 1) return fail(BIPM_EINVAL, "n_iterations must be >= 1");
+  if (b->capacity == 0) return 0;
+  return run_iterations(b, n_iterations);
+}
+
+int bipm_get_solution(const bipm_batch* bc, double* x, double* y, double* zl, double* zu,
+                      int first_slot, int count, int on_device) {
+  bipm_batch* b = const_cast<bipm_batch*>(bc);
+  int rc = check_slots(b, first_slot, count);
+  if (rc) return rc;
+  if (count == 0) return 0;
+  struct Item { double* dst; long long off; int len; } items[4] = {
+      {x, b->L.x, b->d.n}, {y, b->L.y, b->d.m}, {zl, b->L.zl, b->d.n}, {zu, b->L.zu, b->d.n}};
+  for (auto& it : items) {
+    if (!it.dst) continue;
+    size_t bytes = (size_t)count * it.len * sizeof(double);
+    if ((rc = ensure_stage(b, bytes))) return rc;
+    long long total = (long long)count * it.len;
+    int threads = 256;
+    int blocks = (int)((total + threads - 1) / threads);
+    gather_kernel<<<blocks, threads, 0, b->stream>>>(b->dparams, first_slot, count, it.off, it.len,
+                                                     b->stage);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(it.dst, b->stage, bytes,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return 0;
+}
+
+int bipm_get_stats(const bipm_batch* b, bipm_stats* out, int first_slot, int count) {
+  int rc = check_slots(b, first_slot, count);
+  if (rc) return rc;
+  if (count == 0) return 0;
+  if (!out) return fail(BIPM_EINVAL, "null output");
+  std::vector<SlotState> h(count);
+  CUDA_TRY(cudaMemcpyAsync(h.data(), b->st + first_slot, count * sizeof(SlotState),
+                           cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < count; ++i) {
+    const SlotState& s = h[i];
+    bipm_stats& o = out[i];
+    o.status = s.status;
+    o.iters = s.iter;
+    o.resto_iters = s.n_resto_iter;
+    o.soc = s.n_soc;
+    o.inertia_corr = s.n_inertia_corr;
+    o.ir_steps = s.n_ir_steps;
+    o.fp64_escalations = s.n_escalations;
+    o.tiny_steps = s.n_tiny;
+    o.factorizations = s.n_fact;
+    o.solves = s.n_solve;
+    o.trials = s.n_trial;
+    o.reserved = 0;
+    o.obj = s.obj;
+    o.kkt_err = s.kkt;
+    o.primal_inf = s.inf;
+    o.mu = s.mu;
+  }
+  return 0;
+}
+
+int bipm_get_iterate(const bipm_batch* b, int slot, bipm_iterate* out) {
+  int rc = check_slots(b, slot, 1);
+  if (rc) return rc;
+  if (!out) return fail(BIPM_EINVAL, "null output");
+  const Dims& d = b->d;
+  const Layout& L = b->L;
+  const double* base = b->f64 + (size_t)slot * L.slot_f64;
+  std::vector<double> buf(L.slot_f64);
+  CUDA_TRY(cudaMemcpyAsync(buf.data(), base, L.slot_f64 * sizeof(double), cudaMemcpyDeviceToHost,
+                           b->stream));
+  SlotState s;
+  CUDA_TRY(cudaMemcpyAsync(&s, b->st + slot, sizeof(s), cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  auto put = [&](double* dst, long long off, int len) {
+    if (dst) std::memcpy(dst, buf.data() + off, len * sizeof(double));
+  };
+  put(out->x, L.x, d.n);
+  put(out->y, L.y, d.m);
+  put(out->zl, L.zl, d.n);
+  put(out->zu, L.zu, d.n);
+  put(out->p, L.x + d.n, d.m);
+  put(out->nn, L.x + d.n + d.m, d.m);
+  put(out->zp, L.zl + d.n, d.m);
+  put(out->zn, L.zl + d.n + d.m, d.m);
+  put(out->x_ref, L.xr, d.n);
+  put(out->filter, L.filt, 2 * kFilterCap);
+  put(out->filter_r, L.filt_r, 2 * kFilterCap);
+  out->mode = s.mode;
+  out->status = s.status;
+  out->iter = s.iter;
+  out->need_init = s.need_init;
+  out->need_y_ls = s.need_y_ls;
+  out->tiny = s.tiny;
+  out->tiny_r = s.tiny_r;
+  out->n_filter = s.n_filt;
+  out->n_filter_r = s.n_filt_r;
+  out->mu = s.mu;
+  out->dw_last = s.dw_last;
+  out->theta_max = s.theta_max;
+  out->theta_min = s.theta_min;
+  out->mu_r = s.mu_r;
+  out->dw_last_r = s.dw_last_r;
+  out->theta_max_r = s.theta_max_r;
+  out->theta_min_r = s.theta_min_r;
+  out->zeta = s.zeta;
+  out->theta_ref = s.theta_ref;
+  return 0;
+}
+
+int bipm_set_iterate(bipm_batch* b, int slot, const bipm_iterate* in) {
+  int rc = check_slots(b, slot, 1);
+  if (rc) return rc;
+  if (!in) return fail(BIPM_EINVAL, "null input");
+  if (!b->loaded) return fail(BIPM_ESTATE, "load the problem (bipm_set_problems) first");
+  if (in->n_filter < 0 || in->n_filter > kFilterCap || in->n_filter_r < 0 || in->n_filter_r > kFilterCap)
+    return fail(BIPM_EINVAL, "filter length outside 0..64");
+  if (in->mode != 0 && in->mode != 1) return fail(BIPM_EINVAL, "mode must be 0 or 1");
+  const Dims& d = b->d;
+  const Layout& L = b->L;
+  double* base = b->f64 + (size_t)slot * L.slot_f64;
+  std::vector<double> buf(L.slot_f64);
+  CUDA_TRY(cudaMemcpy(buf.data(), base, L.slot_f64 * sizeof(double), cudaMemcpyDeviceToHost));
+  auto get = [&](const double* src, long long off, int len) {
+    if (src)
+      std::memcpy(buf.data() + off, src, len * sizeof(double));
+    else
+      std::memset(buf.data() + off, 0, len * sizeof(double));
+  };
+  get(in->x, L.x, d.n);
+  get(in->y, L.y, d.m);
+  get(in->zl, L.zl, d.n);
+  get(in->zu, L.zu, d.n);
+  get(in->p, L.x + d.n, d.m);
+  get(in->nn, L.x + d.n + d.m, d.m);
+  get(in->zp, L.zl + d.n, d.m);
+  get(in->zn, L.zl + d.n + d.m, d.m);
+  std::memset(buf.data() + L.zu + d.n, 0, 2 * d.m * sizeof(double));
+  get(in->x_ref, L.xr, d.n);
+  get(in->filter, L.filt, 2 * kFilterCap);
+  get(in->filter_r, L.filt_r, 2 * kFilterCap);
+  CUDA_TRY(cudaMemcpy(base, buf.data(), L.slot_f64 * sizeof(double), cudaMemcpyHostToDevice));
+  SlotState s;
+  CUDA_TRY(cudaMemcpy(&s, b->st + slot, sizeof(s), cudaMemcpyDeviceToHost));
+  s.mode = in->mode;
+  s.status = in->status;
+  s.iter = in->iter;
+  s.need_init = in->need_init;
+  s.need_y_ls = in->need_y_ls;
+  s.tiny = in->tiny;
+  s.tiny_r = in->tiny_r;
+  s.n_filt = in->n_filter;
+  s.n_filt_r = in->n_filter_r;
+  s.mu = in->mu;
+  s.dw_last = in->dw_last;
+  s.theta_max = in->theta_max;
+  s.theta_min = in->theta_min;
+  s.mu_r = in->mu_r;
+  s.dw_last_r = in->dw_last_r;
+  s.theta_max_r = in->theta_max_r;
+  s.theta_min_r = in->theta_min_r;
+  s.zeta = in->zeta;
+  s.theta_ref = in->theta_ref;
+  CUDA_TRY(cudaMemcpy(b->st + slot, &s, sizeof(s), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+void bipm_destroy(bipm_batch* b) {
+  if (!b) return;
+  cudaFree(b->f64);
+  cudaFree(b->tb);
+  cudaFree(b->tf);
+  cudaFree(b->theta);
+  cudaFree(b->st);
+  cudaFree(b->counter);
+  cudaFree(b->dparams);
+  cudaFree(b->stage);
+  delete b;
+}
+
+}  // extern "C"

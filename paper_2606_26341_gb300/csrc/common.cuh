@@ -1,0 +1,139 @@
+// Shared device definitions of the batched interior-point solver: dual numbers,
+// warp reductions, the per-slot state record and the workspace layout.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bipm.h"
+#include "scalar.cuh"
+
+namespace bipm {
+
+// --------------------------------------------------------------- warp helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_or(int v) { return __any_sync(0xffffffffu, v); }
+
+// ---------------------------------------------------------- algorithm options
+struct Options {
+  double tol;
+  int max_iter;
+  double mu_init;
+  int precision;  // 0 = FP64 factorisation, 1 = FP32 factorisation + FP64 refinement
+};
+
+// IPOPT constants (Wachter & Biegler 2006 defaults)
+constexpr double kSmax = 100.0, kKappaEps = 10.0, kKappaMu = 0.2, kThetaMu = 1.5;
+constexpr double kTauMin = 0.99, kKappaSigma = 1e10;
+constexpr double kGammaTheta = 1e-5, kGammaPhi = 1e-8, kDelta = 1.0, kSTheta = 1.1;
+constexpr double kSPhi = 2.3, kEtaPhi = 1e-8, kGammaAlpha = 0.05, kKappaSoc = 0.99;
+constexpr int kPmax = 4;
+constexpr double kKappaD = 1e-4;
+constexpr double kDwInit = 1e-4, kDwMin = 1e-20, kDwMax = 1e40;
+constexpr double kKwMinus = 1.0 / 3.0, kKwPlus = 8.0, kKwPlusBar = 100.0;
+constexpr double kBoundPush = 1e-2, kBoundFrac = 1e-2, kYmax = 1e3;
+constexpr double kRho = 1000.0, kKappaResto = 0.9;
+constexpr int kFilterCap = 64;
+constexpr int kLsMaxTrials = 60;
+constexpr int kIrMaxSteps = 10;
+constexpr double kIrTol = 1e-10;
+constexpr double kEpsMach = 2.220446049250313e-16;
+
+enum Mode : int { MODE_NORMAL = 0, MODE_RESTO = 1 };
+enum VarKind : int { VK_FREE = 0, VK_BOX = 1, VK_LOWER = 2 };
+
+// ------------------------------------------------------------ problem layout
+struct Dims {
+  int nq, N, nx, nu, ni, n, m;
+  int n_sph, n_cyl, n_pairs;
+  int n_theta;
+  double dt, pair_d;
+  // offsets inside theta
+  int th_x, th_ref, th_sph, th_cyl;
+};
+
+// primal offset of x_k, u_k, s_k inside one problem's variable vector
+__device__ __forceinline__ int off_x(const Dims& d, int k) {
+  return k == 0 ? 0 : (d.nx + d.nu) + (k - 1) * (d.nx + d.nu + d.ni);
+}
+__device__ __forceinline__ int off_u(const Dims& d, int k) { return off_x(d, k) + d.nx; }
+__device__ __forceinline__ int off_s(const Dims& d, int k) {  // k >= 1
+  return off_x(d, k) + d.nx + (k < d.N ? d.nu : 0);
+}
+// equality rows: init block [0, nx), then per k: dynamics (nx) then inequalities (ni)
+__device__ __forceinline__ int row_dyn(const Dims& d, int k) { return d.nx + k * (d.nx + d.ni); }
+__device__ __forceinline__ int row_ineq(const Dims& d, int k) {  // inequalities of stage k >= 1
+  return d.nx + (k - 1) * (d.nx + d.ni) + d.nx;
+}
+
+__device__ __forceinline__ int var_kind(const Dims& d, int i) {
+  if (i < d.nx + d.nu) return i < d.nx ? VK_FREE : VK_BOX;
+  int j = i - (d.nx + d.nu);
+  int blk = d.nx + d.nu + d.ni;
+  int k = 1 + j / blk;
+  int loc = j - (k - 1) * blk;
+  if (k >= d.N) return loc < d.nx ? VK_FREE : VK_LOWER;
+  if (loc < d.nx) return VK_FREE;
+  return loc < d.nx + d.nu ? VK_BOX : VK_LOWER;
+}
+
+// Offsets (in elements) of the per-slot arrays.  Every slot owns `slot_f64`
+// doubles and `slot_tf` factor-type elements; arrays of one slot are contiguous
+// so the warp that owns the slot reads them with unit stride.
+// "W-sized" arrays have nw = n + 2m entries: the primal variables x followed
+// by the restoration elastics p and n (used in restoration mode only).
+// "K-sized" arrays have nw + m entries: a W-sized part then an m-sized part.
+struct Layout {
+  long long nw, nk;
+  // FP64 arrays
+  long long x, zl, zu, y, xt, c, ct, csoc, gf, jty, gphi, xr;
+  long long dsv, ev, ipv, inv, dv;  // condensation diagonals (slacks / rows)
+  long long rhs, sol, rhs2, sol2, res, corr, rct;
+  long long filt, filt_r;
+  long long f64_fac;  // FP64 factor arrays (mixed precision: escalation and LS)
+  long long slot_f64;
+  // derivative blocks (block type) and factor arrays (factor type), per slot
+  long long A, B, H;
+  long long slot_tb;
+  long long Pt, K, Lr, LM, Yr, kff, ptv;  // offsets inside a factor region
+  long long fac_size;
+};
+// Per-slot scalar state (the complete solver state besides the vectors).
+struct SlotState {
+  int status, mode, iter, need_init, need_y_ls, tiny, tiny_r, n_filt, n_filt_r;
+  int n_soc, n_resto_iter, n_inertia_corr, n_ir_steps, n_escalations, n_tiny, problem_id;
+  int n_fact, n_solve, n_trial, pad_;
+  double mu, dw_last, theta_max, theta_min;
+  double mu_r, dw_last_r, theta_max_r, theta_min_r, zeta, theta_ref;
+  double obj, kkt, inf, last_alpha;
+};
+
+struct Params {
+  Dims d;
+  Layout L;
+  Options opt;
+  int n_slots;
+  double* f64;        // n_slots * slot_f64
+  void* tb;           // n_slots * slot_tb (double or float)
+  void* tf;           // n_slots * fac_size (double or float)
+  double* theta;      // n_slots * n_theta
+  SlotState* st;      // n_slots
+  int* work_counter;  // persistent scheduling counter
+  int smem_per_warp;  // bytes of dynamic shared memory per warp
+};
+
+}  // namespace bipm

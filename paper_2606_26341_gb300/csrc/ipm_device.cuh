@@ -1,0 +1,1136 @@
+// One fused interior-point iteration for one problem, executed by one warp.
+//
+// Every problem of a batch runs this same code; the per-problem state record
+// (mode, barrier parameter, filter, status) decides which of the branches of
+// Table I a problem takes.  Branch decisions are warp-uniform, so problems only
+// diverge across warps, never inside one: the heterogeneous iteration fusion of
+// Sec. V realised as per-problem control flow in one kernel, without
+// per-branch launches.
+//
+// Linear algebra: the augmented system Eq. 7 of one NMPC problem is block
+// banded.  Slacks and inequality multipliers are eliminated stage by stage,
+// the initial-state row fixes Delta x_0, and the remaining optimal-control KKT
+// system is factorised by a backward Riccati recursion.  The inertia required
+// after Eq. 7 (n positive, m negative eigenvalues) holds exactly when every
+// stage pivot block R^_k is positive definite (in restoration also the state
+// pivots I + D^1/2 P D^1/2), so the Cholesky factorisations of these blocks
+// are the inertia test.
+#pragma once
+
+#include "common.cuh"
+#include "quad_model.cuh"
+
+namespace bipm {
+
+#define LANE_LOOP(i, n) for (int i = lane; i < (n); i += 32)
+
+template <class T>
+struct Fac {  // factor arrays of one slot in precision T
+  T *Pt, *K, *Lr, *LM, *Yr, *kff, *ptv;
+};
+
+template <class T>
+__device__ __forceinline__ Fac<T> make_fac(T* base, const Layout& L) {
+  Fac<T> f;
+  f.Pt = base + L.Pt;
+  f.K = base + L.K;
+  f.Lr = base + L.Lr;
+  f.LM = base + L.LM;
+  f.Yr = base + L.Yr;
+  f.kff = base + L.kff;
+  f.ptv = base + L.ptv;
+  return f;
+}
+
+enum FactorFlags : int { FF_IDENT = 1, FF_RESTO = 2 };
+
+template <class TB, class TF>
+struct Ctx {
+  const Params* P;
+  Dims d;
+  Layout L;
+  int lane;
+  int slot;
+  double* f;           // this slot's FP64 arrays
+  TB* blk;             // derivative blocks
+  Fac<TF> fac;         // factor arrays in the factorisation precision
+  Fac<double> fac64;   // FP64 factor arrays (= fac when TF is double)
+  const double* th;    // theta of this slot
+  char* smem;          // per-warp shared scratch
+  // phase data of the current iteration
+  int resto;
+  int nw;              // primal length of the current phase (n or n + 2m)
+  double mu;           // barrier parameter of the current phase
+  double zeta;         // restoration: sqrt(mu) at its start
+  double dw;           // regularisation used in the last factorisation
+  int use64;           // 1: the last factorisation is the FP64 one
+  int n_ir, n_esc;
+  int n_fact, n_solve, n_trial;  // work counters of the current iteration
+};
+
+__device__ __forceinline__ double sq(double a) { return a * a; }
+
+// ------------------------------------------------------------ index helpers
+struct VarInfo {
+  int kind;   // VK_FREE, VK_BOX, VK_LOWER
+  int k;      // stage
+  int loc;    // position in the stage block
+};
+
+__device__ __forceinline__ VarInfo var_info(const Dims& d, int i) {
+  VarInfo v;
+  if (i < d.nx + d.nu) {
+    v.k = 0;
+    v.loc = i;
+    v.kind = i < d.nx ? VK_FREE : VK_BOX;
+    return v;
+  }
+  int j = i - (d.nx + d.nu);
+  int blk = d.nx + d.nu + d.ni;
+  v.k = 1 + j / blk;
+  v.loc = j - (v.k - 1) * blk;
+  if (v.k >= d.N)
+    v.kind = v.loc < d.nx ? VK_FREE : VK_LOWER;
+  else
+    v.kind = v.loc < d.nx ? VK_FREE : (v.loc < d.nx + d.nu ? VK_BOX : VK_LOWER);
+  return v;
+}
+
+// kind of entry i of a W-sized vector (x, then p, then n)
+__device__ __forceinline__ int wkind(const Dims& d, int i) {
+  return i < d.n ? var_kind(d, i) : VK_LOWER;
+}
+__device__ __forceinline__ bool has_lower(int kind) { return kind != VK_FREE; }
+__device__ __forceinline__ bool has_upper(int kind) { return kind == VK_BOX; }
+
+// ------------------------------------------------------ reference trajectory
+__device__ __forceinline__ double ref_comp(const double* th, const Dims& d, int k, int q, int j) {
+  // reference state component j of quad q at stage k: circle position and
+  // velocity, zero attitude and body rates
+  if (j >= 6) return 0.0;
+  const double* r = th + d.th_ref + 6 * q;
+  double t = k * d.dt;
+  double a = r[4] * t + r[5];
+  double sa, ca;
+  sincos(a, &sa, &ca);
+  switch (j) {
+    case 0: return r[0] + r[3] * ca;
+    case 1: return r[1] + r[3] * sa;
+    case 2: return r[2];
+    case 3: return -r[3] * r[4] * sa;
+    case 4: return r[3] * r[4] * ca;
+    default: return 0.0;
+  }
+}
+
+__device__ __forceinline__ double cost_weight(const Dims& d, int k, int j) {
+  return q_weight(j) * (k == d.N ? kQNscale : 1.0);
+}
+
+// --------------------------------------------------------- inequality rows
+// Value and gradient (w.r.t. the quad positions) of inequality j of a stage.
+struct IneqRow {
+  int q0, q1;      // quads involved (q1 < 0: one quad)
+  int ncomp;       // position components involved per quad (3, or 2 for cylinders)
+  double gval;     // g(x)
+  double grad[6];  // d g / d p_q0 (3) then d g / d p_q1 (3)
+  double hdiag;    // Hessian of g: hdiag * (I on involved components); pairs: +-hdiag
+};
+
+__device__ __forceinline__ IneqRow ineq_row(const Dims& d, const double* th, const double* xk,
+                                            int j) {
+  IneqRow r;
+  r.q1 = -1;
+  r.hdiag = 2.0;
+  int nsq = d.nq * d.n_sph;
+  int ncq = d.nq * d.n_cyl;
+  if (j < nsq) {
+    int q = j / d.n_sph, o = j - (j / d.n_sph) * d.n_sph;
+    const double* s = th + d.th_sph + 4 * o;
+    const double* p = xk + 12 * q;
+    double dx = p[0] - s[0], dy = p[1] - s[1], dz = p[2] - s[2];
+    r.q0 = q;
+    r.ncomp = 3;
+    r.gval = dx * dx + dy * dy + dz * dz - s[3] * s[3];
+    r.grad[0] = 2 * dx; r.grad[1] = 2 * dy; r.grad[2] = 2 * dz;
+  } else if (j < nsq + ncq) {
+    int jj = j - nsq;
+    int q = jj / d.n_cyl, o = jj - (jj / d.n_cyl) * d.n_cyl;
+    const double* s = th + d.th_cyl + 3 * o;
+    const double* p = xk + 12 * q;
+    double dx = p[0] - s[0], dy = p[1] - s[1];
+    r.q0 = q;
+    r.ncomp = 2;
+    r.gval = dx * dx + dy * dy - s[2] * s[2];
+    r.grad[0] = 2 * dx; r.grad[1] = 2 * dy; r.grad[2] = 0.0;
+  } else {
+    int rem = j - nsq - ncq;
+    int a = 0;
+    while (rem >= d.nq - 1 - a) { rem -= d.nq - 1 - a; ++a; }
+    int b = a + 1 + rem;
+    const double* pa = xk + 12 * a;
+    const double* pb = xk + 12 * b;
+    double dx = pa[0] - pb[0], dy = pa[1] - pb[1], dz = pa[2] - pb[2];
+    r.q0 = a;
+    r.q1 = b;
+    r.ncomp = 3;
+    r.gval = dx * dx + dy * dy + dz * dz - d.pair_d * d.pair_d;
+    r.grad[0] = 2 * dx; r.grad[1] = 2 * dy; r.grad[2] = 2 * dz;
+    r.grad[3] = -2 * dx; r.grad[4] = -2 * dy; r.grad[5] = -2 * dz;
+  }
+  return r;
+}
+
+// gradient component of row r w.r.t. stage-state component i (0..nx-1); also
+// returns whether the row touches that component
+__device__ __forceinline__ double ineq_grad_at(const IneqRow& r, int i) {
+  int q = i / 12, c = i - 12 * (i / 12);
+  if (c >= r.ncomp) return 0.0;
+  if (q == r.q0) return r.grad[c];
+  if (q == r.q1) return r.grad[3 + c];
+  return 0.0;
+}
+// Hessian entry of row r at stage-state components (i, j)
+__device__ __forceinline__ double ineq_hess_at(const IneqRow& r, int i, int j) {
+  int qi = i / 12, ci = i - 12 * qi;
+  int qj = j / 12, cj = j - 12 * qj;
+  if (ci != cj || ci >= r.ncomp) return 0.0;
+  double si = qi == r.q0 ? 1.0 : (qi == r.q1 ? -1.0 : 0.0);
+  double sj = qj == r.q0 ? 1.0 : (qj == r.q1 ? -1.0 : 0.0);
+  return r.hdiag * si * sj;
+}
+
+// ---------------------------------------------------------------- evaluation
+// Constraint values c(x) (original problem) into cout and the objective f(x).
+template <class TB, class TF>
+__device__ double eval_values(Ctx<TB, TF>& c, const double* x, double* cout) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  LANE_LOOP(i, d.nx) cout[i] = x[i] - c.th[d.th_x + i];
+  for (int t = lane; t < d.N * d.nq; t += 32) {
+    int k = t / d.nq, q = t - (t / d.nq) * d.nq;
+    double xx[12], uu[4], F[12];
+    const double* xk = x + off_x(d, k) + 12 * q;
+    const double* uk = x + off_u(d, k) + 4 * q;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) xx[i] = xk[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) uu[i] = uk[i];
+    rk4_value<double>(xx, uu, d.dt, F);
+    const double* xn = x + off_x(d, k + 1) + 12 * q;
+    double* cr = cout + row_dyn(d, k) + 12 * q;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) cr[i] = xn[i] - F[i];
+  }
+  for (int t = lane; t < d.N * d.ni; t += 32) {
+    int k = 1 + t / d.ni, j = t - (t / d.ni) * d.ni;
+    IneqRow r = ineq_row(d, c.th, x + off_x(d, k), j);
+    cout[row_ineq(d, k) + j] = r.gval - x[off_s(d, k) + j];
+  }
+  double fs = 0.0;
+  for (int t = lane; t < (d.N + 1) * d.nx; t += 32) {
+    int k = t / d.nx, i = t - (t / d.nx) * d.nx;
+    int q = i / 12, j = i - 12 * (i / 12);
+    double e = x[off_x(d, k) + i] - ref_comp(c.th, d, k, q, j);
+    fs += cost_weight(d, k, j) * e * e;
+  }
+  for (int t = lane; t < d.N * d.nu; t += 32) {
+    int k = t / d.nu, i = t - (t / d.nu) * d.nu;
+    double e = x[off_u(d, k) + i] - kHover;
+    fs += kRweight * e * e;
+  }
+  __syncwarp();
+  return warp_sum(fs);
+}
+
+// Gradient of the objective of the current phase into g (W-sized).
+template <class TB, class TF>
+__device__ void eval_grad(Ctx<TB, TF>& c, const double* x, double* g) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  const double* xr = c.f + c.L.xr;
+  LANE_LOOP(i, c.nw) {
+    double v;
+    if (i >= d.n) {
+      v = kRho;
+    } else if (c.resto) {
+      double dr = fmin(1.0, 1.0 / fmax(fabs(xr[i]), 1e-300));
+      v = c.zeta * dr * dr * (x[i] - xr[i]);
+    } else {
+      VarInfo vi = var_info(d, i);
+      if (vi.loc < d.nx) {
+        int q = vi.loc / 12, j = vi.loc - 12 * (vi.loc / 12);
+        v = 2.0 * cost_weight(d, vi.k, j) * (x[i] - ref_comp(c.th, d, vi.k, q, j));
+      } else if (vi.kind == VK_BOX) {
+        v = 2.0 * kRweight * (x[i] - kHover);
+      } else {
+        v = 0.0;
+      }
+    }
+    g[i] = v;
+  }
+  __syncwarp();
+}
+
+// Objective of the restoration problem: rho sum(p + n) + zeta/2 |D_R (x - x_R)|^2.
+template <class TB, class TF>
+__device__ double resto_objective(Ctx<TB, TF>& c, const double* w) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  const double* xr = c.f + c.L.xr;
+  double acc = 0.0;
+  LANE_LOOP(i, c.nw) {
+    if (i >= d.n) {
+      acc += kRho * w[i];
+    } else {
+      double dr = fmin(1.0, 1.0 / fmax(fabs(xr[i]), 1e-300));
+      acc += 0.5 * c.zeta * sq(dr * (w[i] - xr[i]));
+    }
+  }
+  return warp_sum(acc);
+}
+
+// Jacobian / Hessian blocks of the dynamics by forward-over-reverse dual
+// numbers: lane task (k, q, j) seeds direction j of (eta, omega, u) of quad q
+// at stage k.  The columns of A for p and v are constant (F is affine in p, v)
+// and the Hessian of lam^T F vanishes in those rows, so only ten directions
+// carry derivatives.  lam = -y_dyn (the Lagrangian term is +y^T (x_{k+1} - F)).
+template <class TB, class TF>
+__device__ void eval_blocks(Ctx<TB, TF>& c, const double* x, const double* y, bool hess) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  typedef Dual<TB> DT;
+  const int ntask = d.N * d.nq * 10;
+  for (int t = lane; t < ntask; t += 32) {
+    int j = t - (t / 10) * 10;
+    int kq = t / 10;
+    int k = kq / d.nq, q = kq - (kq / d.nq) * d.nq;
+    const double* xk = x + off_x(d, k) + 12 * q;
+    const double* uk = x + off_u(d, k) + 4 * q;
+    DT xx[12], uu[4], F[12], gx[12], gu[4];
+    TB lam[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      xx[i] = DT{(TB)xk[i], (TB)0};
+      lam[i] = hess ? (TB)(-y[row_dyn(d, k) + 12 * q + i]) : (TB)0;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) uu[i] = DT{(TB)uk[i], (TB)0};
+    if (j < 6)
+      xx[6 + j].d = (TB)1;
+    else
+      uu[j - 6].d = (TB)1;
+    rk4_fwd_rev<DT>(xx, uu, (TB)d.dt, lam, F, gx, gu);
+    TB* A = c.blk + c.L.A + ((long long)k * d.nq + q) * 144;
+    TB* B = c.blk + c.L.B + ((long long)k * d.nq + q) * 48;
+    TB* H = c.blk + c.L.H + ((long long)k * d.nq + q) * 100;
+    if (j < 6) {
+#pragma unroll
+      for (int r = 0; r < 12; ++r) A[(6 + j) * 12 + r] = F[r].d;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 12; ++r) B[(j - 6) * 12 + r] = F[r].d;
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) H[j * 10 + r] = gx[6 + r].d;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) H[j * 10 + 6 + r] = gu[r].d;
+    if (j == 0) {
+      for (int col = 0; col < 6; ++col)
+        for (int r = 0; r < 12; ++r) {
+          TB v = (TB)0;
+          if (col < 3) v = (r == col) ? (TB)1 : (TB)0;
+          else v = (r == col - 3) ? (TB)d.dt : ((r == col) ? (TB)1 : (TB)0);
+          A[col * 12 + r] = v;
+        }
+    }
+  }
+  __syncwarp();
+}
+
+// J^T y of the original constraints (x-part, n entries) in FP64, plus the
+// elastic parts (-y, +y) in restoration.
+template <class TB, class TF>
+__device__ void eval_jty(Ctx<TB, TF>& c, const double* x, const double* y, double* jty) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  for (int t = lane; t < d.N * d.nq; t += 32) {
+    int k = t / d.nq, q = t - (t / d.nq) * d.nq;
+    double xx[12], uu[4], F[12], gx[12], gu[4], lam[12];
+    const double* xk = x + off_x(d, k) + 12 * q;
+    const double* uk = x + off_u(d, k) + 4 * q;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      xx[i] = xk[i];
+      lam[i] = -y[row_dyn(d, k) + 12 * q + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) uu[i] = uk[i];
+    rk4_fwd_rev<double>(xx, uu, d.dt, lam, F, gx, gu);
+    const double* yprev = y + (k == 0 ? 0 : row_dyn(d, k - 1)) + 12 * q;
+    double* jx = jty + off_x(d, k) + 12 * q;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) jx[i] = gx[i] + yprev[i];
+    double* ju = jty + off_u(d, k) + 4 * q;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ju[i] = gu[i];
+  }
+  LANE_LOOP(i, d.nx) jty[off_x(d, d.N) + i] = y[row_dyn(d, d.N - 1) + i];
+  __syncwarp();
+  // inequality rows: + G_k^T y_ineq on the positions, - y_ineq on the slacks
+  for (int t = lane; t < d.N * 3 * d.nq; t += 32) {
+    int k = 1 + t / (3 * d.nq);
+    int pc = t - (t / (3 * d.nq)) * (3 * d.nq);
+    int q = pc / 3, comp = pc - 3 * (pc / 3);
+    int i = 12 * q + comp;
+    const double* xk = x + off_x(d, k);
+    const double* yi = y + row_ineq(d, k);
+    double acc = 0.0;
+    for (int r = 0; r < d.ni; ++r) {
+      IneqRow row = ineq_row(d, c.th, xk, r);
+      acc += ineq_grad_at(row, i) * yi[r];
+    }
+    jty[off_x(d, k) + i] += acc;
+  }
+  for (int t = lane; t < d.N * d.ni; t += 32) {
+    int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
+    jty[off_s(d, k) + r] = -y[row_ineq(d, k) + r];
+  }
+  if (c.resto) {
+    LANE_LOOP(i, d.m) {
+      jty[d.n + i] = -y[i];
+      jty[d.n + d.m + i] = y[i];
+    }
+  }
+  __syncwarp();
+}
+
+// ------------------------------------------------- barrier quantities (FP64)
+// Sigma_i = z_L/s_L + z_U/s_U of W-entry i.
+template <class TB, class TF>
+__device__ __forceinline__ double sigma_of(Ctx<TB, TF>& c, int i) {
+  int kind = wkind(c.d, i);
+  if (kind == VK_FREE) return 0.0;
+  const double* x = c.f + c.L.x;
+  const double* zl = c.f + c.L.zl;
+  const double* zu = c.f + c.L.zu;
+  double s = zl[i] / x[i];
+  if (kind == VK_BOX) s += zu[i] / (kUmax - x[i]);
+  return s;
+}
+
+// Diagonal Hessian of the objective on W-entry i (cost weights, or zeta D_R^2
+// in restoration, or 1 for the least-squares multiplier system).
+template <class TB, class TF>
+__device__ __forceinline__ double obj_hdiag(Ctx<TB, TF>& c, int i, int flags) {
+  if (flags & FF_IDENT) return 1.0;
+  const Dims& d = c.d;
+  if (i >= d.n) return 0.0;
+  if (c.resto) {
+    const double* xr = c.f + c.L.xr;
+    double dr = fmin(1.0, 1.0 / fmax(fabs(xr[i]), 1e-300));
+    return c.zeta * dr * dr;
+  }
+  VarInfo vi = var_info(d, i);
+  if (vi.loc < d.nx) return 2.0 * cost_weight(d, vi.k, vi.loc - 12 * (vi.loc / 12));
+  if (vi.kind == VK_BOX) return 2.0 * kRweight;
+  return 0.0;
+}
+
+// Condensation diagonals for regularisation dw:
+//   slack (k, r):  D_s = H_ss + Sigma_s + dw,  E = D_s / (1 + D_s D_g)
+//   row i (restoration): 1/(Sigma_p + dw), 1/(Sigma_n + dw), D = their sum
+template <class TB, class TF>
+__device__ void compute_diag(Ctx<TB, TF>& c, double dw, int flags) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  double* dsv = c.f + c.L.dsv;
+  double* ev = c.f + c.L.ev;
+  double* ipv = c.f + c.L.ipv;
+  double* inv = c.f + c.L.inv;
+  double* dv = c.f + c.L.dv;
+  const double* w = c.f + c.L.x;
+  const double* zl = c.f + c.L.zl;
+  LANE_LOOP(i, d.m) {
+    if (c.resto) {
+      double ip = 1.0 / (zl[d.n + i] / w[d.n + i] + dw);
+      double in = 1.0 / (zl[d.n + d.m + i] / w[d.n + d.m + i] + dw);
+      ipv[i] = ip;
+      inv[i] = in;
+      dv[i] = ip + in;
+    } else {
+      ipv[i] = 0.0;
+      inv[i] = 0.0;
+      dv[i] = 0.0;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < d.N * d.ni; t += 32) {
+    int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
+    int vi = off_s(d, k) + r;
+    double ds = (flags & FF_IDENT) ? 1.0 : obj_hdiag(c, vi, flags) + sigma_of(c, vi) + dw;
+    double dg = dv[row_ineq(d, k) + r];
+    dsv[t] = ds;
+    ev[t] = ds / (1.0 + ds * dg);
+  }
+  __syncwarp();
+}
+
+// -------------------------------------------------------- factorisation
+// Builds the condensed stage matrices and runs the Riccati recursion in
+// precision TX.  Returns 0 if some pivot block is not positive definite
+// (wrong inertia), 1 on success, 2 on success with a pivot inside the FP32
+// guard band (the caller refactors in FP64).
+template <class TX>
+struct Scratch {
+  TX *Pb, *PA, *PB, *Rh, *Sh, *Kb, *Ab, *Bb, *v0, *v1, *v2, *v3;
+  double* R64;
+};
+
+template <class TX>
+__device__ __forceinline__ Scratch<TX> scratch(char* smem, const Dims& d) {
+  Scratch<TX> s;
+  TX* p = (TX*)smem;
+  int nx = d.nx, nu = d.nu;
+  s.Pb = p; p += nx * nx;
+  s.PA = p; p += nx * nx;
+  s.PB = p; p += nx * nu;
+  s.Rh = p; p += nu * nu;
+  s.Sh = p; p += nu * nx;
+  s.Kb = p; p += nu * nx;
+  s.Ab = p; p += 144 * d.nq;
+  s.Bb = p; p += 48 * d.nq;
+  s.v0 = p; p += nx;
+  s.v1 = p; p += nx;
+  s.v2 = p; p += nx;
+  s.v3 = p; p += nx;
+  size_t off = ((size_t)((char*)p - smem) + 15) & ~(size_t)15;
+  s.R64 = (double*)(smem + off);
+  return s;
+}
+
+// bytes of per-warp scratch for problems of dims d (FP64 worst case)
+__host__ __device__ inline size_t scratch_bytes(int nq, int nx, int nu) {
+  size_t e = (size_t)2 * nx * nx + 3 * (size_t)nx * nu + (size_t)nu * nu + 192 * (size_t)nq +
+             4 * (size_t)nx;
+  size_t b = ((e * 8 + 15) & ~(size_t)15) + (size_t)nu * nu * 8;
+  return (b + 127) & ~(size_t)127;
+}
+
+// Q~_k (state block, written to Pb as TX), including the inequality terms.
+template <class TB, class TF, class TX>
+__device__ void add_state_block(Ctx<TB, TF>& c, int k, TX* Q, double dw, int flags,
+                                const double* y, bool accumulate) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  const int nx = d.nx;
+  const double* x = c.f + c.L.x;
+  const double* ev = c.f + c.L.ev;
+  const bool ident = flags & FF_IDENT;
+  LANE_LOOP(e, nx * nx) {
+    int i = e / nx, j = e - (e / nx) * nx;
+    double v = 0.0;
+    if (i == j) v += obj_hdiag(c, off_x(d, k) + i, flags) + (ident ? 0.0 : dw);
+    int qi = i / 12, qj = j / 12;
+    int ci = i - 12 * qi, cj = j - 12 * qj;
+    if (!ident && k < d.N && qi == qj && ci >= 6 && cj >= 6) {
+      const TB* H = c.blk + c.L.H + ((long long)k * d.nq + qi) * 100;
+      v += (double)H[(cj - 6) * 10 + (ci - 6)];
+    }
+    if (k >= 1 && ci < 3 && cj < 3) {
+      const double* xk = x + off_x(d, k);
+      const double* yi = y + row_ineq(d, k);
+      for (int r = 0; r < d.ni; ++r) {
+        IneqRow row = ineq_row(d, c.th, xk, r);
+        double gi = ineq_grad_at(row, i), gj = ineq_grad_at(row, j);
+        v += ev[(k - 1) * d.ni + r] * gi * gj;
+        if (!ident) v += yi[r] * ineq_hess_at(row, i, j);
+      }
+    }
+    if (accumulate)
+      Q[e] = (TX)((double)Q[e] + v);
+    else
+      Q[e] = (TX)v;
+  }
+}
+
+// Cholesky of the nxn symmetric matrix in `a` (row-major, double) in place;
+// lower triangle holds L.  Returns min pivot ratio L_jj^2 / a_jj, or -1 if a
+// pivot is not positive.
+__device__ inline double warp_cholesky(double* a, int n, int lane) {
+  double ratio = 1.0;
+  for (int j = 0; j < n; ++j) {
+    __syncwarp();
+    double diag0 = a[j * n + j];
+    // a_jj already holds the Schur complement pivot
+    double piv = diag0;
+    if (!(piv > 0.0) || !isfinite(piv)) return -1.0;
+    double l = sqrt(piv);
+    __syncwarp();
+    if (lane == 0) a[j * n + j] = l;
+    for (int i = j + 1 + lane; i < n; i += 32) a[i * n + j] /= l;
+    __syncwarp();
+    int rem = n - j - 1;
+    for (int e = lane; e < rem * rem; e += 32) {
+      int i = j + 1 + e / rem, t = j + 1 + (e - (e / rem) * rem);
+      if (t <= i) a[i * n + t] -= a[i * n + j] * a[t * n + j];
+    }
+  }
+  __syncwarp();
+  return ratio;
+}
+
+// Pivot ratio of a factorised matrix: min_j L_jj^2 / orig_jj
+__device__ __forceinline__ double pivot_ratio(const double* L, const double* diag, int n) {
+  double r = 1.0;
+  for (int j = 0; j < n; ++j) r = fmin(r, L[j * n + j] * L[j * n + j] / fmax(diag[j], 1e-300));
+  return r;
+}
+
+// Restoration: P~ = P - Y^T Y with Y = L_M^{-1} D^1/2 P, M = I + D^1/2 P D^1/2 = L_M L_M^T.
+template <class TB, class TF, class TX>
+__device__ bool resto_transform(Ctx<TB, TF>& c, TX* Pb, const double* D, TX* LM, TX* Y) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  const int nx = d.nx;
+  // M in LM (as TX) ; factor in double would need nx^2 doubles: factor in TX
+  LANE_LOOP(e, nx * nx) {
+    int i = e / nx, j = e - (e / nx) * nx;
+    double v = sqrt(D[i]) * (double)Pb[e] * sqrt(D[j]) + (i == j ? 1.0 : 0.0);
+    LM[e] = (TX)v;
+  }
+  __syncwarp();
+  for (int j = 0; j < nx; ++j) {
+    __syncwarp();
+    double piv = (double)LM[j * nx + j];
+    if (!(piv > 0.0) || !isfinite(piv)) return false;
+    double l = sqrt(piv);
+    __syncwarp();
+    if (lane == 0) LM[j * nx + j] = (TX)l;
+    for (int i = j + 1 + lane; i < nx; i += 32) LM[i * nx + j] = (TX)((double)LM[i * nx + j] / l);
+    __syncwarp();
+    int rem = nx - j - 1;
+    for (int e = lane; e < rem * rem; e += 32) {
+      int i = j + 1 + e / rem, t = j + 1 + (e - (e / rem) * rem);
+      if (t <= i) LM[i * nx + t] = (TX)((double)LM[i * nx + t] - (double)LM[i * nx + j] * (double)LM[t * nx + j]);
+    }
+  }
+  __syncwarp();
+  // Y = L^{-1} (D^1/2 P): forward substitution, one column per lane
+  for (int col = lane; col < nx; col += 32) {
+    for (int i = 0; i < nx; ++i) {
+      double acc = sqrt(D[i]) * (double)Pb[i * nx + col];
+      for (int t = 0; t < i; ++t) acc -= (double)LM[i * nx + t] * (double)Y[t * nx + col];
+      Y[i * nx + col] = (TX)(acc / (double)LM[i * nx + i]);
+    }
+  }
+  __syncwarp();
+  LANE_LOOP(e, nx * nx) {
+    int i = e / nx, j = e - (e / nx) * nx;
+    double acc = 0.0;
+    for (int t = 0; t < nx; ++t) acc += (double)Y[t * nx + i] * (double)Y[t * nx + j];
+    Pb[e] = (TX)((double)Pb[e] - acc);
+  }
+  __syncwarp();
+  return true;
+}
+
+template <class TB, class TF, class TX>
+__device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const double* y) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  const int nx = d.nx, nu = d.nu, nq = d.nq, N = d.N;
+  const bool ident = flags & FF_IDENT;
+  const bool resto = flags & FF_RESTO;
+  Scratch<TX> s = scratch<TX>(c.smem, d);
+  const double* dv = c.f + c.L.dv;
+  c.n_fact++;
+  compute_diag(c, dw, flags);
+  double min_ratio = 1.0;
+
+  // terminal block P_N = Q~_N
+  add_state_block<TB, TF, TX>(c, N, s.Pb, dw, flags, y, false);
+  __syncwarp();
+  if (resto) {
+    if (!resto_transform<TB, TF, TX>(c, s.Pb, dv + row_dyn(d, N - 1), F.LM + (long long)N * nx * nx,
+                                     F.Yr + (long long)N * nx * nx))
+      return 0;
+  }
+  LANE_LOOP(e, nx * nx) F.Pt[(long long)N * nx * nx + e] = s.Pb[e];
+  __syncwarp();
+
+  for (int k = N - 1; k >= 0; --k) {
+    // stage Jacobian blocks
+    const TB* Ag = c.blk + c.L.A + (long long)k * nq * 144;
+    const TB* Bg = c.blk + c.L.B + (long long)k * nq * 48;
+    LANE_LOOP(e, 144 * nq) s.Ab[e] = (TX)Ag[e];
+    LANE_LOOP(e, 48 * nq) s.Bb[e] = (TX)Bg[e];
+    __syncwarp();
+    // PA = P~ A, PB = P~ B (block-diagonal A, B; column-major blocks)
+    LANE_LOOP(e, nx * nx) {
+      int i = e / nx, col = e - (e / nx) * nx;
+      int q = col / 12, cc = col - 12 * q;
+      const TX* a = s.Ab + q * 144 + cc * 12;
+      const TX* prow = s.Pb + i * nx + 12 * q;
+      TX acc = 0;
+#pragma unroll
+      for (int r = 0; r < 12; ++r) acc += prow[r] * a[r];
+      s.PA[e] = acc;
+    }
+    LANE_LOOP(e, nx * nu) {
+      int i = e / nu, col = e - (e / nu) * nu;
+      int q = col / 4, cc = col - 4 * q;
+      const TX* b = s.Bb + q * 48 + cc * 12;
+      const TX* prow = s.Pb + i * nx + 12 * q;
+      TX acc = 0;
+#pragma unroll
+      for (int r = 0; r < 12; ++r) acc += prow[r] * b[r];
+      s.PB[e] = acc;
+    }
+    __syncwarp();
+    // R^ = R~ + B^T P~ B ; S^ = S + B^T P~ A
+    LANE_LOOP(e, nu * nu) {
+      int a = e / nu, b = e - (e / nu) * nu;
+      int qa = a / 4, ca = a - 4 * qa;
+      const TX* bcol = s.Bb + qa * 48 + ca * 12;
+      TX acc = 0;
+#pragma unroll
+      for (int r = 0; r < 12; ++r) acc += bcol[r] * s.PB[(12 * qa + r) * nu + b];
+      double v = (double)acc;
+      int ui = off_u(d, k) + a;
+      if (a == b) v += obj_hdiag(c, ui, flags) + (ident ? 0.0 : sigma_of(c, ui) + dw);
+      int qb = b / 4;
+      if (!ident && qa == qb) {
+        const TB* H = c.blk + c.L.H + ((long long)k * nq + qa) * 100;
+        v += (double)H[(6 + (b - 4 * qb)) * 10 + (6 + ca)];
+      }
+      s.Rh[e] = (TX)v;
+      s.R64[e] = v;
+    }
+    LANE_LOOP(e, nu * nx) {
+      int a = e / nx, col = e - (e / nx) * nx;
+      int qa = a / 4, ca = a - 4 * qa;
+      const TX* bcol = s.Bb + qa * 48 + ca * 12;
+      TX acc = 0;
+#pragma unroll
+      for (int r = 0; r < 12; ++r) acc += bcol[r] * s.PA[(12 * qa + r) * nx + col];
+      double v = (double)acc;
+      int qc = col / 12, cc = col - 12 * qc;
+      if (!ident && qc == qa && cc >= 6) {
+        const TB* H = c.blk + c.L.H + ((long long)k * nq + qa) * 100;
+        v += (double)H[(cc - 6) * 10 + (6 + ca)];
+      }
+      s.Sh[e] = (TX)v;
+    }
+    __syncwarp();
+    // Q^ = A^T P~ A + Q~_k (overwrites Pb)
+    LANE_LOOP(e, nx * nx) {
+      int i = e / nx, col = e - (e / nx) * nx;
+      int q = i / 12, ci = i - 12 * q;
+      const TX* acol = s.Ab + q * 144 + ci * 12;
+      TX acc = 0;
+#pragma unroll
+      for (int r = 0; r < 12; ++r) acc += acol[r] * s.PA[(12 * q + r) * nx + col];
+      s.Pb[e] = acc;
+    }
+    __syncwarp();
+    add_state_block<TB, TF, TX>(c, k, s.Pb, dw, flags, y, true);
+    // Cholesky of R^ in FP64: the inertia test
+    double* R64 = s.R64;
+    __syncwarp();
+    double diag_j[32];
+    for (int j = 0; j < nu && j < 32; ++j) diag_j[j] = R64[j * nu + j];
+    if (warp_cholesky(R64, nu, lane) < 0.0) return 0;
+    if (sizeof(TX) == 4) min_ratio = fmin(min_ratio, pivot_ratio(R64, diag_j, nu < 32 ? nu : 32));
+    // K = -R^{-1} S^: one column per lane
+    for (int col = lane; col < nx; col += 32) {
+      double z[32];
+      for (int i = 0; i < nu; ++i) {
+        double acc = (double)s.Sh[i * nx + col];
+        for (int t = 0; t < i; ++t) acc -= R64[i * nu + t] * z[t];
+        z[i] = acc / R64[i * nu + i];
+      }
+      for (int i = nu - 1; i >= 0; --i) {
+        double acc = z[i];
+        for (int t = i + 1; t < nu; ++t) acc -= R64[t * nu + i] * z[t];
+        z[i] = acc / R64[i * nu + i];
+      }
+      for (int i = 0; i < nu; ++i) s.Kb[i * nx + col] = (TX)(-z[i]);
+    }
+    __syncwarp();
+    // P_k = Q^ + S^T K, symmetrised
+    LANE_LOOP(e, nx * nx) {
+      int i = e / nx, j = e - (e / nx) * nx;
+      TX acc = 0;
+      for (int a = 0; a < nu; ++a) acc += s.Sh[a * nx + i] * s.Kb[a * nx + j];
+      s.PA[e] = s.Pb[e] + acc;
+    }
+    __syncwarp();
+    LANE_LOOP(e, nx * nx) {
+      int i = e / nx, j = e - (e / nx) * nx;
+      s.Pb[e] = (TX)(0.5 * ((double)s.PA[i * nx + j] + (double)s.PA[j * nx + i]));
+    }
+    TX* Kg = F.K + (long long)k * nu * nx;
+    LANE_LOOP(e, nu * nx) Kg[e] = s.Kb[e];
+    TX* Lg = F.Lr + (long long)k * nu * nu;
+    LANE_LOOP(e, nu * nu) Lg[e] = (TX)R64[e];
+    __syncwarp();
+    if (resto) {
+      const double* D = dv + (k == 0 ? 0 : row_dyn(d, k - 1));
+      if (!resto_transform<TB, TF, TX>(c, s.Pb, D, F.LM + (long long)k * nx * nx,
+                                       F.Yr + (long long)k * nx * nx))
+        return 0;
+    }
+    LANE_LOOP(e, nx * nx) F.Pt[(long long)k * nx * nx + e] = s.Pb[e];
+    __syncwarp();
+  }
+  if (sizeof(TX) == 4 && min_ratio < 1e-5) return 2;
+  return 1;
+}
+
+// ------------------------------------------------------------------ solve
+// Solves K delta = -r for the current factorisation (precision TX), where K
+// is the augmented matrix of Eq. 7 (restoration: with the elastic variables)
+// and r is K-sized: [r_x (n) | r_p (m) | r_n (m) | r_c (m)] (r_p, r_n only in
+// restoration; the layout always reserves them).  out has the same layout.
+template <class TB, class TF, class TX>
+__device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, int flags,
+                      const double* y) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  const int nx = d.nx, nu = d.nu, N = d.N, n = d.n, m = d.m;
+  const bool resto = flags & FF_RESTO;
+  Scratch<TX> s = scratch<TX>(c.smem, d);
+  c.n_solve++;
+  const double* dsv = c.f + c.L.dsv;
+  const double* ev = c.f + c.L.ev;
+  const double* ipv = c.f + c.L.ipv;
+  const double* inv = c.f + c.L.inv;
+  const double* dv = c.f + c.L.dv;
+  const double* x = c.f + c.L.x;
+  const long long nwk = c.L.nw;  // offset of r_c inside K-sized vectors
+  const double* rx = r;
+  const double* rp = r + n;
+  const double* rn = r + n + m;
+  const double* rc = r + nwk;
+  double* ox = out;
+  double* op = out + n;
+  double* on = out + n + m;
+  double* oy = out + nwk;
+  // condensed constraint residual r~_c (restoration folds r_p, r_n in)
+  double* rct = c.f + c.L.rct;  // condensed constraint residual (m)
+  LANE_LOOP(i, m) rct[i] = resto ? rc[i] + rp[i] * ipv[i] - rn[i] * inv[i] : rc[i];
+  __syncwarp();
+  TX* pv = s.v0;  // p_k / p~_k
+  TX* tv = s.v1;
+  TX* gv = s.v2;  // nu entries (nu <= nx)
+  TX* wv = s.v3;
+  // q~_k into pv: r_x(x_k) + sum_r g_r E_r (r_s / D_s + r~_g)
+  auto qtilde = [&](int k) {
+    LANE_LOOP(i, nx) {
+      double v = rx[off_x(d, k) + i];
+      int ci = i - 12 * (i / 12);
+      if (k >= 1 && ci < 3) {
+        const double* xk = x + off_x(d, k);
+        for (int rr = 0; rr < d.ni; ++rr) {
+          IneqRow row = ineq_row(d, c.th, xk, rr);
+          double g = ineq_grad_at(row, i);
+          if (g != 0.0) {
+            int t = (k - 1) * d.ni + rr;
+            v += g * ev[t] * (rx[off_s(d, k) + rr] / dsv[t] + rct[row_ineq(d, k) + rr]);
+          }
+        }
+      }
+      pv[i] = (TX)v;
+    }
+    __syncwarp();
+  };
+  // p~ = p - Y^T L^{-1} D^1/2 p (restoration), in place on pv
+  auto ptransform = [&](int k, const double* D) {
+    const TX* LM = F.LM + (long long)k * nx * nx;
+    const TX* Y = F.Yr + (long long)k * nx * nx;
+    if (lane == 0) {
+      for (int i = 0; i < nx; ++i) {
+        double acc = sqrt(D[i]) * (double)pv[i];
+        for (int t = 0; t < i; ++t) acc -= (double)LM[i * nx + t] * (double)wv[t];
+        wv[i] = (TX)(acc / (double)LM[i * nx + i]);
+      }
+    }
+    __syncwarp();
+    LANE_LOOP(i, nx) {
+      double acc = 0.0;
+      for (int t = 0; t < nx; ++t) acc += (double)Y[t * nx + i] * (double)wv[t];
+      tv[i] = (TX)((double)pv[i] - acc);
+    }
+    __syncwarp();
+    LANE_LOOP(i, nx) pv[i] = tv[i];
+    __syncwarp();
+  };
+
+  // ---- backward sweep
+  qtilde(N);
+  if (resto) ptransform(N, dv + row_dyn(d, N - 1));
+  LANE_LOOP(i, nx) F.ptv[(long long)N * nx + i] = pv[i];
+  __syncwarp();
+  for (int k = N - 1; k >= 0; --k) {
+    const TX* Pt = F.Pt + (long long)(k + 1) * nx * nx;
+    const TB* Ag = c.blk + c.L.A + (long long)k * d.nq * 144;
+    const TB* Bg = c.blk + c.L.B + (long long)k * d.nq * 48;
+    // t = P~_{k+1} d~_k + p~_{k+1},  d~_k = -r~_c(dyn_k)
+    LANE_LOOP(i, nx) {
+      TX acc = pv[i];
+      for (int j = 0; j < nx; ++j) acc += Pt[i * nx + j] * (TX)(-rct[row_dyn(d, k) + j]);
+      tv[i] = acc;
+    }
+    __syncwarp();
+    // g^ = r_u + B^T t
+    LANE_LOOP(a, nu) {
+      int q = a / 4, ca = a - 4 * q;
+      const TB* b = Bg + q * 48 + ca * 12;
+      TX acc = (TX)rx[off_u(d, k) + a];
+      for (int rr = 0; rr < 12; ++rr) acc += (TX)b[rr] * tv[12 * q + rr];
+      gv[a] = acc;
+    }
+    __syncwarp();
+    // k_k = -R^{-1} g^ (lane 0)
+    const TX* Lr = F.Lr + (long long)k * nu * nu;
+    TX* kf = F.kff + (long long)k * nu;
+    if (lane == 0) {
+      double z[32];
+      for (int i = 0; i < nu; ++i) {
+        double acc = (double)gv[i];
+        for (int t = 0; t < i; ++t) acc -= (double)Lr[i * nu + t] * z[t];
+        z[i] = acc / (double)Lr[i * nu + i];
+      }
+      for (int i = nu - 1; i >= 0; --i) {
+        double acc = z[i];
+        for (int t = i + 1; t < nu; ++t) acc -= (double)Lr[t * nu + i] * z[t];
+        z[i] = acc / (double)Lr[i * nu + i];
+      }
+      for (int i = 0; i < nu; ++i) kf[i] = (TX)(-z[i]);
+    }
+    // p_k = q~_k + A^T t + K^T g^
+    const TX* Kg = F.K + (long long)k * nu * nx;
+    LANE_LOOP(i, nx) {
+      int q = i / 12, ci = i - 12 * q;
+      const TB* a = Ag + q * 144 + ci * 12;
+      TX acc = 0;
+      for (int rr = 0; rr < 12; ++rr) acc += (TX)a[rr] * tv[12 * q + rr];
+      for (int aa = 0; aa < nu; ++aa) acc += Kg[aa * nx + i] * gv[aa];
+      wv[i] = acc;
+    }
+    __syncwarp();
+    qtilde(k);
+    LANE_LOOP(i, nx) pv[i] = pv[i] + wv[i];
+    __syncwarp();
+    if (resto) ptransform(k, dv + (k == 0 ? 0 : row_dyn(d, k - 1)));
+    LANE_LOOP(i, nx) F.ptv[(long long)k * nx + i] = pv[i];
+    __syncwarp();
+  }
+
+  // ---- forward sweep; pv = Delta x_k, tv = xi / lambda scratch
+  {
+    const TX* Pt0 = F.Pt;
+    const TX* pt0 = F.ptv;
+    // xi_0 = -r~_c(init); lambda_0 = P~_0 xi_0 + p~_0; dx_0 = xi_0 - D lambda_0
+    LANE_LOOP(i, nx) wv[i] = (TX)(-rct[i]);
+    __syncwarp();
+    LANE_LOOP(i, nx) {
+      TX acc = pt0[i];
+      for (int j = 0; j < nx; ++j) acc += Pt0[i * nx + j] * wv[j];
+      tv[i] = acc;
+    }
+    __syncwarp();
+    LANE_LOOP(i, nx) {
+      double lam = (double)tv[i];
+      double dx0 = (double)wv[i] - (resto ? dv[i] * lam : 0.0);
+      pv[i] = (TX)dx0;
+      ox[i] = dx0;
+      oy[i] = -lam;
+    }
+    __syncwarp();
+  }
+  for (int k = 0; k < N; ++k) {
+    const TB* Ag = c.blk + c.L.A + (long long)k * d.nq * 144;
+    const TB* Bg = c.blk + c.L.B + (long long)k * d.nq * 48;
+    const TX* Kg = F.K + (long long)k * nu * nx;
+    const TX* kf = F.kff + (long long)k * nu;
+    LANE_LOOP(a, nu) {
+      TX acc = kf[a];
+      for (int j = 0; j < nx; ++j) acc += Kg[a * nx + j] * pv[j];
+      gv[a] = acc;
+      ox[off_u(d, k) + a] = (double)acc;
+    }
+    __syncwarp();
+    // xi = A dx + B du + d~
+    LANE_LOOP(i, nx) {
+      int q = i / 12, ri = i - 12 * q;
+      TX acc = (TX)(-rct[row_dyn(d, k) + i]);
+      for (int j = 0; j < 12; ++j) acc += (TX)Ag[q * 144 + j * 12 + ri] * pv[12 * q + j];
+      for (int j = 0; j < 4; ++j) acc += (TX)Bg[q * 48 + j * 12 + ri] * gv[4 * q + j];
+      wv[i] = acc;
+    }
+    __syncwarp();
+    const TX* Pt = F.Pt + (long long)(k + 1) * nx * nx;
+    const TX* ptk = F.ptv + (long long)(k + 1) * nx;
+    LANE_LOOP(i, nx) {
+      TX acc = ptk[i];
+      for (int j = 0; j < nx; ++j) acc += Pt[i * nx + j] * wv[j];
+      tv[i] = acc;
+    }
+    __syncwarp();
+    LANE_LOOP(i, nx) {
+      double lam = (double)tv[i];
+      double dxn = (double)wv[i] - (resto ? dv[row_dyn(d, k) + i] * lam : 0.0);
+      pv[i] = (TX)dxn;
+      ox[off_x(d, k + 1) + i] = dxn;
+      oy[row_dyn(d, k) + i] = -lam;
+    }
+    __syncwarp();
+  }
+  // inequality multipliers and slacks
+  for (int t = lane; t < N * d.ni; t += 32) {
+    int k = 1 + t / d.ni, rr = t - (t / d.ni) * d.ni;
+    IneqRow row = ineq_row(d, c.th, x + off_x(d, k), rr);
+    double gdx = 0.0;
+    const double* dxk = ox + off_x(d, k);
+    for (int comp = 0; comp < row.ncomp; ++comp) {
+      gdx += row.grad[comp] * dxk[12 * row.q0 + comp];
+      if (row.q1 >= 0) gdx += row.grad[3 + comp] * dxk[12 * row.q1 + comp];
+    }
+    double rs = rx[off_s(d, k) + rr];
+    double dyi = ev[t] * (gdx + rs / dsv[t] + rct[row_ineq(d, k) + rr]);
+    oy[row_ineq(d, k) + rr] = dyi;
+    ox[off_s(d, k) + rr] = (dyi - rs) / dsv[t];
+  }
+  if (resto) {
+    __syncwarp();
+    LANE_LOOP(i, m) {
+      op[i] = (oy[i] - rp[i]) * ipv[i];
+      on[i] = (-oy[i] - rn[i]) * inv[i];
+    }
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------- KKT mat-vec (FP64)
+// out = K v for the matrix that `factor` condensed (same dw, same phase),
+// K-sized layout as in `solve`.  Used for iterative refinement.
+template <class TB, class TF>
+__device__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double* out, double dw,
+                           const double* y) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  const int nx = d.nx, nu = d.nu, N = d.N, n = d.n, m = d.m;
+  const long long nwk = c.L.nw;
+  const double* x = c.f + c.L.x;
+  const double* vy = v + nwk;
+  double* oy = out + nwk;
+  const int flags = c.resto ? FF_RESTO : 0;
+  // W-part diagonal terms and dynamics Hessian, and J^T v_y (dynamics)
+  LANE_LOOP(i, c.nw) {
+    double acc = 0.0;
+    int kind = wkind(d, i);
+    acc += (obj_hdiag(c, i, flags) + sigma_of(c, i) + dw) * v[i];
+    (void)kind;
+    out[i] = acc;
+  }
+  __syncwarp();
+  for (int t = lane; t < N * d.nq; t += 32) {
+    int k = t / d.nq, q = t - (t / d.nq) * d.nq;
+    const TB* A = c.blk + c.L.A + ((long long)k * d.nq + q) * 144;
+    const TB* B = c.blk + c.L.B + ((long long)k * d.nq + q) * 48;
+    const TB* H = c.blk + c.L.H + ((long long)k * d.nq + q) * 100;
+    int ox = off_x(d, k) + 12 * q, ou = off_u(d, k) + 4 * q;
+    double vz[10];
+    for (int j = 0; j < 6; ++j) vz[j] = v[ox + 6 + j];
+    for (int j = 0; j < 4; ++j) vz[6 + j] = v[ou + j];
+    const double* yd = vy + row_dyn(d, k) + 12 * q;
+    const double* yp = vy + (k == 0 ? 0 : row_dyn(d, k - 1)) + 12 * q;
+    for (int r = 0; r < 12; ++r) {
+      double acc = yp[r];
+      for (int j = 0; j < 12; ++j) acc -= (double)A[r * 12 + j] * yd[j];
+      if (r >= 6)
+        for (int j = 0; j < 10; ++j) acc += (double)H[j * 10 + (r - 6)] * vz[j];
+      out[ox + r] += acc;
+    }
+    for (int a = 0; a < 4; ++a) {
+      double acc = 0.0;
+      for (int j = 0; j < 12; ++j) acc -= (double)B[a * 12 + j] * yd[j];
+      for (int j = 0; j < 10; ++j) acc += (double)H[j * 10 + 6 + a] * vz[j];
+      out[ou + a] += acc;
+    }
+  }
+  __syncwarp();
+  LANE_LOOP(i, nx) out[off_x(d, N) + i] += vy[row_dyn(d, N - 1) + i];
+  __syncwarp();
+  // inequality Hessian and G^T v_y on positions; -v_y on slacks
+  for (int t = lane; t < N * 3 * d.nq; t += 32) {
+    int k = 1 + t / (3 * d.nq);
+    int pc = t - (t / (3 * d.nq)) * (3 * d.nq);
+    int q = pc / 3, comp = pc - 3 * (pc / 3);
+    int i = 12 * q + comp;
+    const double* xk = x + off_x(d, k);
+    const double* yi = y + row_ineq(d, k);
+    const double* vyi = vy + row_ineq(d, k);
+    const double* vx = v + off_x(d, k);
+    double acc = 0.0;
+    for (int r = 0; r < d.ni; ++r) {
+      IneqRow row = ineq_row(d, c.th, xk, r);
+      double g = ineq_grad_at(row, i);
+      acc += g * vyi[r];
+      for (int jq = 0; jq < d.nq; ++jq)
+        for (int jc = 0; jc < 3; ++jc) {
+          double h = ineq_hess_at(row, i, 12 * jq + jc);
+          if (h != 0.0) acc += yi[r] * h * vx[12 * jq + jc];
+        }
+    }
+    out[off_x(d, k) + i] += acc;
+  }
+  for (int t = lane; t < N * d.ni; t += 32) {
+    int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
+    out[off_s(d, k) + r] -= vy[row_ineq(d, k) + r];
+  }
+  if (c.resto) {
+    LANE_LOOP(i, m) {
+      out[n + i] -= vy[i];
+      out[n + m + i] += vy[i];
+    }
+  }
+  __syncwarp();
+  // constraint part: J v_w (- v_p + v_n in restoration)
+  LANE_LOOP(i, nx) oy[i] = v[i];
+  for (int t = lane; t < N * d.nq; t += 32) {
+    int k = t / d.nq, q = t - (t / d.nq) * d.nq;
+    const TB* A = c.blk + c.L.A + ((long long)k * d.nq + q) * 144;
+    const TB* B = c.blk + c.L.B + ((long long)k * d.nq + q) * 48;
+    const double* vx = v + off_x(d, k) + 12 * q;
+    const double* vu = v + off_u(d, k) + 4 * q;
+    const double* vn = v + off_x(d, k + 1) + 12 * q;
+    for (int r = 0; r < 12; ++r) {
+      double acc = vn[r];
+      for (int j = 0; j < 12; ++j) acc -= (double)A[j * 12 + r] * vx[j];
+      for (int j = 0; j < 4; ++j) acc -= (double)B[j * 12 + r] * vu[j];
+      oy[row_dyn(d, k) + 12 * q + r] = acc;
+    }
+  }
+  for (int t = lane; t < N * d.ni; t += 32) {
+    int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
+    IneqRow row = ineq_row(d, c.th, x + off_x(d, k), r);
+    const double* vx = v + off_x(d, k);
+    double acc = -v[off_s(d, k) + r];
+    for (int comp = 0; comp < row.ncomp; ++comp) {
+      acc += row.grad[comp] * vx[12 * row.q0 + comp];
+      if (row.q1 >= 0) acc += row.grad[3 + comp] * vx[12 * row.q1 + comp];
+    }
+    oy[row_ineq(d, k) + r] = acc;
+  }
+  __syncwarp();
+  if (c.resto) {
+    LANE_LOOP(i, m) oy[i] += -v[n + i] + v[n + m + i];
+  }
+  __syncwarp();
+  (void)nu;
+}
+
+}  // namespace bipm

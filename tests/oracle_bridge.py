@@ -1,0 +1,80 @@
+"""Test helpers that move solver states between the oracle and the library.
+
+Test infrastructure only: it reads oracle states and writes the equivalent
+bipm_iterate record, and builds the comparison vectors of the state-injection
+test (Sec. VI, Eq. 8).
+"""
+
+from __future__ import annotations
+
+import multiprocessing as mp
+
+import numpy as np
+
+from oracle import ipm
+from oracle.quadrotor import QuadNLP
+
+
+def oracle_to_iterate(nlp, st: ipm.SolverState) -> dict:
+    n, m = nlp.n, nlp.m
+    ph = st.normal
+    out = {
+        "mode": st.mode, "status": st.status, "iter": st.iter,
+        "need_init": int(st.need_init), "need_y_ls": int(st.need_y_ls),
+        "tiny": int(ph.tiny), "mu": ph.mu, "dw_last": ph.dw_last,
+        "theta_max": ph.theta_max, "theta_min": ph.theta_min,
+        "filter": np.array(ph.filt, dtype=np.float64).reshape(-1, 2),
+    }
+    if st.mode == ipm.NORMAL:
+        out.update(x=ph.x, y=ph.y, zl=ph.zl, zu=ph.zu)
+    else:
+        r = st.resto
+        out.update(x=r.x[:n], p=r.x[n:n + m], nn=r.x[n + m:], y=r.y,
+                   zl=r.zl[:n], zp=r.zl[n:n + m], zn=r.zl[n + m:], zu=r.zu[:n],
+                   x_ref=st.x_ref, zeta=st.zeta, mu_r=r.mu, dw_last_r=r.dw_last,
+                   theta_max_r=r.theta_max, theta_min_r=r.theta_min, tiny_r=int(r.tiny),
+                   filter_r=np.array(r.filt, dtype=np.float64).reshape(-1, 2),
+                   theta_ref=float(np.sum(np.abs(nlp.c(st.x_ref)))))
+    return out
+
+
+def compare_vector(state: dict) -> np.ndarray:
+    """Quantities compared by e_v: the active iterate and the barrier parameter(s)."""
+    parts = [state["x"], state["y"], state["zl"], state["zu"], [state["mu"]]]
+    if state["mode"] == ipm.RESTO:
+        parts += [state["p"], state["nn"], state["zp"], state["zn"], [state["mu_r"]]]
+    return np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in parts])
+
+
+def e_v(v, v_ref) -> float:
+    """Largest scaled elementwise deviation, Eq. 8."""
+    v = np.asarray(v)
+    v_ref = np.asarray(v_ref)
+    if v.size == 0:
+        return 0.0
+    return float(np.max(np.abs(v - v_ref) / (1.0 + np.abs(v_ref))))
+
+
+def _solve_one(args):
+    desc, theta, record, opt_kw = args
+    nlp = QuadNLP(desc, theta)
+    opt = ipm.Options(**opt_kw)
+    st, hist = ipm.solve(nlp, opt=opt, record=record)
+    res = {
+        "status": st.status, "iter": st.iter, "resto": st.n_resto_iter, "soc": st.n_soc,
+        "ic": st.n_inertia_corr, "x": st.normal.x.copy(), "y": st.normal.y.copy(),
+        "metrics": ipm.final_metrics(nlp, st, opt) if st.status == ipm.CONVERGED else None,
+    }
+    if record:
+        res["history"] = [(oracle_to_iterate(nlp, s), tr) for (s, tr) in hist]
+    return res
+
+
+def oracle_solve_batch(desc, theta, record=False, processes=None, **opt_kw):
+    """Oracle solves of every row of theta, in a spawn process pool."""
+    jobs = [(desc, theta[j], record, opt_kw) for j in range(theta.shape[0])]
+    if processes == 1 or len(jobs) <= 1:
+        return [_solve_one(j) for j in jobs]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=processes or min(len(jobs), mp.cpu_count())) as pool:
+        return pool.map(_solve_one, jobs)

