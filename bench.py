@@ -340,6 +340,9 @@ def desc_theta_len(desc):
 def _oracle_one(args):
     desc, theta = args
     sys.path.insert(0, ROOT)
+    import torch
+
+    torch.set_num_threads(1)
     from oracle import ipm
     from oracle.quadrotor import QuadNLP
     t0 = time.perf_counter()
@@ -347,7 +350,13 @@ def _oracle_one(args):
     return st.status == ipm.CONVERGED, time.perf_counter() - t0
 
 
+def single_thread_env():
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"  # one thread per worker process: cores = processes
+
+
 def oracle_rate(desc, theta, n_problems, processes):
+    single_thread_env()
     ctx = mp.get_context("spawn")
     jobs = [(desc, theta[j]) for j in range(n_problems)]
     with ctx.Pool(processes=processes) as pool:
@@ -374,6 +383,7 @@ def run_reference(args):
         return
     desc, theta = make_batch(WORKLOAD, 64)
     cores = min(os.cpu_count() or 1, 16)
+    single_thread_env()
     ctx = mp.get_context("spawn")
     per_step = cores
     times, convs = [], []

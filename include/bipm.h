@@ -78,6 +78,14 @@ typedef struct {
   double mu_init;     /* initial barrier parameter (0.1) */
   int precision;      /* 0: FP64 factorisation; 1: FP32 factorisation with FP64
                          iterative refinement of the Newton step */
+  int schedule;       /* 0: warp per problem for the first iterations, then a
+                         block per remaining problem; 1: warp per problem only;
+                         2: block per problem only */
+  double fp32_switch; /* precision = 1: an iteration factorises in FP32 only while
+                         the largest barrier diagonal of the condensed system
+                         (input Sigma, slack condensation weight) is at most
+                         this; above it the factorisation is FP64.  0 selects
+                         the default (1e5); negative: always FP64. */
 } bipm_options;
 
 /* Per-slot outcome and counters. */
@@ -99,6 +107,19 @@ typedef struct {
   double primal_inf;    /* max |c| at the final iterate */
   double mu;            /* final barrier parameter */
 } bipm_stats;
+
+/* Per-slot SM clock cycles spent in the phases of the iterations so far
+ * (profile counters): eval, derivatives, factorisation, solve, line search,
+ * other, least-squares multipliers, total.  out holds count x 8 values. */
+int bipm_get_phase_cycles(const bipm_batch* b, long long* out, int first_slot, int count);
+
+/* Outcome of one problem solved through the queue. */
+typedef struct {
+  int status;
+  int iters;
+  double obj;
+  double kkt_err;
+} bipm_result;
 
 /* Complete solver state of one slot (state injection, Sec. VI "Correctness").
  * Vector members point to caller-owned host arrays of the stated length; a
@@ -153,6 +174,17 @@ int bipm_set_initial_guess(bipm_batch* b, const double* x, const double* y, int 
 /* Runs every loaded slot to termination (persistent kernel; a warp that
  * finishes its problem takes the next unfinished one). */
 int bipm_solve(bipm_batch* b);
+
+/* Iteration-level batching (Sec. V "Iteration level batching"): solves the
+ * `n_queue` problems of `theta_queue` (n_queue x n_theta, row-major) through
+ * the batch's slots.  Every resident warp owns one slot; when its problem
+ * terminates it writes that problem's solution (x_out row, n doubles; x_out
+ * may be NULL) and result record, then starts the next problem of the queue
+ * in the same slot.  Problems start in queue order from the default starting
+ * point.  All pointers are device pointers (on_device = 1) or host pointers
+ * (0).  The slots' previous contents are overwritten. */
+int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, double* x_out,
+                     bipm_result* results, int on_device);
 
 /* Runs exactly `n_iterations` iterations on every running slot. */
 int bipm_step(bipm_batch* b, int n_iterations);

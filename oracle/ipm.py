@@ -75,6 +75,7 @@ class Options:
     kappa_resto: float = 0.9
     filter_cap: int = 64
     ls_max_trials: int = 60
+    trace_cond: bool = False  # record the 2-norm condition number of each step's matrix
 
 
 @dataclasses.dataclass
@@ -430,6 +431,8 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
                 return _Outcome.LS_FAILED
         ph.dw_last = dw
     trace["delta_w"] = dw
+    if opt.trace_cond:
+        trace["cond"] = float(np.linalg.cond(fac.K))
 
     def solve(rhs_vec):
         sol = fac.solve(rhs_vec)

@@ -30,7 +30,8 @@ class ProblemDescC(ctypes.Structure):
 
 class OptionsC(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mu_init", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("fp32_switch", ctypes.c_double)]
 
 
 class StatsC(ctypes.Structure):
@@ -44,6 +45,11 @@ class StatsC(ctypes.Structure):
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
+
+
+class ResultC(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("obj", ctypes.c_double),
+                ("kkt_err", ctypes.c_double)]
 
 
 class IterateC(ctypes.Structure):
@@ -61,7 +67,9 @@ class IterateC(ctypes.Structure):
 
 EXPORTS = ["bipm_create_batch", "bipm_dims", "bipm_set_problems", "bipm_set_initial_guess",
            "bipm_solve", "bipm_step", "bipm_get_solution", "bipm_get_stats", "bipm_get_iterate",
-           "bipm_set_iterate", "bipm_last_error", "bipm_destroy"]
+           "bipm_set_iterate", "bipm_get_phase_cycles", "bipm_solve_queue", "bipm_last_error",
+           "bipm_destroy"]
+PHASES = ["eval", "derivs", "factor", "solve", "line_search", "other", "lsq_mult", "total"]
 
 _LIB = None
 
@@ -91,6 +99,8 @@ def load_library(build_if_missing: bool = True):
     lib.bipm_get_stats.argtypes = [vp, ctypes.POINTER(StatsC), i, i]
     lib.bipm_get_iterate.argtypes = [vp, i, ctypes.POINTER(IterateC)]
     lib.bipm_set_iterate.argtypes = [vp, i, ctypes.POINTER(IterateC)]
+    lib.bipm_get_phase_cycles.argtypes = [vp, vp, i, i]
+    lib.bipm_solve_queue.argtypes = [vp, vp, i, vp, vp, i]
     lib.bipm_last_error.restype = ctypes.c_char_p
     lib.bipm_destroy.argtypes = [vp]
     lib.bipm_destroy.restype = None
@@ -131,6 +141,8 @@ class Options:
     max_iter: int = 500
     mu_init: float = 0.1
     precision: int = 0  # 0 FP64 factorisation, 1 FP32 factorisation + FP64 refinement
+    schedule: int = 0   # 0 warp then block teams, 1 warp teams only, 2 block teams only
+    fp32_switch: float = 0.0  # barrier scale above which precision 1 factorises in FP64
 
 
 class Batch:
@@ -140,7 +152,7 @@ class Batch:
         self.lib = load_library()
         d = ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist)
         o = options or Options()
-        oc = OptionsC(o.tol, o.max_iter, o.mu_init, o.precision)
+        oc = OptionsC(o.tol, o.max_iter, o.mu_init, o.precision, o.schedule, o.fp32_switch)
         h = ctypes.c_void_p()
         sp = None
         if stream is not None:
@@ -187,6 +199,25 @@ class Batch:
     def solve(self):
         _check(self.lib.bipm_solve(self.h))
 
+    def solve_queue(self, theta_queue, x_out=None, results=None):
+        """Iteration-level batching over a queue of problems (rows of theta_queue).
+
+        theta_queue / x_out are numpy arrays (host) or CUDA tensors (device);
+        `results` (device mode) is a CUDA int8/uint8 tensor of n_queue * 24 bytes.
+        Returns a dict of numpy arrays (status, iters, obj, kkt_err) in host mode.
+        """
+        nq = theta_queue.shape[0]
+        pt, dev = _ptr(theta_queue)
+        px, _ = _ptr(x_out)
+        if dev:
+            if results is None:
+                raise ValueError("device mode needs a results buffer")
+            _check(self.lib.bipm_solve_queue(self.h, pt, nq, px, ctypes.c_void_p(results.data_ptr()), 1))
+            return None
+        arr = (ResultC * max(nq, 1))()
+        _check(self.lib.bipm_solve_queue(self.h, pt, nq, px, arr, 0))
+        return {f: np.array([getattr(arr[j], f) for j in range(nq)]) for f, _ in ResultC._fields_}
+
     def step(self, n_iterations: int = 1):
         _check(self.lib.bipm_step(self.h, n_iterations))
 
@@ -212,6 +243,14 @@ class Batch:
         _check(self.lib.bipm_get_stats(self.h, arr, first_slot, count))
         fields = [f for f, _ in StatsC._fields_]
         return {f: np.array([getattr(arr[i], f) for i in range(count)]) for f in fields}
+
+    def get_phase_cycles(self, first_slot: int = 0, count: int | None = None):
+        """Per-slot SM cycles per phase (columns: PHASES)."""
+        count = self.capacity - first_slot if count is None else count
+        out = np.zeros((max(count, 1), 8), dtype=np.int64)
+        _check(self.lib.bipm_get_phase_cycles(self.h, out.ctypes.data_as(ctypes.c_void_p),
+                                              first_slot, count))
+        return out[:count]
 
     def get_iterate(self, slot: int) -> dict:
         n, m = self.n, self.m

@@ -50,6 +50,8 @@ struct bipm_batch {
   size_t stage_bytes = 0;
   int smem_per_warp = 0;
   int blocks = 0;
+  int block_blocks = 0;
+  int schedule = 0;
   int loaded = 0;
 };
 
@@ -66,6 +68,8 @@ __global__ void gather_kernel(const Params* __restrict__ P, int first, int count
 // ------------------------------------------------------------- host helpers
 void* iter_kernel_ptr(int precision) { return precision ? iter_kernel_f32() : iter_kernel_f64(); }
 void* init_kernel_ptr(int precision) { return precision ? init_kernel_f32() : init_kernel_f64(); }
+void* block_kernel_ptr(int precision) { return precision ? block_kernel_f32() : block_kernel_f64(); }
+void* queue_kernel_ptr(int precision) { return precision ? queue_kernel_f32() : queue_kernel_f64(); }
 
 Layout make_layout(const Dims& d, int precision) {
   Layout L;
@@ -91,6 +95,8 @@ Layout make_layout(const Dims& d, int precision) {
   L.jty = take(L.nw);
   L.gphi = take(L.nw);
   L.xr = take(n);
+  L.xref = take((N + 1) * nx);
+  L.sig = take(L.nw);
   L.dsv = take(N * d.ni);
   L.ev = take(N * d.ni);
   L.ipv = take(m);
@@ -121,6 +127,8 @@ Layout make_layout(const Dims& d, int precision) {
   L.ptv = ftake((N + 1) * nx);
   L.fac_size = fo;
   L.f64_fac = precision ? take(L.fac_size) : 0;
+  L.gscr = take((scratch_bytes(d.nq, d.nx, d.nu, 8) + 7) / 8);
+  L.gmv = precision ? take((kGmresM + 1) * L.nk) : 0;
   L.slot_f64 = o;
   long long bo = 0;
   L.A = bo;
@@ -154,11 +162,24 @@ int ensure_stage(bipm_batch* b, size_t bytes) {
 
 int run_iterations(bipm_batch* b, int n_iter) {
   if (!b->loaded) return fail(BIPM_ESTATE, "no problems loaded");
-  CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
-  void* args[] = {&b->dparams, &n_iter};
-  CUDA_TRY(cudaLaunchKernel(iter_kernel_ptr(b->opt.precision), dim3(b->blocks),
-                            dim3(32 * kWarpsPerBlock), args,
-                            (size_t)b->smem_per_warp * kWarpsPerBlock, b->stream));
+  // warp teams: every problem (at most kBulkVisit iterations in solve mode
+  // when block teams take over the remainder)
+  if (b->schedule != 2) {
+    int cap = (n_iter > 0 || b->schedule == 1) ? 0 : kBulkVisit;
+    CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
+    void* args[] = {&b->dparams, &n_iter, &cap};
+    CUDA_TRY(cudaLaunchKernel(iter_kernel_ptr(b->opt.precision), dim3(b->blocks),
+                              dim3(32 * kWarpsPerBlock), args,
+                              (size_t)b->smem_per_warp * kWarpsPerBlock, b->stream));
+  }
+  if (b->schedule == 2 || (n_iter <= 0 && b->schedule == 0)) {
+    // block teams: the long-running remainder, to termination
+    CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
+    void* args2[] = {&b->dparams, &n_iter};
+    CUDA_TRY(cudaLaunchKernel(block_kernel_ptr(b->opt.precision), dim3(b->block_blocks),
+                              dim3(kBlockTeam), args2, (size_t)b->smem_per_warp + 128,
+                              b->stream));
+  }
   CUDA_TRY(cudaStreamSynchronize(b->stream));
   return 0;
 }
@@ -181,8 +202,10 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
     return fail(BIPM_EINVAL, "obstacle counts must be 0..256");
   if (!(desc->pair_dist >= 0.0)) return fail(BIPM_EINVAL, "pair_dist must be >= 0");
   if (capacity < 0) return fail(BIPM_EINVAL, "capacity must be >= 0");
-  bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0};
-  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || (o.precision != 0 && o.precision != 1))
+  bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0, 0, 0.0};
+  if (o.fp32_switch == 0.0) o.fp32_switch = kFp32BarrierMax;
+  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || (o.precision != 0 && o.precision != 1) ||
+      o.schedule < 0 || o.schedule > 2)
     return fail(BIPM_EINVAL, "bad options");
 
   bipm_batch* b = new bipm_batch();
@@ -209,10 +232,19 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
   b->opt.max_iter = o.max_iter;
   b->opt.mu_init = o.mu_init;
   b->opt.precision = o.precision;
+  b->opt.fp32_switch = o.fp32_switch;
+  b->schedule = o.schedule;
   b->capacity = capacity;
   b->stream = (cudaStream_t)cuda_stream;
   b->L = make_layout(d, o.precision);
-  b->smem_per_warp = (int)scratch_bytes(d.nq, d.nx, d.nu);
+  // shared-memory scratch per warp: the factorisation precision's scratch when
+  // it fits in 24 KB, otherwise none (the slot's global scratch is used)
+  {
+    size_t need = scratch_bytes(d.nq, d.nx, d.nu, o.precision ? 4 : 8);
+    size_t need64 = scratch_bytes(d.nq, d.nx, d.nu, 8);
+    size_t cap_b = 24 * 1024;
+    b->smem_per_warp = (int)(need64 <= cap_b ? need64 : (need <= cap_b ? need : 128));
+  }
 
   auto cleanup = [&](int code, const std::string& msg) {
     bipm_destroy(b);
@@ -260,7 +292,9 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
   void* kfn = iter_kernel_ptr(o.precision);
   size_t smem = (size_t)b->smem_per_warp * kWarpsPerBlock;
   if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(queue_kernel_ptr(o.precision), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
       return cleanup(BIPM_ECUDA, "shared memory attribute");
   }
   int dev = 0, sms = 0, per_sm = 0;
@@ -272,6 +306,18 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
     return cleanup(BIPM_ECUDA, "kernel does not fit on an SM (shared memory " + std::to_string(smem) + " B)");
   int need = (int)((cap + kWarpsPerBlock - 1) / kWarpsPerBlock);
   b->blocks = std::max(1, std::min(need, sms * per_sm));
+  {
+    void* bfn = block_kernel_ptr(o.precision);
+    size_t bsm = (size_t)b->smem_per_warp + 128;
+    if (bsm > 48 * 1024 &&
+        cudaFuncSetAttribute(bfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm) != cudaSuccess)
+      return cleanup(BIPM_ECUDA, "shared memory attribute (block kernel)");
+    int per_sm_b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, bfn, kBlockTeam, bsm) != cudaSuccess ||
+        per_sm_b < 1)
+      return cleanup(BIPM_ECUDA, "block kernel does not fit on an SM");
+    b->block_blocks = std::max(1, std::min((int)cap, sms * per_sm_b));
+  }
   *out = b;
   g_err.clear();
   return 0;
@@ -337,6 +383,45 @@ int bipm_solve(bipm_batch* b) {
   return run_iterations(b, 0);
 }
 
+int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, double* x_out,
+                     bipm_result* results, int on_device) {
+  if (!b) return fail(BIPM_EINVAL, "null batch");
+  if (n_queue < 0) return fail(BIPM_EINVAL, "n_queue must be >= 0");
+  if (n_queue == 0) return 0;
+  if (!theta_queue || !results) return fail(BIPM_EINVAL, "null theta_queue or results");
+  if (b->capacity == 0) return fail(BIPM_ESTATE, "batch has no slots");
+  const Dims& d = b->d;
+  size_t tb = (size_t)n_queue * d.n_theta * sizeof(double);
+  size_t xb = x_out ? (size_t)n_queue * d.n * sizeof(double) : 0;
+  size_t rb = (size_t)n_queue * sizeof(bipm_result);
+  const double* th_dev = theta_queue;
+  double* x_dev = x_out;
+  bipm_result* r_dev = results;
+  int rc;
+  if (!on_device) {
+    if ((rc = ensure_stage(b, tb + xb + rb + 256))) return rc;
+    char* base = (char*)b->stage;
+    th_dev = (const double*)base;
+    x_dev = x_out ? (double*)(base + tb) : nullptr;
+    r_dev = (bipm_result*)(base + ((tb + xb + 15) & ~(size_t)15));
+    CUDA_TRY(cudaMemcpyAsync((void*)th_dev, theta_queue, tb, cudaMemcpyHostToDevice, b->stream));
+  }
+  // one slot per resident warp
+  int warps = std::min(b->capacity, b->blocks * kWarpsPerBlock);
+  int blocks = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
+  void* args[] = {&b->dparams, &th_dev, &n_queue, &warps, &x_dev, &r_dev};
+  CUDA_TRY(cudaLaunchKernel(queue_kernel_ptr(b->opt.precision), dim3(blocks), dim3(32 * kWarpsPerBlock),
+                            args, (size_t)b->smem_per_warp * kWarpsPerBlock, b->stream));
+  if (!on_device) {
+    if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, x_dev, xb, cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaMemcpyAsync(results, r_dev, rb, cudaMemcpyDeviceToHost, b->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  b->loaded = 1;
+  return 0;
+}
+
 int bipm_step(bipm_batch* b, int n_iterations) {
   if (!b) return fail(BIPM_EINVAL, "null batch");
   if (n_iterations < 1) return fail(BIPM_EINVAL, "n_iterations must be >= 1");
@@ -398,6 +483,20 @@ int bipm_get_stats(const bipm_batch* b, bipm_stats* out, int first_slot, int cou
     o.primal_inf = s.inf;
     o.mu = s.mu;
   }
+  return 0;
+}
+
+int bipm_get_phase_cycles(const bipm_batch* b, long long* out, int first_slot, int count) {
+  int rc = check_slots(b, first_slot, count);
+  if (rc) return rc;
+  if (count == 0) return 0;
+  if (!out) return fail(BIPM_EINVAL, "null output");
+  std::vector<SlotState> h(count);
+  CUDA_TRY(cudaMemcpyAsync(h.data(), b->st + first_slot, count * sizeof(SlotState),
+                           cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < count; ++i)
+    for (int p = 0; p < 8; ++p) out[(size_t)i * 8 + p] = h[i].cyc[p];
   return 0;
 }
 

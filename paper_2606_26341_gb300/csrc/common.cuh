@@ -28,12 +28,63 @@ __device__ __forceinline__ double warp_min(double v) {
 }
 __device__ __forceinline__ int warp_or(int v) { return __any_sync(0xffffffffu, v); }
 
+// Team primitives.  A team is either one warp (T = 32; several teams share a
+// block) or a whole block (T = blockDim.x; one team per block).  `c` is any
+// context with members lane (thread index in the team), T and red (a shared
+// buffer of at least T/32 doubles, block teams only).
+template <class C>
+__device__ __forceinline__ void team_sync(const C& c) {
+  if (c.T == 32)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+template <class C, class Op>
+__device__ __forceinline__ double team_reduce(const C& c, double v, Op op) {
+  if (c.T == 32) return v;
+  __syncthreads();
+  if ((c.lane & 31) == 0) c.red[c.lane >> 5] = v;
+  __syncthreads();
+  double r = c.red[0];
+  for (int i = 1; i < (c.T >> 5); ++i) r = op(r, c.red[i]);
+  return r;
+}
+struct OpSum { __device__ double operator()(double a, double b) const { return a + b; } };
+struct OpMax { __device__ double operator()(double a, double b) const { return fmax(a, b); } };
+struct OpMin { __device__ double operator()(double a, double b) const { return fmin(a, b); } };
+template <class C>
+__device__ __forceinline__ double team_sum(const C& c, double v) {
+  return team_reduce(c, warp_sum(v), OpSum());
+}
+template <class C>
+__device__ __forceinline__ double team_max(const C& c, double v) {
+  return team_reduce(c, warp_max(v), OpMax());
+}
+template <class C>
+__device__ __forceinline__ double team_min(const C& c, double v) {
+  return team_reduce(c, warp_min(v), OpMin());
+}
+template <class C>
+__device__ __forceinline__ int team_or(const C& c, int v) {
+  return team_reduce(c, warp_or(v) ? 1.0 : 0.0, OpMax()) != 0.0;
+}
+// value of thread 0 of the team, for every thread
+template <class C>
+__device__ __forceinline__ int team_bcast0(const C& c, int v) {
+  if (c.T == 32) return __shfl_sync(0xffffffffu, v, 0);
+  __syncthreads();
+  if (c.lane == 0) c.red[0] = (double)v;
+  __syncthreads();
+  return (int)c.red[0];
+}
+
 // ---------------------------------------------------------- algorithm options
 struct Options {
   double tol;
   int max_iter;
   double mu_init;
   int precision;  // 0 = FP64 factorisation, 1 = FP32 factorisation + FP64 refinement
+  double fp32_switch;  // barrier scale above which precision 1 factorises in FP64
 };
 
 // IPOPT constants (Wachter & Biegler 2006 defaults)
@@ -51,9 +102,23 @@ constexpr int kFilterCap = 64;
 constexpr int kLsMaxTrials = 60;
 constexpr int kIrMaxSteps = 10;
 constexpr double kIrTol = 1e-10;
+constexpr int kGmresM = 6;        // Krylov dimension per restart
+constexpr double kFp32BarrierMax = 1e5;  // above: factorise in FP64 this iteration
+constexpr int kGmresRestarts = 3;
 constexpr double kEpsMach = 2.220446049250313e-16;
 
 enum Mode : int { MODE_NORMAL = 0, MODE_RESTO = 1 };
+// phases of one iteration timed with the SM clock (per-slot profile counters)
+enum Phase : int {
+  PH_EVAL = 0,    // c, f, grad f, J^T y at the iterate
+  PH_DERIV = 1,   // Jacobian and Hessian blocks
+  PH_FACTOR = 2,  // factorisations incl. inertia correction
+  PH_SOLVE = 3,   // solves incl. refinement (main step)
+  PH_LS = 4,      // line search: trial points, SOC solves, acceptance
+  PH_MISC = 5,    // barrier terms, error norms, mu update, restoration bookkeeping
+  PH_LSQ = 6,     // least-squares multipliers
+  PH_TOTAL = 7
+};
 enum VarKind : int { VK_FREE = 0, VK_BOX = 1, VK_LOWER = 2 };
 
 // ------------------------------------------------------------ problem layout
@@ -100,11 +165,13 @@ __device__ __forceinline__ int var_kind(const Dims& d, int i) {
 struct Layout {
   long long nw, nk;
   // FP64 arrays
-  long long x, zl, zu, y, xt, c, ct, csoc, gf, jty, gphi, xr;
+  long long x, zl, zu, y, xt, c, ct, csoc, gf, jty, gphi, xr, xref, sig;
   long long dsv, ev, ipv, inv, dv;  // condensation diagonals (slacks / rows)
   long long rhs, sol, rhs2, sol2, res, corr, rct;
   long long filt, filt_r;
   long long f64_fac;  // FP64 factor arrays (mixed precision: escalation and LS)
+  long long gscr;     // factorisation scratch in global memory (large problems)
+  long long gmv;      // GMRES basis (kGmresM + 1 K-sized vectors, mixed precision)
   long long slot_f64;
   // derivative blocks (block type) and factor arrays (factor type), per slot
   long long A, B, H;
@@ -117,6 +184,7 @@ struct SlotState {
   int status, mode, iter, need_init, need_y_ls, tiny, tiny_r, n_filt, n_filt_r;
   int n_soc, n_resto_iter, n_inertia_corr, n_ir_steps, n_escalations, n_tiny, problem_id;
   int n_fact, n_solve, n_trial, pad_;
+  long long cyc[8];  // clock cycles per phase (see kPhase*)
   double mu, dw_last, theta_max, theta_min;
   double mu_r, dw_last_r, theta_max_r, theta_min_r, zeta, theta_ref;
   double obj, kkt, inf, last_alpha;

@@ -22,7 +22,7 @@
 
 namespace bipm {
 
-#define LANE_LOOP(i, n) for (int i = lane; i < (n); i += 32)
+#define LANE_LOOP(i, n) for (int i = lane; i < (n); i += c.T)
 
 template <class T>
 struct Fac {  // factor arrays of one slot in precision T
@@ -49,7 +49,9 @@ struct Ctx {
   const Params* P;
   Dims d;
   Layout L;
-  int lane;
+  int lane;            // thread index within the team
+  int T;               // team size: 32 (warp) or the block size
+  double* red;         // shared reduction buffer (block teams)
   int slot;
   double* f;           // this slot's FP64 arrays
   TB* blk;             // derivative blocks
@@ -57,6 +59,8 @@ struct Ctx {
   Fac<double> fac64;   // FP64 factor arrays (= fac when TF is double)
   const double* th;    // theta of this slot
   char* smem;          // per-warp shared scratch
+  char* gscratch;      // per-slot global scratch (used when shared memory is too small)
+  int smem_bytes;      // bytes of `smem`
   // phase data of the current iteration
   int resto;
   int nw;              // primal length of the current phase (n or n + 2m)
@@ -104,9 +108,9 @@ __device__ __forceinline__ bool has_lower(int kind) { return kind != VK_FREE; }
 __device__ __forceinline__ bool has_upper(int kind) { return kind == VK_BOX; }
 
 // ------------------------------------------------------ reference trajectory
-__device__ __forceinline__ double ref_comp(const double* th, const Dims& d, int k, int q, int j) {
-  // reference state component j of quad q at stage k: circle position and
-  // velocity, zero attitude and body rates
+// reference state component j of quad q at stage k: circle position and
+// velocity, zero attitude and body rates (evaluated once per problem)
+__device__ __forceinline__ double ref_value(const double* th, const Dims& d, int k, int q, int j) {
   if (j >= 6) return 0.0;
   const double* r = th + d.th_ref + 6 * q;
   double t = k * d.dt;
@@ -203,11 +207,12 @@ __device__ __forceinline__ double ineq_hess_at(const IneqRow& r, int i, int j) {
 // ---------------------------------------------------------------- evaluation
 // Constraint values c(x) (original problem) into cout and the objective f(x).
 template <class TB, class TF>
-__device__ double eval_values(Ctx<TB, TF>& c, const double* x, double* cout) {
+__device__ __noinline__ double eval_values(Ctx<TB, TF>& c, const double* x, double* cout,
+                              bool dynamics = true) {
   const Dims& d = c.d;
   const int lane = c.lane;
   LANE_LOOP(i, d.nx) cout[i] = x[i] - c.th[d.th_x + i];
-  for (int t = lane; t < d.N * d.nq; t += 32) {
+  for (int t = lane; t < (dynamics ? d.N * d.nq : 0); t += c.T) {
     int k = t / d.nq, q = t - (t / d.nq) * d.nq;
     double xx[12], uu[4], F[12];
     const double* xk = x + off_x(d, k) + 12 * q;
@@ -222,30 +227,31 @@ __device__ double eval_values(Ctx<TB, TF>& c, const double* x, double* cout) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) cr[i] = xn[i] - F[i];
   }
-  for (int t = lane; t < d.N * d.ni; t += 32) {
+  for (int t = lane; t < d.N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, j = t - (t / d.ni) * d.ni;
     IneqRow r = ineq_row(d, c.th, x + off_x(d, k), j);
     cout[row_ineq(d, k) + j] = r.gval - x[off_s(d, k) + j];
   }
   double fs = 0.0;
-  for (int t = lane; t < (d.N + 1) * d.nx; t += 32) {
+  for (int t = lane; t < (d.N + 1) * d.nx; t += c.T) {
     int k = t / d.nx, i = t - (t / d.nx) * d.nx;
     int q = i / 12, j = i - 12 * (i / 12);
-    double e = x[off_x(d, k) + i] - ref_comp(c.th, d, k, q, j);
+    double e = x[off_x(d, k) + i] - c.f[c.L.xref + k * d.nx + i];
+    (void)q;
     fs += cost_weight(d, k, j) * e * e;
   }
-  for (int t = lane; t < d.N * d.nu; t += 32) {
+  for (int t = lane; t < d.N * d.nu; t += c.T) {
     int k = t / d.nu, i = t - (t / d.nu) * d.nu;
     double e = x[off_u(d, k) + i] - kHover;
     fs += kRweight * e * e;
   }
-  __syncwarp();
-  return warp_sum(fs);
+  team_sync(c);
+  return team_sum(c, fs);
 }
 
 // Gradient of the objective of the current phase into g (W-sized).
 template <class TB, class TF>
-__device__ void eval_grad(Ctx<TB, TF>& c, const double* x, double* g) {
+__device__ __noinline__ void eval_grad(Ctx<TB, TF>& c, const double* x, double* g) {
   const Dims& d = c.d;
   const int lane = c.lane;
   const double* xr = c.f + c.L.xr;
@@ -260,7 +266,8 @@ __device__ void eval_grad(Ctx<TB, TF>& c, const double* x, double* g) {
       VarInfo vi = var_info(d, i);
       if (vi.loc < d.nx) {
         int q = vi.loc / 12, j = vi.loc - 12 * (vi.loc / 12);
-        v = 2.0 * cost_weight(d, vi.k, j) * (x[i] - ref_comp(c.th, d, vi.k, q, j));
+        v = 2.0 * cost_weight(d, vi.k, j) * (x[i] - c.f[c.L.xref + vi.k * d.nx + vi.loc]);
+        (void)q;
       } else if (vi.kind == VK_BOX) {
         v = 2.0 * kRweight * (x[i] - kHover);
       } else {
@@ -269,12 +276,12 @@ __device__ void eval_grad(Ctx<TB, TF>& c, const double* x, double* g) {
     }
     g[i] = v;
   }
-  __syncwarp();
+  team_sync(c);
 }
 
 // Objective of the restoration problem: rho sum(p + n) + zeta/2 |D_R (x - x_R)|^2.
 template <class TB, class TF>
-__device__ double resto_objective(Ctx<TB, TF>& c, const double* w) {
+__device__ __noinline__ double resto_objective(Ctx<TB, TF>& c, const double* w) {
   const Dims& d = c.d;
   const int lane = c.lane;
   const double* xr = c.f + c.L.xr;
@@ -287,7 +294,7 @@ __device__ double resto_objective(Ctx<TB, TF>& c, const double* w) {
       acc += 0.5 * c.zeta * sq(dr * (w[i] - xr[i]));
     }
   }
-  return warp_sum(acc);
+  return team_sum(c, acc);
 }
 
 // Jacobian / Hessian blocks of the dynamics by forward-over-reverse dual
@@ -296,12 +303,12 @@ __device__ double resto_objective(Ctx<TB, TF>& c, const double* w) {
 // and the Hessian of lam^T F vanishes in those rows, so only ten directions
 // carry derivatives.  lam = -y_dyn (the Lagrangian term is +y^T (x_{k+1} - F)).
 template <class TB, class TF>
-__device__ void eval_blocks(Ctx<TB, TF>& c, const double* x, const double* y, bool hess) {
+__device__ __noinline__ void eval_blocks(Ctx<TB, TF>& c, const double* x, const double* y, bool hess) {
   const Dims& d = c.d;
   const int lane = c.lane;
   typedef Dual<TB> DT;
   const int ntask = d.N * d.nq * 10;
-  for (int t = lane; t < ntask; t += 32) {
+  for (int t = lane; t < ntask; t += c.T) {
     int j = t - (t / 10) * 10;
     int kq = t / 10;
     int k = kq / d.nq, q = kq - (kq / d.nq) * d.nq;
@@ -345,16 +352,17 @@ __device__ void eval_blocks(Ctx<TB, TF>& c, const double* x, const double* y, bo
         }
     }
   }
-  __syncwarp();
+  team_sync(c);
 }
 
 // J^T y of the original constraints (x-part, n entries) in FP64, plus the
 // elastic parts (-y, +y) in restoration.
 template <class TB, class TF>
-__device__ void eval_jty(Ctx<TB, TF>& c, const double* x, const double* y, double* jty) {
+__device__ __noinline__ void eval_jty(Ctx<TB, TF>& c, const double* x, const double* y, double* jty,
+                         double* cout = nullptr) {
   const Dims& d = c.d;
   const int lane = c.lane;
-  for (int t = lane; t < d.N * d.nq; t += 32) {
+  for (int t = lane; t < d.N * d.nq; t += c.T) {
     int k = t / d.nq, q = t - (t / d.nq) * d.nq;
     double xx[12], uu[4], F[12], gx[12], gu[4], lam[12];
     const double* xk = x + off_x(d, k) + 12 * q;
@@ -367,6 +375,12 @@ __device__ void eval_jty(Ctx<TB, TF>& c, const double* x, const double* y, doubl
 #pragma unroll
     for (int i = 0; i < 4; ++i) uu[i] = uk[i];
     rk4_fwd_rev<double>(xx, uu, d.dt, lam, F, gx, gu);
+    if (cout) {
+      const double* xn = x + off_x(d, k + 1) + 12 * q;
+      double* cr = cout + row_dyn(d, k) + 12 * q;
+#pragma unroll
+      for (int i = 0; i < 12; ++i) cr[i] = xn[i] - F[i];
+    }
     const double* yprev = y + (k == 0 ? 0 : row_dyn(d, k - 1)) + 12 * q;
     double* jx = jty + off_x(d, k) + 12 * q;
 #pragma unroll
@@ -376,9 +390,9 @@ __device__ void eval_jty(Ctx<TB, TF>& c, const double* x, const double* y, doubl
     for (int i = 0; i < 4; ++i) ju[i] = gu[i];
   }
   LANE_LOOP(i, d.nx) jty[off_x(d, d.N) + i] = y[row_dyn(d, d.N - 1) + i];
-  __syncwarp();
+  team_sync(c);
   // inequality rows: + G_k^T y_ineq on the positions, - y_ineq on the slacks
-  for (int t = lane; t < d.N * 3 * d.nq; t += 32) {
+  for (int t = lane; t < d.N * 3 * d.nq; t += c.T) {
     int k = 1 + t / (3 * d.nq);
     int pc = t - (t / (3 * d.nq)) * (3 * d.nq);
     int q = pc / 3, comp = pc - 3 * (pc / 3);
@@ -392,7 +406,7 @@ __device__ void eval_jty(Ctx<TB, TF>& c, const double* x, const double* y, doubl
     }
     jty[off_x(d, k) + i] += acc;
   }
-  for (int t = lane; t < d.N * d.ni; t += 32) {
+  for (int t = lane; t < d.N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
     jty[off_s(d, k) + r] = -y[row_ineq(d, k) + r];
   }
@@ -402,21 +416,31 @@ __device__ void eval_jty(Ctx<TB, TF>& c, const double* x, const double* y, doubl
       jty[d.n + d.m + i] = y[i];
     }
   }
-  __syncwarp();
+  team_sync(c);
 }
 
 // ------------------------------------------------- barrier quantities (FP64)
-// Sigma_i = z_L/s_L + z_U/s_U of W-entry i.
+// Sigma_i = z_L/s_L + z_U/s_U of W-entry i, from the array fill_sigma wrote
+// for the current iterate.
 template <class TB, class TF>
 __device__ __forceinline__ double sigma_of(Ctx<TB, TF>& c, int i) {
-  int kind = wkind(c.d, i);
-  if (kind == VK_FREE) return 0.0;
+  return c.f[c.L.sig + i];
+}
+
+template <class TB, class TF>
+__device__ __noinline__ void fill_sigma(Ctx<TB, TF>& c) {
   const double* x = c.f + c.L.x;
   const double* zl = c.f + c.L.zl;
   const double* zu = c.f + c.L.zu;
-  double s = zl[i] / x[i];
-  if (kind == VK_BOX) s += zu[i] / (kUmax - x[i]);
-  return s;
+  double* sg = c.f + c.L.sig;
+  for (int i = c.lane; i < c.nw; i += c.T) {
+    int kind = wkind(c.d, i);
+    double v = 0.0;
+    if (kind != VK_FREE) v = zl[i] / x[i];
+    if (kind == VK_BOX) v += zu[i] / (kUmax - x[i]);
+    sg[i] = v;
+  }
+  team_sync(c);
 }
 
 // Diagonal Hessian of the objective on W-entry i (cost weights, or zeta D_R^2
@@ -441,7 +465,7 @@ __device__ __forceinline__ double obj_hdiag(Ctx<TB, TF>& c, int i, int flags) {
 //   slack (k, r):  D_s = H_ss + Sigma_s + dw,  E = D_s / (1 + D_s D_g)
 //   row i (restoration): 1/(Sigma_p + dw), 1/(Sigma_n + dw), D = their sum
 template <class TB, class TF>
-__device__ void compute_diag(Ctx<TB, TF>& c, double dw, int flags) {
+__device__ __noinline__ void compute_diag(Ctx<TB, TF>& c, double dw, int flags) {
   const Dims& d = c.d;
   const int lane = c.lane;
   double* dsv = c.f + c.L.dsv;
@@ -464,8 +488,8 @@ __device__ void compute_diag(Ctx<TB, TF>& c, double dw, int flags) {
       dv[i] = 0.0;
     }
   }
-  __syncwarp();
-  for (int t = lane; t < d.N * d.ni; t += 32) {
+  team_sync(c);
+  for (int t = lane; t < d.N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
     int vi = off_s(d, k) + r;
     double ds = (flags & FF_IDENT) ? 1.0 : obj_hdiag(c, vi, flags) + sigma_of(c, vi) + dw;
@@ -473,7 +497,7 @@ __device__ void compute_diag(Ctx<TB, TF>& c, double dw, int flags) {
     dsv[t] = ds;
     ev[t] = ds / (1.0 + ds * dg);
   }
-  __syncwarp();
+  team_sync(c);
 }
 
 // -------------------------------------------------------- factorisation
@@ -509,17 +533,26 @@ __device__ __forceinline__ Scratch<TX> scratch(char* smem, const Dims& d) {
   return s;
 }
 
-// bytes of per-warp scratch for problems of dims d (FP64 worst case)
-__host__ __device__ inline size_t scratch_bytes(int nq, int nx, int nu) {
+// bytes of factorisation scratch for problems of dims d with elements of
+// `elem` bytes (the FP64 Cholesky block is always double)
+__host__ __device__ inline size_t scratch_bytes(int nq, int nx, int nu, int elem) {
   size_t e = (size_t)2 * nx * nx + 3 * (size_t)nx * nu + (size_t)nu * nu + 192 * (size_t)nq +
              4 * (size_t)nx;
-  size_t b = ((e * 8 + 15) & ~(size_t)15) + (size_t)nu * nu * 8;
+  size_t b = ((e * elem + 15) & ~(size_t)15) + (size_t)nu * nu * 8;
   return (b + 127) & ~(size_t)127;
+}
+
+// shared memory when the scratch of precision TX fits, else the slot's
+// global scratch region
+template <class TX, class TB, class TF>
+__device__ __forceinline__ char* scratch_base(const Ctx<TB, TF>& c) {
+  return scratch_bytes(c.d.nq, c.d.nx, c.d.nu, (int)sizeof(TX)) <= (size_t)c.smem_bytes ? c.smem
+                                                                                        : c.gscratch;
 }
 
 // Q~_k (state block, written to Pb as TX), including the inequality terms.
 template <class TB, class TF, class TX>
-__device__ void add_state_block(Ctx<TB, TF>& c, int k, TX* Q, double dw, int flags,
+__device__ __noinline__ void add_state_block(Ctx<TB, TF>& c, int k, TX* Q, double dw, int flags,
                                 const double* y, bool accumulate) {
   const Dims& d = c.d;
   const int lane = c.lane;
@@ -529,54 +562,53 @@ __device__ void add_state_block(Ctx<TB, TF>& c, int k, TX* Q, double dw, int fla
   const bool ident = flags & FF_IDENT;
   LANE_LOOP(e, nx * nx) {
     int i = e / nx, j = e - (e / nx) * nx;
-    double v = 0.0;
-    if (i == j) v += obj_hdiag(c, off_x(d, k) + i, flags) + (ident ? 0.0 : dw);
+    TX v = accumulate ? Q[e] : (TX)0;
+    if (i == j) v += (TX)(obj_hdiag(c, off_x(d, k) + i, flags) + (ident ? 0.0 : dw));
     int qi = i / 12, qj = j / 12;
     int ci = i - 12 * qi, cj = j - 12 * qj;
     if (!ident && k < d.N && qi == qj && ci >= 6 && cj >= 6) {
       const TB* H = c.blk + c.L.H + ((long long)k * d.nq + qi) * 100;
-      v += (double)H[(cj - 6) * 10 + (ci - 6)];
+      v += (TX)H[(cj - 6) * 10 + (ci - 6)];
     }
     if (k >= 1 && ci < 3 && cj < 3) {
       const double* xk = x + off_x(d, k);
       const double* yi = y + row_ineq(d, k);
       for (int r = 0; r < d.ni; ++r) {
         IneqRow row = ineq_row(d, c.th, xk, r);
-        double gi = ineq_grad_at(row, i), gj = ineq_grad_at(row, j);
-        v += ev[(k - 1) * d.ni + r] * gi * gj;
-        if (!ident) v += yi[r] * ineq_hess_at(row, i, j);
+        TX gi = (TX)ineq_grad_at(row, i), gj = (TX)ineq_grad_at(row, j);
+        v += (TX)ev[(k - 1) * d.ni + r] * gi * gj;
+        if (!ident) v += (TX)(yi[r] * ineq_hess_at(row, i, j));
       }
     }
-    if (accumulate)
-      Q[e] = (TX)((double)Q[e] + v);
-    else
-      Q[e] = (TX)v;
+    Q[e] = v;
   }
 }
 
 // Cholesky of the nxn symmetric matrix in `a` (row-major, double) in place;
 // lower triangle holds L.  Returns min pivot ratio L_jj^2 / a_jj, or -1 if a
 // pivot is not positive.
-__device__ inline double warp_cholesky(double* a, int n, int lane) {
+template <class C>
+__device__ inline double warp_cholesky(const C& c, double* a, int n) {
+  const int lane = c.lane;
   double ratio = 1.0;
   for (int j = 0; j < n; ++j) {
-    __syncwarp();
+    team_sync(c);
     double diag0 = a[j * n + j];
     // a_jj already holds the Schur complement pivot
     double piv = diag0;
     if (!(piv > 0.0) || !isfinite(piv)) return -1.0;
     double l = sqrt(piv);
-    __syncwarp();
+    team_sync(c);
     if (lane == 0) a[j * n + j] = l;
-    for (int i = j + 1 + lane; i < n; i += 32) a[i * n + j] /= l;
-    __syncwarp();
+    for (int i = j + 1 + lane; i < n; i += c.T) a[i * n + j] /= l;
+    team_sync(c);
     int rem = n - j - 1;
-    for (int e = lane; e < rem * rem; e += 32) {
+    for (int e = lane; e < rem * rem; e += c.T) {
       int i = j + 1 + e / rem, t = j + 1 + (e - (e / rem) * rem);
       if (t <= i) a[i * n + t] -= a[i * n + j] * a[t * n + j];
     }
   }
-  __syncwarp();
+  team_sync(c);
   return ratio;
 }
 
@@ -589,7 +621,7 @@ __device__ __forceinline__ double pivot_ratio(const double* L, const double* dia
 
 // Restoration: P~ = P - Y^T Y with Y = L_M^{-1} D^1/2 P, M = I + D^1/2 P D^1/2 = L_M L_M^T.
 template <class TB, class TF, class TX>
-__device__ bool resto_transform(Ctx<TB, TF>& c, TX* Pb, const double* D, TX* LM, TX* Y) {
+__device__ __noinline__ bool resto_transform(Ctx<TB, TF>& c, TX* Pb, const double* D, TX* LM, TX* Y) {
   const Dims& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx;
@@ -599,50 +631,50 @@ __device__ bool resto_transform(Ctx<TB, TF>& c, TX* Pb, const double* D, TX* LM,
     double v = sqrt(D[i]) * (double)Pb[e] * sqrt(D[j]) + (i == j ? 1.0 : 0.0);
     LM[e] = (TX)v;
   }
-  __syncwarp();
+  team_sync(c);
   for (int j = 0; j < nx; ++j) {
-    __syncwarp();
+    team_sync(c);
     double piv = (double)LM[j * nx + j];
     if (!(piv > 0.0) || !isfinite(piv)) return false;
     double l = sqrt(piv);
-    __syncwarp();
+    team_sync(c);
     if (lane == 0) LM[j * nx + j] = (TX)l;
-    for (int i = j + 1 + lane; i < nx; i += 32) LM[i * nx + j] = (TX)((double)LM[i * nx + j] / l);
-    __syncwarp();
+    for (int i = j + 1 + lane; i < nx; i += c.T) LM[i * nx + j] = (TX)((double)LM[i * nx + j] / l);
+    team_sync(c);
     int rem = nx - j - 1;
-    for (int e = lane; e < rem * rem; e += 32) {
+    for (int e = lane; e < rem * rem; e += c.T) {
       int i = j + 1 + e / rem, t = j + 1 + (e - (e / rem) * rem);
       if (t <= i) LM[i * nx + t] = (TX)((double)LM[i * nx + t] - (double)LM[i * nx + j] * (double)LM[t * nx + j]);
     }
   }
-  __syncwarp();
+  team_sync(c);
   // Y = L^{-1} (D^1/2 P): forward substitution, one column per lane
-  for (int col = lane; col < nx; col += 32) {
+  for (int col = lane; col < nx; col += c.T) {
     for (int i = 0; i < nx; ++i) {
       double acc = sqrt(D[i]) * (double)Pb[i * nx + col];
       for (int t = 0; t < i; ++t) acc -= (double)LM[i * nx + t] * (double)Y[t * nx + col];
       Y[i * nx + col] = (TX)(acc / (double)LM[i * nx + i]);
     }
   }
-  __syncwarp();
+  team_sync(c);
   LANE_LOOP(e, nx * nx) {
     int i = e / nx, j = e - (e / nx) * nx;
     double acc = 0.0;
     for (int t = 0; t < nx; ++t) acc += (double)Y[t * nx + i] * (double)Y[t * nx + j];
     Pb[e] = (TX)((double)Pb[e] - acc);
   }
-  __syncwarp();
+  team_sync(c);
   return true;
 }
 
 template <class TB, class TF, class TX>
-__device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const double* y) {
+__device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const double* y) {
   const Dims& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx, nu = d.nu, nq = d.nq, N = d.N;
   const bool ident = flags & FF_IDENT;
   const bool resto = flags & FF_RESTO;
-  Scratch<TX> s = scratch<TX>(c.smem, d);
+  Scratch<TX> s = scratch<TX>(scratch_base<TX>(c), d);
   const double* dv = c.f + c.L.dv;
   c.n_fact++;
   compute_diag(c, dw, flags);
@@ -650,14 +682,14 @@ __device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const dou
 
   // terminal block P_N = Q~_N
   add_state_block<TB, TF, TX>(c, N, s.Pb, dw, flags, y, false);
-  __syncwarp();
+  team_sync(c);
   if (resto) {
     if (!resto_transform<TB, TF, TX>(c, s.Pb, dv + row_dyn(d, N - 1), F.LM + (long long)N * nx * nx,
                                      F.Yr + (long long)N * nx * nx))
       return 0;
   }
   LANE_LOOP(e, nx * nx) F.Pt[(long long)N * nx * nx + e] = s.Pb[e];
-  __syncwarp();
+  team_sync(c);
 
   for (int k = N - 1; k >= 0; --k) {
     // stage Jacobian blocks
@@ -665,7 +697,7 @@ __device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const dou
     const TB* Bg = c.blk + c.L.B + (long long)k * nq * 48;
     LANE_LOOP(e, 144 * nq) s.Ab[e] = (TX)Ag[e];
     LANE_LOOP(e, 48 * nq) s.Bb[e] = (TX)Bg[e];
-    __syncwarp();
+    team_sync(c);
     // PA = P~ A, PB = P~ B (block-diagonal A, B; column-major blocks)
     LANE_LOOP(e, nx * nx) {
       int i = e / nx, col = e - (e / nx) * nx;
@@ -687,7 +719,7 @@ __device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const dou
       for (int r = 0; r < 12; ++r) acc += prow[r] * b[r];
       s.PB[e] = acc;
     }
-    __syncwarp();
+    team_sync(c);
     // R^ = R~ + B^T P~ B ; S^ = S + B^T P~ A
     LANE_LOOP(e, nu * nu) {
       int a = e / nu, b = e - (e / nu) * nu;
@@ -696,16 +728,14 @@ __device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const dou
       TX acc = 0;
 #pragma unroll
       for (int r = 0; r < 12; ++r) acc += bcol[r] * s.PB[(12 * qa + r) * nu + b];
-      double v = (double)acc;
       int ui = off_u(d, k) + a;
-      if (a == b) v += obj_hdiag(c, ui, flags) + (ident ? 0.0 : sigma_of(c, ui) + dw);
+      if (a == b) acc += (TX)(obj_hdiag(c, ui, flags) + (ident ? 0.0 : sigma_of(c, ui) + dw));
       int qb = b / 4;
       if (!ident && qa == qb) {
         const TB* H = c.blk + c.L.H + ((long long)k * nq + qa) * 100;
-        v += (double)H[(6 + (b - 4 * qb)) * 10 + (6 + ca)];
+        acc += (TX)H[(6 + (b - 4 * qb)) * 10 + (6 + ca)];
       }
-      s.Rh[e] = (TX)v;
-      s.R64[e] = v;
+      s.R64[e] = (double)acc;
     }
     LANE_LOOP(e, nu * nx) {
       int a = e / nx, col = e - (e / nx) * nx;
@@ -714,15 +744,14 @@ __device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const dou
       TX acc = 0;
 #pragma unroll
       for (int r = 0; r < 12; ++r) acc += bcol[r] * s.PA[(12 * qa + r) * nx + col];
-      double v = (double)acc;
       int qc = col / 12, cc = col - 12 * qc;
       if (!ident && qc == qa && cc >= 6) {
         const TB* H = c.blk + c.L.H + ((long long)k * nq + qa) * 100;
-        v += (double)H[(cc - 6) * 10 + (6 + ca)];
+        acc += (TX)H[(cc - 6) * 10 + (6 + ca)];
       }
-      s.Sh[e] = (TX)v;
+      s.Sh[e] = acc;
     }
-    __syncwarp();
+    team_sync(c);
     // Q^ = A^T P~ A + Q~_k (overwrites Pb)
     LANE_LOOP(e, nx * nx) {
       int i = e / nx, col = e - (e / nx) * nx;
@@ -733,31 +762,34 @@ __device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const dou
       for (int r = 0; r < 12; ++r) acc += acol[r] * s.PA[(12 * q + r) * nx + col];
       s.Pb[e] = acc;
     }
-    __syncwarp();
+    team_sync(c);
     add_state_block<TB, TF, TX>(c, k, s.Pb, dw, flags, y, true);
     // Cholesky of R^ in FP64: the inertia test
     double* R64 = s.R64;
-    __syncwarp();
+    team_sync(c);
     double diag_j[32];
     for (int j = 0; j < nu && j < 32; ++j) diag_j[j] = R64[j * nu + j];
-    if (warp_cholesky(R64, nu, lane) < 0.0) return 0;
+    if (warp_cholesky(c, R64, nu) < 0.0) return 0;
     if (sizeof(TX) == 4) min_ratio = fmin(min_ratio, pivot_ratio(R64, diag_j, nu < 32 ? nu : 32));
+    // Cholesky factor in the factorisation precision (stored, and used for K)
+    LANE_LOOP(e, nu * nu) s.Rh[e] = (TX)R64[e];
+    team_sync(c);
     // K = -R^{-1} S^: one column per lane
-    for (int col = lane; col < nx; col += 32) {
-      double z[32];
+    for (int col = lane; col < nx; col += c.T) {
+      TX z[32];
       for (int i = 0; i < nu; ++i) {
-        double acc = (double)s.Sh[i * nx + col];
-        for (int t = 0; t < i; ++t) acc -= R64[i * nu + t] * z[t];
-        z[i] = acc / R64[i * nu + i];
+        TX acc = s.Sh[i * nx + col];
+        for (int t = 0; t < i; ++t) acc -= s.Rh[i * nu + t] * z[t];
+        z[i] = acc / s.Rh[i * nu + i];
       }
       for (int i = nu - 1; i >= 0; --i) {
-        double acc = z[i];
-        for (int t = i + 1; t < nu; ++t) acc -= R64[t * nu + i] * z[t];
-        z[i] = acc / R64[i * nu + i];
+        TX acc = z[i];
+        for (int t = i + 1; t < nu; ++t) acc -= s.Rh[t * nu + i] * z[t];
+        z[i] = acc / s.Rh[i * nu + i];
       }
-      for (int i = 0; i < nu; ++i) s.Kb[i * nx + col] = (TX)(-z[i]);
+      for (int i = 0; i < nu; ++i) s.Kb[i * nx + col] = -z[i];
     }
-    __syncwarp();
+    team_sync(c);
     // P_k = Q^ + S^T K, symmetrised
     LANE_LOOP(e, nx * nx) {
       int i = e / nx, j = e - (e / nx) * nx;
@@ -765,16 +797,16 @@ __device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const dou
       for (int a = 0; a < nu; ++a) acc += s.Sh[a * nx + i] * s.Kb[a * nx + j];
       s.PA[e] = s.Pb[e] + acc;
     }
-    __syncwarp();
+    team_sync(c);
     LANE_LOOP(e, nx * nx) {
       int i = e / nx, j = e - (e / nx) * nx;
-      s.Pb[e] = (TX)(0.5 * ((double)s.PA[i * nx + j] + (double)s.PA[j * nx + i]));
+      s.Pb[e] = (TX)0.5 * (s.PA[i * nx + j] + s.PA[j * nx + i]);
     }
     TX* Kg = F.K + (long long)k * nu * nx;
     LANE_LOOP(e, nu * nx) Kg[e] = s.Kb[e];
     TX* Lg = F.Lr + (long long)k * nu * nu;
-    LANE_LOOP(e, nu * nu) Lg[e] = (TX)R64[e];
-    __syncwarp();
+    LANE_LOOP(e, nu * nu) Lg[e] = s.Rh[e];
+    team_sync(c);
     if (resto) {
       const double* D = dv + (k == 0 ? 0 : row_dyn(d, k - 1));
       if (!resto_transform<TB, TF, TX>(c, s.Pb, D, F.LM + (long long)k * nx * nx,
@@ -782,7 +814,7 @@ __device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const dou
         return 0;
     }
     LANE_LOOP(e, nx * nx) F.Pt[(long long)k * nx * nx + e] = s.Pb[e];
-    __syncwarp();
+    team_sync(c);
   }
   if (sizeof(TX) == 4 && min_ratio < 1e-5) return 2;
   return 1;
@@ -794,13 +826,13 @@ __device__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const dou
 // and r is K-sized: [r_x (n) | r_p (m) | r_n (m) | r_c (m)] (r_p, r_n only in
 // restoration; the layout always reserves them).  out has the same layout.
 template <class TB, class TF, class TX>
-__device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, int flags,
+__device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, int flags,
                       const double* y) {
   const Dims& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx, nu = d.nu, N = d.N, n = d.n, m = d.m;
   const bool resto = flags & FF_RESTO;
-  Scratch<TX> s = scratch<TX>(c.smem, d);
+  Scratch<TX> s = scratch<TX>(scratch_base<TX>(c), d);
   c.n_solve++;
   const double* dsv = c.f + c.L.dsv;
   const double* ev = c.f + c.L.ev;
@@ -820,7 +852,7 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
   // condensed constraint residual r~_c (restoration folds r_p, r_n in)
   double* rct = c.f + c.L.rct;  // condensed constraint residual (m)
   LANE_LOOP(i, m) rct[i] = resto ? rc[i] + rp[i] * ipv[i] - rn[i] * inv[i] : rc[i];
-  __syncwarp();
+  team_sync(c);
   TX* pv = s.v0;  // p_k / p~_k
   TX* tv = s.v1;
   TX* gv = s.v2;  // nu entries (nu <= nx)
@@ -843,7 +875,7 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
       }
       pv[i] = (TX)v;
     }
-    __syncwarp();
+    team_sync(c);
   };
   // p~ = p - Y^T L^{-1} D^1/2 p (restoration), in place on pv
   auto ptransform = [&](int k, const double* D) {
@@ -856,22 +888,22 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
         wv[i] = (TX)(acc / (double)LM[i * nx + i]);
       }
     }
-    __syncwarp();
+    team_sync(c);
     LANE_LOOP(i, nx) {
       double acc = 0.0;
       for (int t = 0; t < nx; ++t) acc += (double)Y[t * nx + i] * (double)wv[t];
       tv[i] = (TX)((double)pv[i] - acc);
     }
-    __syncwarp();
+    team_sync(c);
     LANE_LOOP(i, nx) pv[i] = tv[i];
-    __syncwarp();
+    team_sync(c);
   };
 
   // ---- backward sweep
   qtilde(N);
   if (resto) ptransform(N, dv + row_dyn(d, N - 1));
   LANE_LOOP(i, nx) F.ptv[(long long)N * nx + i] = pv[i];
-  __syncwarp();
+  team_sync(c);
   for (int k = N - 1; k >= 0; --k) {
     const TX* Pt = F.Pt + (long long)(k + 1) * nx * nx;
     const TB* Ag = c.blk + c.L.A + (long long)k * d.nq * 144;
@@ -882,7 +914,7 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
       for (int j = 0; j < nx; ++j) acc += Pt[i * nx + j] * (TX)(-rct[row_dyn(d, k) + j]);
       tv[i] = acc;
     }
-    __syncwarp();
+    team_sync(c);
     // g^ = r_u + B^T t
     LANE_LOOP(a, nu) {
       int q = a / 4, ca = a - 4 * q;
@@ -891,7 +923,7 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
       for (int rr = 0; rr < 12; ++rr) acc += (TX)b[rr] * tv[12 * q + rr];
       gv[a] = acc;
     }
-    __syncwarp();
+    team_sync(c);
     // k_k = -R^{-1} g^ (lane 0)
     const TX* Lr = F.Lr + (long long)k * nu * nu;
     TX* kf = F.kff + (long long)k * nu;
@@ -919,13 +951,13 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
       for (int aa = 0; aa < nu; ++aa) acc += Kg[aa * nx + i] * gv[aa];
       wv[i] = acc;
     }
-    __syncwarp();
+    team_sync(c);
     qtilde(k);
     LANE_LOOP(i, nx) pv[i] = pv[i] + wv[i];
-    __syncwarp();
+    team_sync(c);
     if (resto) ptransform(k, dv + (k == 0 ? 0 : row_dyn(d, k - 1)));
     LANE_LOOP(i, nx) F.ptv[(long long)k * nx + i] = pv[i];
-    __syncwarp();
+    team_sync(c);
   }
 
   // ---- forward sweep; pv = Delta x_k, tv = xi / lambda scratch
@@ -934,13 +966,13 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
     const TX* pt0 = F.ptv;
     // xi_0 = -r~_c(init); lambda_0 = P~_0 xi_0 + p~_0; dx_0 = xi_0 - D lambda_0
     LANE_LOOP(i, nx) wv[i] = (TX)(-rct[i]);
-    __syncwarp();
+    team_sync(c);
     LANE_LOOP(i, nx) {
       TX acc = pt0[i];
       for (int j = 0; j < nx; ++j) acc += Pt0[i * nx + j] * wv[j];
       tv[i] = acc;
     }
-    __syncwarp();
+    team_sync(c);
     LANE_LOOP(i, nx) {
       double lam = (double)tv[i];
       double dx0 = (double)wv[i] - (resto ? dv[i] * lam : 0.0);
@@ -948,7 +980,7 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
       ox[i] = dx0;
       oy[i] = -lam;
     }
-    __syncwarp();
+    team_sync(c);
   }
   for (int k = 0; k < N; ++k) {
     const TB* Ag = c.blk + c.L.A + (long long)k * d.nq * 144;
@@ -961,7 +993,7 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
       gv[a] = acc;
       ox[off_u(d, k) + a] = (double)acc;
     }
-    __syncwarp();
+    team_sync(c);
     // xi = A dx + B du + d~
     LANE_LOOP(i, nx) {
       int q = i / 12, ri = i - 12 * q;
@@ -970,7 +1002,7 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
       for (int j = 0; j < 4; ++j) acc += (TX)Bg[q * 48 + j * 12 + ri] * gv[4 * q + j];
       wv[i] = acc;
     }
-    __syncwarp();
+    team_sync(c);
     const TX* Pt = F.Pt + (long long)(k + 1) * nx * nx;
     const TX* ptk = F.ptv + (long long)(k + 1) * nx;
     LANE_LOOP(i, nx) {
@@ -978,7 +1010,7 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
       for (int j = 0; j < nx; ++j) acc += Pt[i * nx + j] * wv[j];
       tv[i] = acc;
     }
-    __syncwarp();
+    team_sync(c);
     LANE_LOOP(i, nx) {
       double lam = (double)tv[i];
       double dxn = (double)wv[i] - (resto ? dv[row_dyn(d, k) + i] * lam : 0.0);
@@ -986,10 +1018,10 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
       ox[off_x(d, k + 1) + i] = dxn;
       oy[row_dyn(d, k) + i] = -lam;
     }
-    __syncwarp();
+    team_sync(c);
   }
   // inequality multipliers and slacks
-  for (int t = lane; t < N * d.ni; t += 32) {
+  for (int t = lane; t < N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, rr = t - (t / d.ni) * d.ni;
     IneqRow row = ineq_row(d, c.th, x + off_x(d, k), rr);
     double gdx = 0.0;
@@ -1004,20 +1036,20 @@ __device__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, i
     ox[off_s(d, k) + rr] = (dyi - rs) / dsv[t];
   }
   if (resto) {
-    __syncwarp();
+    team_sync(c);
     LANE_LOOP(i, m) {
       op[i] = (oy[i] - rp[i]) * ipv[i];
       on[i] = (-oy[i] - rn[i]) * inv[i];
     }
   }
-  __syncwarp();
+  team_sync(c);
 }
 
 // ---------------------------------------------------- KKT mat-vec (FP64)
 // out = K v for the matrix that `factor` condensed (same dw, same phase),
 // K-sized layout as in `solve`.  Used for iterative refinement.
 template <class TB, class TF>
-__device__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double* out, double dw,
+__device__ __noinline__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double* out, double dw,
                            const double* y) {
   const Dims& d = c.d;
   const int lane = c.lane;
@@ -1035,8 +1067,8 @@ __device__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double* out, double 
     (void)kind;
     out[i] = acc;
   }
-  __syncwarp();
-  for (int t = lane; t < N * d.nq; t += 32) {
+  team_sync(c);
+  for (int t = lane; t < N * d.nq; t += c.T) {
     int k = t / d.nq, q = t - (t / d.nq) * d.nq;
     const TB* A = c.blk + c.L.A + ((long long)k * d.nq + q) * 144;
     const TB* B = c.blk + c.L.B + ((long long)k * d.nq + q) * 48;
@@ -1061,11 +1093,11 @@ __device__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double* out, double 
       out[ou + a] += acc;
     }
   }
-  __syncwarp();
+  team_sync(c);
   LANE_LOOP(i, nx) out[off_x(d, N) + i] += vy[row_dyn(d, N - 1) + i];
-  __syncwarp();
+  team_sync(c);
   // inequality Hessian and G^T v_y on positions; -v_y on slacks
-  for (int t = lane; t < N * 3 * d.nq; t += 32) {
+  for (int t = lane; t < N * 3 * d.nq; t += c.T) {
     int k = 1 + t / (3 * d.nq);
     int pc = t - (t / (3 * d.nq)) * (3 * d.nq);
     int q = pc / 3, comp = pc - 3 * (pc / 3);
@@ -1087,7 +1119,7 @@ __device__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double* out, double 
     }
     out[off_x(d, k) + i] += acc;
   }
-  for (int t = lane; t < N * d.ni; t += 32) {
+  for (int t = lane; t < N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
     out[off_s(d, k) + r] -= vy[row_ineq(d, k) + r];
   }
@@ -1097,10 +1129,10 @@ __device__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double* out, double 
       out[n + m + i] += vy[i];
     }
   }
-  __syncwarp();
+  team_sync(c);
   // constraint part: J v_w (- v_p + v_n in restoration)
   LANE_LOOP(i, nx) oy[i] = v[i];
-  for (int t = lane; t < N * d.nq; t += 32) {
+  for (int t = lane; t < N * d.nq; t += c.T) {
     int k = t / d.nq, q = t - (t / d.nq) * d.nq;
     const TB* A = c.blk + c.L.A + ((long long)k * d.nq + q) * 144;
     const TB* B = c.blk + c.L.B + ((long long)k * d.nq + q) * 48;
@@ -1114,7 +1146,7 @@ __device__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double* out, double 
       oy[row_dyn(d, k) + 12 * q + r] = acc;
     }
   }
-  for (int t = lane; t < N * d.ni; t += 32) {
+  for (int t = lane; t < N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
     IneqRow row = ineq_row(d, c.th, x + off_x(d, k), r);
     const double* vx = v + off_x(d, k);
@@ -1125,11 +1157,11 @@ __device__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double* out, double 
     }
     oy[row_ineq(d, k) + r] = acc;
   }
-  __syncwarp();
+  team_sync(c);
   if (c.resto) {
     LANE_LOOP(i, m) oy[i] += -v[n + i] + v[n + m + i];
   }
-  __syncwarp();
+  team_sync(c);
   (void)nu;
 }
 

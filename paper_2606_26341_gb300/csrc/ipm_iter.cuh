@@ -19,29 +19,29 @@ enum Outcome : int { OUT_ACCEPTED = 0, OUT_LS_FAILED = 1 };
 template <class TB, class TF>
 __device__ double l1_norm(Ctx<TB, TF>& c, const double* v, int len) {
   double a = 0.0;
-  for (int i = c.lane; i < len; i += 32) a += fabs(v[i]);
-  return warp_sum(a);
+  for (int i = c.lane; i < len; i += c.T) a += fabs(v[i]);
+  return team_sum(c, a);
 }
 template <class TB, class TF>
 __device__ double inf_norm(Ctx<TB, TF>& c, const double* v, int len) {
   double a = 0.0;
-  for (int i = c.lane; i < len; i += 32) a = fmax(a, fabs(v[i]));
-  return warp_max(a);
+  for (int i = c.lane; i < len; i += c.T) a = fmax(a, fabs(v[i]));
+  return team_max(c, a);
 }
 template <class TB, class TF>
 __device__ bool all_finite(Ctx<TB, TF>& c, const double* v, int len) {
   int bad = 0;
-  for (int i = c.lane; i < len; i += 32) bad |= !isfinite(v[i]);
-  return !warp_or(bad);
+  for (int i = c.lane; i < len; i += c.T) bad |= !isfinite(v[i]);
+  return !team_or(c, bad);
 }
 
 // barrier objective phi_mu (Eq. 3) with the one-sided damping term, over the
 // first `len` entries of a W-sized point w; +inf outside the bounds
 template <class TB, class TF>
-__device__ double barrier_phi(Ctx<TB, TF>& c, const double* w, double f, double mu, int len) {
+__device__ __noinline__ double barrier_phi(Ctx<TB, TF>& c, const double* w, double f, double mu, int len) {
   double acc = 0.0;
   int bad = 0;
-  for (int i = c.lane; i < len; i += 32) {
+  for (int i = c.lane; i < len; i += c.T) {
     int kind = wkind(c.d, i);
     if (kind == VK_FREE) continue;
     double sl = w[i];
@@ -55,8 +55,8 @@ __device__ double barrier_phi(Ctx<TB, TF>& c, const double* w, double f, double 
       acc += kKappaD * mu * sl;
     }
   }
-  if (warp_or(bad)) return INFINITY;
-  return f + warp_sum(acc);
+  if (team_or(c, bad)) return INFINITY;
+  return f + team_sum(c, acc);
 }
 
 // scaled optimality error E_mu of Eq. 5 (IPOPT's scaling)
@@ -65,7 +65,7 @@ struct ErrParts {
 };
 
 template <class TB, class TF>
-__device__ ErrParts err_parts(Ctx<TB, TF>& c) {
+__device__ __noinline__ ErrParts err_parts(Ctx<TB, TF>& c) {
   const double* gf = c.f + c.L.gf;
   const double* jty = c.f + c.L.jty;
   const double* zl = c.f + c.L.zl;
@@ -73,7 +73,7 @@ __device__ ErrParts err_parts(Ctx<TB, TF>& c) {
   const double* y = c.f + c.L.y;
   const double* cv = c.f + c.L.c;
   double du = 0.0, z1 = 0.0, nb = 0.0;
-  for (int i = c.lane; i < c.nw; i += 32) {
+  for (int i = c.lane; i < c.nw; i += c.T) {
     int kind = wkind(c.d, i);
     double zli = has_lower(kind) ? zl[i] : 0.0;
     double zui = has_upper(kind) ? zu[i] : 0.0;
@@ -82,31 +82,31 @@ __device__ ErrParts err_parts(Ctx<TB, TF>& c) {
     nb += (has_lower(kind) ? 1.0 : 0.0) + (has_upper(kind) ? 1.0 : 0.0);
   }
   double pr = 0.0, y1 = 0.0;
-  for (int i = c.lane; i < c.d.m; i += 32) {
+  for (int i = c.lane; i < c.d.m; i += c.T) {
     pr = fmax(pr, fabs(cv[i]));
     y1 += fabs(y[i]);
   }
   ErrParts e;
-  e.dual = warp_max(du);
-  e.prim = warp_max(pr);
-  e.y1 = warp_sum(y1);
-  e.z1 = warp_sum(z1);
-  e.nb = warp_sum(nb);
+  e.dual = team_max(c, du);
+  e.prim = team_max(c, pr);
+  e.y1 = team_sum(c, y1);
+  e.z1 = team_sum(c, z1);
+  e.nb = team_sum(c, nb);
   return e;
 }
 
 template <class TB, class TF>
-__device__ double opt_error(Ctx<TB, TF>& c, const ErrParts& e, double mu) {
+__device__ __noinline__ double opt_error(Ctx<TB, TF>& c, const ErrParts& e, double mu) {
   const double* w = c.f + c.L.x;
   const double* zl = c.f + c.L.zl;
   const double* zu = c.f + c.L.zu;
   double comp = 0.0;
-  for (int i = c.lane; i < c.nw; i += 32) {
+  for (int i = c.lane; i < c.nw; i += c.T) {
     int kind = wkind(c.d, i);
     if (has_lower(kind)) comp = fmax(comp, fabs(w[i] * zl[i] - mu));
     if (has_upper(kind)) comp = fmax(comp, fabs((kUmax - w[i]) * zu[i] - mu));
   }
-  comp = warp_max(comp);
+  comp = team_max(c, comp);
   double nb = fmax(1.0, e.nb);
   double s_d = fmax(kSmax, (e.y1 + e.z1) / fmax(1.0, c.d.m + e.nb)) / kSmax;
   double s_c = fmax(kSmax, e.z1 / nb) / kSmax;
@@ -116,15 +116,15 @@ __device__ double opt_error(Ctx<TB, TF>& c, const ErrParts& e, double mu) {
 // largest alpha in (0, 1] keeping the bounded entries of w + alpha dw at least
 // the fraction 1 - tau of their distance to the bounds
 template <class TB, class TF>
-__device__ double ftb_primal(Ctx<TB, TF>& c, const double* w, const double* dw, double tau) {
+__device__ __noinline__ double ftb_primal(Ctx<TB, TF>& c, const double* w, const double* dw, double tau) {
   double a = 1.0;
-  for (int i = c.lane; i < c.nw; i += 32) {
+  for (int i = c.lane; i < c.nw; i += c.T) {
     int kind = wkind(c.d, i);
     if (kind == VK_FREE) continue;
     if (dw[i] < 0.0) a = fmin(a, -tau * w[i] / dw[i]);
     if (kind == VK_BOX && dw[i] > 0.0) a = fmin(a, tau * (kUmax - w[i]) / dw[i]);
   }
-  return warp_min(a);
+  return team_min(c, a);
 }
 
 // bound-multiplier steps (text after Eq. 6) for the primal step dx at the
@@ -137,18 +137,20 @@ __device__ __forceinline__ double dz_upper(double su, double zu, double mu, doub
 }
 
 // ---------------------------------------------------------------- filter
-__device__ __forceinline__ bool in_filter(const double* filt, int nf, double theta, double phi,
-                                          double theta_max, int lane) {
+template <class C>
+__device__ __forceinline__ bool in_filter(const C& c, const double* filt, int nf, double theta,
+                                          double phi, double theta_max) {
   if (!(theta < theta_max)) return true;
   int hit = 0;
-  for (int j = lane; j < nf; j += 32) hit |= (theta >= filt[2 * j] && phi >= filt[2 * j + 1]);
-  return warp_or(hit);
+  for (int j = c.lane; j < nf; j += c.T) hit |= (theta >= filt[2 * j] && phi >= filt[2 * j + 1]);
+  return team_or(c, hit);
 }
 
-__device__ __forceinline__ void filter_add(double* filt, int& nf, double theta, double phi,
-                                           int lane) {
+template <class C>
+__device__ __forceinline__ void filter_add(const C& c, double* filt, int& nf, double theta,
+                                           double phi) {
   int cnt = nf;
-  if (lane == 0) {
+  if (c.lane == 0) {
     int w = 0;
     for (int j = 0; j < cnt; ++j) {
       double t = filt[2 * j], p = filt[2 * j + 1];
@@ -170,15 +172,42 @@ __device__ __forceinline__ void filter_add(double* filt, int& nf, double theta, 
     }
     cnt = w;
   }
-  __syncwarp();
-  nf = __shfl_sync(0xffffffffu, cnt, 0);
+  team_sync(c);
+  nf = team_bcast0(c, cnt);
 }
 
 // -------------------------------------------------- factorisation and solve
+// Largest barrier diagonal of the condensed system: Sigma of the inputs and
+// the condensation weight E of the slacks.  Relative to the O(1) Hessian
+// blocks it measures how much of FP32's 24-bit mantissa the factorisation
+// loses in the position and input blocks.
 template <class TB, class TF>
-__device__ bool factor_any(Ctx<TB, TF>& c, double dw, bool force64) {
+__device__ __noinline__ double barrier_scale(Ctx<TB, TF>& c) {
+  const Dims& d = c.d;
+  const double* ev = c.f + c.L.ev;
+  const double* sg = c.f + c.L.sig;
+  double b = 0.0;
+  for (int t = c.lane; t < d.N * d.ni; t += c.T) b = fmax(b, ev[t]);
+  for (int t = c.lane; t < d.N * d.nu; t += c.T) {
+    int k = t / d.nu, a = t - (t / d.nu) * d.nu;
+    b = fmax(b, sg[off_u(d, k) + a]);
+  }
+  return team_max(c, b);
+}
+
+template <class TB, class TF>
+__device__ __noinline__ bool factor_any(Ctx<TB, TF>& c, double dw, bool force64) {
   const int flags = c.resto ? FF_RESTO : 0;
   const double* y = c.f + c.L.y;
+  if (sizeof(TF) == 4 && !c.resto && !force64) {
+    // per-problem precision choice: FP32 only while the barrier terms leave
+    // the refinement a well-conditioned preconditioned system
+    compute_diag(c, dw, flags);
+    if (c.P->opt.fp32_switch < 0.0 || barrier_scale(c) > c.P->opt.fp32_switch) {
+      force64 = true;
+      c.n_esc++;
+    }
+  }
   if (sizeof(TF) == 8 || c.resto || force64) {
     c.use64 = 1;
     return factor<TB, TF, double>(c, c.fac64, dw, flags, y) != 0;
@@ -195,59 +224,118 @@ __device__ bool factor_any(Ctx<TB, TF>& c, double dw, bool force64) {
 }
 
 // Solves K out = -r.  With an FP32 factorisation the step is refined in FP64
-// (residual with the FP64 KKT mat-vec, correction with the FP32 factors) until
-// IPOPT's residual ratio drops below 1e-10; if that fails within 10 steps the
-// matrix is refactorised in FP64.  Returns false only if that FP64
-// refactorisation reports wrong inertia.
+// by restarted GMRES on K, right-preconditioned with the FP32 factors (the
+// GMRES form of iterative refinement): residuals and Krylov vectors are FP64,
+// each preconditioner application is one FP32 solve.  It stops when IPOPT's
+// residual ratio |K out + r| / (min(|out|, 1e6 |r|) + |r|) drops below 1e-10;
+// if that fails within the restarts the matrix is refactorised in FP64.
+// Returns false only if that FP64 refactorisation reports wrong inertia.
 template <class TB, class TF>
-__device__ bool solve_refined(Ctx<TB, TF>& c, const double* r, double* out) {
+__device__ __noinline__ bool solve_refined(Ctx<TB, TF>& c, const double* r, double* out) {
   const int flags = c.resto ? FF_RESTO : 0;
   const double* y = c.f + c.L.y;
   if (c.use64) {
     solve<TB, TF, double>(c, c.fac64, r, out, flags, y);
     return true;
   }
-  solve<TB, TF, TF>(c, c.fac, r, out, flags, y);
+  const int lane = c.lane;
   const int nwk = (int)c.L.nw;
   const int nused = c.nw;
-  const int mm = c.d.m;
+  const int len = nused + c.d.m;
+  const long long nk = c.L.nk;
   double* res = c.f + c.L.res;
   double* corr = c.f + c.L.corr;
-  // norms over the used entries: [0, nw) and [nwk, nwk + m)
-  auto norm_used = [&](const double* v) {
+  double* V = c.f + c.L.gmv;
+  auto at = [&](int i) { return i < nused ? i : nwk + (i - nused); };
+  auto norm2 = [&](const double* v) {
     double a = 0.0;
-    for (int i = c.lane; i < nused + mm; i += 32) {
-      int j = i < nused ? i : nwk + (i - nused);
-      a = fmax(a, fabs(v[j]));
+    for (int i = lane; i < len; i += c.T) {
+      double t = v[at(i)];
+      a += t * t;
     }
-    return warp_max(a);
+    return sqrt(team_sum(c, a));
   };
-  double rnorm = norm_used(r);
+  auto norm_inf = [&](const double* v) {
+    double a = 0.0;
+    for (int i = lane; i < len; i += c.T) a = fmax(a, fabs(v[at(i)]));
+    return team_max(c, a);
+  };
+  // preconditioner: z = M^{-1} v  (solve(r') returns K z = -r', so r' = -v)
+  auto precond = [&](const double* v, double* z) {
+    for (int i = lane; i < len; i += c.T) corr[at(i)] = -v[at(i)];
+    team_sync(c);
+    solve<TB, TF, TF>(c, c.fac, corr, z, flags, y);
+  };
+  solve<TB, TF, TF>(c, c.fac, r, out, flags, y);
+  const double rnorm = norm_inf(r);
   if (rnorm == 0.0) return true;
-  for (int it = 0; it <= kIrMaxSteps; ++it) {
+  for (int rs = 0; rs <= kGmresRestarts; ++rs) {
+    // residual of K out = -r
     kkt_matvec(c, out, res, c.dw, y);
-    for (int i = c.lane; i < nused + mm; i += 32) {
-      int j = i < nused ? i : nwk + (i - nused);
-      res[j] = -r[j] - res[j];
-    }
-    __syncwarp();
-    double nres = norm_used(res);
-    double snorm = norm_used(out);
-    double ratio = nres / (fmin(snorm, 1e6 * rnorm) + rnorm);
+    for (int i = lane; i < len; i += c.T) res[at(i)] = -r[at(i)] - res[at(i)];
+    team_sync(c);
+    double ratio = norm_inf(res) / (fmin(norm_inf(out), 1e6 * rnorm) + rnorm);
     if (ratio <= kIrTol) return true;
-    if (it == kIrMaxSteps) break;
-    for (int i = c.lane; i < nused + mm; i += 32) {
-      int j = i < nused ? i : nwk + (i - nused);
-      res[j] = -res[j];
+    if (rs == kGmresRestarts) break;
+    double beta = norm2(res);
+    double H[kGmresM + 1][kGmresM], cs[kGmresM], sn[kGmresM], g[kGmresM + 1];
+    for (int i = lane; i < len; i += c.T) V[at(i)] = res[at(i)] / beta;
+    g[0] = beta;
+    team_sync(c);
+    int jm = 0;
+    for (int j = 0; j < kGmresM; ++j) {
+      double* vj = V + (long long)j * nk;
+      double* vn = V + (long long)(j + 1) * nk;
+      precond(vj, res);           // res <- M^{-1} v_j
+      kkt_matvec(c, res, vn, c.dw, y);  // v_{j+1} <- K M^{-1} v_j
+      c.n_ir++;
+      for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
+        const double* vi = V + (long long)i * nk;
+        double h = 0.0;
+        for (int t = lane; t < len; t += c.T) h += vn[at(t)] * vi[at(t)];
+        h = team_sum(c, h);
+        for (int t = lane; t < len; t += c.T) vn[at(t)] -= h * vi[at(t)];
+        team_sync(c);
+        H[i][j] = h;
+      }
+      double hn = norm2(vn);
+      H[j + 1][j] = hn;
+      if (hn > 0.0) {
+        for (int t = lane; t < len; t += c.T) vn[at(t)] /= hn;
+        team_sync(c);
+      }
+      for (int i = 0; i < j; ++i) {  // previous Givens rotations
+        double a = H[i][j], b = H[i + 1][j];
+        H[i][j] = cs[i] * a + sn[i] * b;
+        H[i + 1][j] = -sn[i] * a + cs[i] * b;
+      }
+      double a = H[j][j], b = H[j + 1][j];
+      double rr = hypot(a, b);
+      cs[j] = rr > 0.0 ? a / rr : 1.0;
+      sn[j] = rr > 0.0 ? b / rr : 0.0;
+      H[j][j] = rr;
+      H[j + 1][j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      jm = j + 1;
+      if (fabs(g[j + 1]) <= 1e-12 * beta || hn == 0.0) break;
     }
-    __syncwarp();
-    solve<TB, TF, TF>(c, c.fac, res, corr, flags, y);
-    for (int i = c.lane; i < nused + mm; i += 32) {
-      int j = i < nused ? i : nwk + (i - nused);
-      out[j] += corr[j];
+    // y = H^{-1} g, out += M^{-1} (V y)
+    double yv[kGmresM];
+    for (int i = jm - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int t = i + 1; t < jm; ++t) acc -= H[i][t] * yv[t];
+      yv[i] = H[i][i] != 0.0 ? acc / H[i][i] : 0.0;
     }
-    __syncwarp();
-    c.n_ir++;
+    for (int t = lane; t < len; t += c.T) {
+      double acc = 0.0;
+      for (int i = 0; i < jm; ++i) acc += yv[i] * V[(long long)i * nk + at(t)];
+      res[at(t)] = acc;
+    }
+    team_sync(c);
+    precond(res, res);
+    for (int t = lane; t < len; t += c.T) out[at(t)] += res[at(t)];
+    team_sync(c);
   }
   // refinement did not converge: refactorise in FP64
   c.n_esc++;
@@ -260,7 +348,7 @@ __device__ bool solve_refined(Ctx<TB, TF>& c, const double* r, double* out) {
 // Least-squares multipliers: [[I, J^T], [J, 0]] (w, y) = (-(grad f - z_L + z_U), 0);
 // y = 0 if |y|_inf > y_max.
 template <class TB, class TF>
-__device__ void ls_multipliers(Ctx<TB, TF>& c) {
+__device__ __noinline__ void ls_multipliers(Ctx<TB, TF>& c) {
   const Dims& d = c.d;
   const int lane = c.lane;
   double* w = c.f + c.L.x;
@@ -276,21 +364,21 @@ __device__ void ls_multipliers(Ctx<TB, TF>& c) {
     rhs[i] = gf[i] - (has_lower(kind) ? zl[i] : 0.0) + (has_upper(kind) ? zu[i] : 0.0);
   }
   LANE_LOOP(i, d.m) rhs[c.L.nw + i] = 0.0;
-  __syncwarp();
+  team_sync(c);
   factor<TB, TF, double>(c, c.fac64, 0.0, FF_IDENT, y);
   solve<TB, TF, double>(c, c.fac64, rhs, sol, FF_IDENT, y);
   double ymax = inf_norm(c, sol + c.L.nw, d.m);
   LANE_LOOP(i, d.m) y[i] = ymax > kYmax ? 0.0 : sol[c.L.nw + i];
-  __syncwarp();
+  team_sync(c);
 }
 
 // z <- max(min(z, kappa_Sigma mu / s), mu / (kappa_Sigma s)) over the first len entries
 template <class TB, class TF>
-__device__ void kappa_sigma_reset(Ctx<TB, TF>& c, int len, double mu) {
+__device__ __noinline__ void kappa_sigma_reset(Ctx<TB, TF>& c, int len, double mu) {
   double* w = c.f + c.L.x;
   double* zl = c.f + c.L.zl;
   double* zu = c.f + c.L.zu;
-  for (int i = c.lane; i < len; i += 32) {
+  for (int i = c.lane; i < len; i += c.T) {
     int kind = wkind(c.d, i);
     if (has_lower(kind)) {
       double s = w[i];
@@ -301,7 +389,7 @@ __device__ void kappa_sigma_reset(Ctx<TB, TF>& c, int len, double mu) {
       zu[i] = fmax(fmin(zu[i], kKappaSigma * mu / s), mu / (kKappaSigma * s));
     }
   }
-  __syncwarp();
+  team_sync(c);
 }
 
 // ------------------------------------------------------------- iteration
@@ -314,19 +402,19 @@ struct TrialVal {
 // trial point w + alpha * dir: constraint violation and barrier objective of
 // the current phase; the phase constraint vector goes to ct
 template <class TB, class TF>
-__device__ TrialVal<TB, TF> trial_point(Ctx<TB, TF>& c, double alpha, const double* dir) {
+__device__ __noinline__ TrialVal<TB, TF> trial_point(Ctx<TB, TF>& c, double alpha, const double* dir) {
   const Dims& d = c.d;
   const int lane = c.lane;
   const double* w = c.f + c.L.x;
   double* xt = c.f + c.L.xt;
   double* ct = c.f + c.L.ct;
   LANE_LOOP(i, c.nw) xt[i] = w[i] + alpha * dir[i];
-  __syncwarp();
+  team_sync(c);
   c.n_trial++;
   double f = eval_values(c, xt, ct);
   if (c.resto) {
     LANE_LOOP(i, d.m) ct[i] += -xt[d.n + i] + xt[d.n + d.m + i];
-    __syncwarp();
+    team_sync(c);
     f = resto_objective(c, xt);
   }
   TrialVal<TB, TF> tv;
@@ -338,7 +426,7 @@ __device__ TrialVal<TB, TF> trial_point(Ctx<TB, TF>& c, double alpha, const doub
 }
 
 template <class TB, class TF>
-__device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
+__device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
   const Dims& d = c.d;
   const int lane = c.lane;
   const Options& opt = c.P->opt;
@@ -376,15 +464,24 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
   int& nf = c.resto ? S.n_filt_r : S.n_filt;
   double* filt = c.f + (c.resto ? c.L.filt_r : c.L.filt);
 
-  // ---- evaluation at the current point
-  double f_orig = eval_values(c, w, cv);
+  const long long t_start = clock64();
+  long long t_mark = t_start;
+  auto lap = [&](int ph) {
+    long long now = clock64();
+    S.cyc[ph] += now - t_mark;
+    t_mark = now;
+  };
+  // ---- evaluation at the current point: c(x), f(x) and J^T y in one sweep
+  double f_orig = eval_values(c, w, cv, false);
+  eval_jty(c, w, y, jty, cv);
   double fph = f_orig;
   if (c.resto) {
     LANE_LOOP(i, m) cv[i] += -w[n + i] + w[n + m + i];
-    __syncwarp();
+    team_sync(c);
     fph = resto_objective(c, w);
   }
   eval_grad(c, w, gf);
+  lap(PH_EVAL);
   if (!(isfinite(fph) && all_finite(c, cv, m) && all_finite(c, gf, c.nw))) {
     S.status = BIPM_EVAL_ERROR;
     return;
@@ -401,8 +498,11 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
     }
     return;
   }
-  if (!c.resto && S.need_y_ls) ls_multipliers(c);
-  eval_jty(c, w, y, jty);
+  if (!c.resto && S.need_y_ls) {
+    ls_multipliers(c);
+    eval_jty(c, w, y, jty);
+    lap(PH_LSQ);
+  }
   double theta = l1_norm(c, cv, m);
   if (!c.resto && S.need_init) {
     th_max = 1e4 * fmax(1.0, theta);
@@ -447,7 +547,9 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
   const double tau = fmax(kTauMin, 1.0 - mu);
 
   // ---- derivatives and the right-hand side of Eq. 7
+  lap(PH_MISC);
   eval_blocks(c, w, y, true);
+  lap(PH_DERIV);
   LANE_LOOP(i, c.nw) {
     int kind = wkind(d, i);
     double g = gf[i];
@@ -459,9 +561,11 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
     rhs2[i] = g + jty[i];
   }
   LANE_LOOP(i, m) rhs[nwk + i] = cv[i];
-  __syncwarp();
+  team_sync(c);
 
   // ---- inertia correction (IPOPT Algorithm IC) and the Newton step
+  fill_sigma(c);
+  lap(PH_MISC);
   bool force64 = false;
   double dwc = 0.0;
   bool ls_fail = false;
@@ -486,7 +590,10 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
       dw_last = dwc;
     }
     c.dw = dwc;
-    if (solve_refined(c, rhs, sol)) break;
+    lap(PH_FACTOR);
+    bool solved = solve_refined(c, rhs, sol);
+    lap(PH_SOLVE);
+    if (solved) break;
     // FP64 refactorisation after failed refinement reported wrong inertia:
     // redo the correction in FP64
     if (force64) {
@@ -507,7 +614,7 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
       const double* ddx = dir;
       const double* ddy = dir + nwk;
       double az = 1.0;
-      for (int i = lane; i < c.nw; i += 32) {
+      for (int i = lane; i < c.nw; i += c.T) {
         int kind = wkind(d, i);
         if (has_lower(kind)) {
           double dzl = dz_lower(w[i], zl[i], mu, ddx[i]);
@@ -518,8 +625,8 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
           if (dzu < 0.0) az = fmin(az, -tau * zu[i] / dzu);
         }
       }
-      az = warp_min(az);
-      for (int i = lane; i < c.nw; i += 32) {
+      az = team_min(c, az);
+      for (int i = lane; i < c.nw; i += c.T) {
         int kind = wkind(d, i);
         double dzl = has_lower(kind) ? dz_lower(w[i], zl[i], mu, ddx[i]) : 0.0;
         double dzu = has_upper(kind) ? dz_upper(kUmax - w[i], zu[i], mu, ddx[i]) : 0.0;
@@ -528,16 +635,16 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
         if (has_upper(kind)) zu[i] += az * dzu;
       }
       LANE_LOOP(i, m) y[i] += alpha * ddy[i];
-      __syncwarp();
+      team_sync(c);
       kappa_sigma_reset(c, c.nw, mu);
-      if (augment) filter_add(filt, nf, (1.0 - kGammaTheta) * theta0, phi0 - kGammaPhi * theta0, lane);
+      if (augment) filter_add(c, filt, nf, (1.0 - kGammaTheta) * theta0, phi0 - kGammaPhi * theta0);
       S.last_alpha = alpha;
     };
 
     // tiny step (Table I row 4)
     double rel = 0.0;
-    for (int i = lane; i < c.nw; i += 32) rel = fmax(rel, fabs(dx[i]) / (1.0 + fabs(w[i])));
-    rel = warp_max(rel);
+    for (int i = lane; i < c.nw; i += c.T) rel = fmax(rel, fabs(dx[i]) / (1.0 + fabs(w[i])));
+    rel = team_max(c, rel);
     if (rel < 10.0 * kEpsMach) {
       accept(a_max, sol, false);
       tiny = 1;
@@ -547,8 +654,8 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
       tiny = 0;
       phi0 = barrier_phi(c, w, fph, mu, c.nw);
       double gd = 0.0;
-      for (int i = lane; i < c.nw; i += 32) gd += gphi[i] * dx[i];
-      gdx = warp_sum(gd);
+      for (int i = lane; i < c.nw; i += c.T) gd += gphi[i] * dx[i];
+      gdx = team_sum(c, gd);
       double a_min;
       if (gdx < 0.0 && theta <= th_min)
         a_min = kGammaAlpha * fmin(kGammaTheta, fmin(kGammaPhi * theta / (-gdx),
@@ -562,7 +669,7 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
         return gdx < 0.0 && alpha * pow(-gdx, kSPhi) > kDelta * pow(theta, kSTheta);
       };
       auto acceptable = [&](double th_t, double ph_t, double alpha) {
-        if (!isfinite(ph_t) || in_filter(filt, nf, th_t, ph_t, th_max, lane)) return false;
+        if (!isfinite(ph_t) || in_filter(c, filt, nf, th_t, ph_t, th_max)) return false;
         if (switching(alpha) && theta <= th_min) return ph_t <= phi0 + kEtaPhi * alpha * gdx;
         return th_t <= (1.0 - kGammaTheta) * theta || ph_t <= phi0 - kGammaPhi * theta;
       };
@@ -584,13 +691,13 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
           if (n_trial == 1 && !(tv.theta < theta)) {
             // second-order correction (Table I row 2)
             LANE_LOOP(i, m) csoc[i] = alpha * cv[i] + ct[i];
-            __syncwarp();
+            team_sync(c);
             double theta_old = theta;
             bool soc_ok = false;
             for (int p = 1; p <= kPmax; ++p) {
               S.n_soc++;
               LANE_LOOP(i, m) rhs2[nwk + i] = csoc[i];
-              __syncwarp();
+              team_sync(c);
               if (!solve_refined(c, rhs2, sol2)) break;
               double a_soc = ftb_primal(c, w, sol2, tau);
               TrialVal<TB, TF> sv = trial_point(c, a_soc, sol2);
@@ -602,7 +709,7 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
               }
               if (p == kPmax || sv.theta > kKappaSoc * theta_old) break;
               LANE_LOOP(i, m) csoc[i] = a_soc * csoc[i] + ct[i];
-              __syncwarp();
+              team_sync(c);
               theta_old = sv.theta;
             }
             if (soc_ok) {
@@ -616,6 +723,7 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
       }
     }
   }
+  lap(PH_LS);
   S.n_ir_steps += c.n_ir;
   S.n_escalations += c.n_esc;
   S.n_fact += c.n_fact;
@@ -623,6 +731,7 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
   S.n_trial += c.n_trial;
 
   if (outcome == OUT_ACCEPTED) {
+    S.cyc[PH_TOTAL] += clock64() - t_start;
     S.iter++;
     if (c.resto) {
       S.n_resto_iter++;
@@ -633,14 +742,14 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
       double ph_o = barrier_phi(c, w, f_o, S.mu, n);
       const double* filt_o = c.f + c.L.filt;
       if (isfinite(ph_o) && th_o <= kKappaResto * S.theta_ref &&
-          !in_filter(filt_o, S.n_filt, th_o, ph_o, S.theta_max, lane)) {
+          !in_filter(c, filt_o, S.n_filt, th_o, ph_o, S.theta_max)) {
         kappa_sigma_reset(c, n, S.mu);
         LANE_LOOP(i, 2 * m) {
           w[n + i] = 0.0;
           zl[n + i] = 0.0;
           zu[n + i] = 0.0;
         }
-        __syncwarp();
+        team_sync(c);
         S.mode = MODE_NORMAL;
         S.need_y_ls = 1;
       }
@@ -649,6 +758,7 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
   }
 
   // ---- line search failed (or no regularisation gave the right inertia)
+  S.cyc[PH_TOTAL] += clock64() - t_start;
   if (c.resto) {
     S.status = BIPM_RESTO_FAILED;
     return;
@@ -660,7 +770,7 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
   // enter restoration (IPOPT Sec. 3.3 reading)
   {
     double phi = barrier_phi(c, w, f_orig, S.mu, n);
-    filter_add(filt, nf, (1.0 - kGammaTheta) * theta, phi - kGammaPhi * theta, lane);
+    filter_add(c, filt, nf, (1.0 - kGammaTheta) * theta, phi - kGammaPhi * theta);
     double cmax = inf_norm(c, cv, m);
     double mu_r = fmax(S.mu, cmax);
     S.zeta = sqrt(S.mu);
@@ -686,8 +796,8 @@ __device__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
       y[i] = 0.0;
       acc += fabs(ci - pp + nn);
     }
-    double th_r = warp_sum(acc);
-    __syncwarp();
+    double th_r = team_sum(c, acc);
+    team_sync(c);
     S.mu_r = mu_r;
     S.theta_max_r = 1e4 * fmax(1.0, th_r);
     S.theta_min_r = 1e-4 * fmax(1.0, th_r);

@@ -9,13 +9,18 @@
 namespace bipm {
 
 constexpr int kWarpsPerBlock = 4;
+constexpr int kBlockTeam = 256;    // threads of a block team
+constexpr int kBulkVisit = 64;     // iterations per problem in the warp kernel
 
 template <class TB, class TF>
-__device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, char* smem) {
+__device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, int T, double* red,
+                         char* smem) {
   c.P = P;
   c.d = P->d;
   c.L = P->L;
   c.lane = lane;
+  c.T = T;
+  c.red = red;
   c.slot = slot;
   c.f = P->f64 + (long long)slot * P->L.slot_f64;
   c.blk = (TB*)P->tb + (long long)slot * P->L.slot_tb;
@@ -27,6 +32,8 @@ __device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, ch
     c.fac64 = make_fac<double>(c.f + P->L.f64_fac, P->L);
   c.th = P->theta + (long long)slot * P->d.n_theta;
   c.smem = smem;
+  c.smem_bytes = P->smem_per_warp;
+  c.gscratch = (char*)(c.f + P->L.gscr);
   c.resto = 0;
   c.nw = P->d.n;
   c.mu = 0.0;
@@ -57,9 +64,28 @@ __device__ void slot_metrics(Ctx<TB, TF>& c, SlotState& S) {
   S.inf = e.prim;
 }
 
+// Iterates one slot: exactly n_iter iterations (n_iter > 0), or until it
+// terminates, or (visit_cap > 0) for at most visit_cap iterations in this visit.
+template <class TB, class TF>
+__device__ void run_slot(Ctx<TB, TF>& c, SlotState& S, int n_iter, int visit_cap) {
+  int done = 0;
+  if (n_iter > 0) {
+    for (; done < n_iter && S.status == BIPM_RUNNING; ++done) iterate(c, S);
+  } else {
+    while (S.status == BIPM_RUNNING && (visit_cap <= 0 || done < visit_cap)) {
+      iterate(c, S);
+      ++done;
+    }
+  }
+  if (n_iter > 0 || S.status != BIPM_RUNNING) slot_metrics(c, S);
+}
+
+// Persistent kernel, one warp per problem: each warp takes the next slot from
+// the work counter and iterates it (iteration-level batching: a warp that
+// finishes a problem immediately starts another one).
 template <class TB, class TF>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
-    ipm_kernel(const Params* __restrict__ P, int n_iter) {
+    ipm_kernel(const Params* __restrict__ P, int n_iter, int visit_cap) {
   extern __shared__ __align__(16) char smem_all[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -72,16 +98,39 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     SlotState S = P->st[slot];
     if (S.status != BIPM_RUNNING) continue;
     Ctx<TB, TF> c;
-    make_ctx(c, P, slot, lane, smem);
-    if (n_iter <= 0) {
-      while (S.status == BIPM_RUNNING) iterate(c, S);
-    } else {
-      for (int it = 0; it < n_iter && S.status == BIPM_RUNNING; ++it) iterate(c, S);
-    }
-    slot_metrics(c, S);
+    make_ctx(c, P, slot, lane, 32, nullptr, smem);
+    run_slot(c, S, n_iter, visit_cap);
     __syncwarp();
     if (lane == 0) P->st[slot] = S;
     __syncwarp();
+  }
+}
+
+// Persistent kernel, one block per problem: the same iteration with the
+// block's threads spread over all four SM sub-partitions, for the few
+// long-running problems left after the warp kernel (their per-iteration
+// latency, not the batch throughput, bounds the solve).
+template <class TB, class TF>
+__global__ void __launch_bounds__(kBlockTeam)
+    ipm_block_kernel(const Params* __restrict__ P, int n_iter) {
+  extern __shared__ __align__(16) char smem_all[];
+  double* red = (double*)smem_all;
+  char* smem = smem_all + 128;
+  __shared__ int s_slot;
+  while (true) {
+    if (threadIdx.x == 0) s_slot = atomicAdd(P->work_counter, 1);
+    __syncthreads();
+    const int slot = s_slot;
+    __syncthreads();
+    if (slot >= P->n_slots) break;
+    SlotState S = P->st[slot];
+    if (S.status != BIPM_RUNNING) continue;
+    Ctx<TB, TF> c;
+    make_ctx(c, P, slot, (int)threadIdx.x, (int)blockDim.x, red, smem);
+    run_slot(c, S, n_iter, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) P->st[slot] = S;
+    __syncthreads();
   }
 }
 
@@ -97,13 +146,11 @@ __device__ __forceinline__ double push_into_bounds(int kind, double v) {
   return v;
 }
 
-template <class TB, class TF>
-__global__ void init_kernel(const Params* __restrict__ P, int first, int count,
-                            const double* __restrict__ guess, const double* __restrict__ yguess) {
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (gw >= count) return;
-  const int slot = first + gw;
+// Resets one slot to the starting point of the problem whose theta the slot
+// holds (warp-level; lanes stride 32).  guess / yguess: optional primal /
+// multiplier rows.  Returns the fresh state record (identical in all lanes).
+__device__ __forceinline__ SlotState init_slot(const Params* P, int slot, int lane,
+                                               const double* guess, const double* yguess) {
   const Dims& d = P->d;
   const Layout& L = P->L;
   double* f = P->f64 + (long long)slot * L.slot_f64;
@@ -116,7 +163,7 @@ __global__ void init_kernel(const Params* __restrict__ P, int first, int count,
     VarInfo vi = var_info(d, i);
     double v;
     if (guess) {
-      v = guess[(long long)gw * d.n + i];
+      v = guess[i];
     } else if (vi.loc < d.nx) {
       v = th[d.th_x + vi.loc];
     } else if (vi.kind == VK_BOX) {
@@ -136,25 +183,87 @@ __global__ void init_kernel(const Params* __restrict__ P, int first, int count,
     zl[d.n + i] = 0.0;
     zu[d.n + i] = 0.0;
   }
-  for (int i = lane; i < d.m; i += 32) y[i] = yguess ? yguess[(long long)gw * d.m + i] : 0.0;
-  if (lane == 0) {
-    SlotState S;
-    memset(&S, 0, sizeof(S));
-    S.status = BIPM_RUNNING;
-    S.mode = MODE_NORMAL;
-    S.need_init = 1;
-    S.need_y_ls = yguess ? 0 : 1;
-    S.mu = P->opt.mu_init;
-    S.problem_id = slot;
-    P->st[slot] = S;
+  for (int i = lane; i < d.m; i += 32) y[i] = yguess ? yguess[i] : 0.0;
+  for (int i = lane; i < (d.N + 1) * d.nx; i += 32) {
+    int kk = i / d.nx, c = i - kk * d.nx;
+    f[L.xref + i] = ref_value(th, d, kk, c / 12, c - 12 * (c / 12));
   }
+  __syncwarp();
+  SlotState S;
+  memset(&S, 0, sizeof(S));
+  S.status = BIPM_RUNNING;
+  S.mode = MODE_NORMAL;
+  S.need_init = 1;
+  S.need_y_ls = yguess ? 0 : 1;
+  S.mu = P->opt.mu_init;
+  S.problem_id = slot;
+  return S;
 }
 
+template <class TB, class TF>
+__global__ void init_kernel(const Params* __restrict__ P, int first, int count,
+                            const double* __restrict__ guess, const double* __restrict__ yguess) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= count) return;
+  const int slot = first + gw;
+  SlotState S = init_slot(P, slot, lane, guess ? guess + (long long)gw * P->d.n : nullptr,
+                          yguess ? yguess + (long long)gw * P->d.m : nullptr);
+  if (lane == 0) P->st[slot] = S;
+}
+
+// Iteration-level batching over a queue (Sec. V): each warp owns one slot;
+// when its problem terminates it writes the problem's results and refills the
+// slot with the next problem of the queue, so no slot idles while the queue
+// holds work.
+template <class TB, class TF>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+    queue_kernel(const Params* __restrict__ P, const double* __restrict__ theta_q, int n_queue,
+                 int n_warps, double* __restrict__ x_out, bipm_result* __restrict__ res_out) {
+  extern __shared__ __align__(16) char smem_all[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int slot = blockIdx.x * kWarpsPerBlock + warp;  // this warp's slot
+  if (slot >= n_warps) return;
+  char* smem = smem_all + (size_t)warp * P->smem_per_warp;
+  const Dims& d = P->d;
+  while (true) {
+    int id = 0;
+    if (lane == 0) id = atomicAdd(P->work_counter, 1);
+    id = __shfl_sync(0xffffffffu, id, 0);
+    if (id >= n_queue) break;
+    double* th = P->theta + (long long)slot * d.n_theta;
+    for (int i = lane; i < d.n_theta; i += 32) th[i] = theta_q[(long long)id * d.n_theta + i];
+    __syncwarp();
+    SlotState S = init_slot(P, slot, lane, nullptr, nullptr);
+    S.problem_id = id;
+    Ctx<TB, TF> c;
+    make_ctx(c, P, slot, lane, 32, nullptr, smem);
+    run_slot(c, S, 0, 0);
+    const double* w = c.f + P->L.x;
+    if (x_out)
+      for (int i = lane; i < d.n; i += 32) x_out[(long long)id * d.n + i] = w[i];
+    if (lane == 0) {
+      bipm_result r;
+      r.status = S.status;
+      r.iters = S.iter;
+      r.obj = S.obj;
+      r.kkt_err = S.kkt;
+      res_out[id] = r;
+      P->st[slot] = S;
+    }
+    __syncwarp();
+  }
+}
 
 // host-side accessors of the kernel entry points of one precision
 void* iter_kernel_f64();
 void* init_kernel_f64();
+void* queue_kernel_f64();
+void* queue_kernel_f32();
+void* block_kernel_f64();
 void* iter_kernel_f32();
 void* init_kernel_f32();
+void* block_kernel_f32();
 
 }  // namespace bipm

@@ -4,4 +4,5 @@
 namespace bipm {
 void* iter_kernel_f64() { return (void*)ipm_kernel<double, double>; }
 void* init_kernel_f64() { return (void*)init_kernel<double, double>; }
+void* queue_kernel_f64() { return (void*)queue_kernel<double, double>; }
 }  // namespace bipm

@@ -1,0 +1,6 @@
+// FP64 factorisation instantiation of the block-team kernel.
+#include "kernels.cuh"
+
+namespace bipm {
+void* block_kernel_f64() { return (void*)ipm_block_kernel<double, double>; }
+}  // namespace bipm

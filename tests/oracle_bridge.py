@@ -8,6 +8,7 @@ test (Sec. VI, Eq. 8).
 from __future__ import annotations
 
 import multiprocessing as mp
+import os
 
 import numpy as np
 
@@ -55,8 +56,15 @@ def e_v(v, v_ref) -> float:
     return float(np.max(np.abs(v - v_ref) / (1.0 + np.abs(v_ref))))
 
 
+def _single_thread():
+    import torch
+
+    torch.set_num_threads(1)
+
+
 def _solve_one(args):
     desc, theta, record, opt_kw = args
+    _single_thread()
     nlp = QuadNLP(desc, theta)
     opt = ipm.Options(**opt_kw)
     st, hist = ipm.solve(nlp, opt=opt, record=record)
@@ -76,5 +84,32 @@ def oracle_solve_batch(desc, theta, record=False, processes=None, **opt_kw):
     if processes == 1 or len(jobs) <= 1:
         return [_solve_one(j) for j in jobs]
     ctx = mp.get_context("spawn")
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"  # one thread per worker process
     with ctx.Pool(processes=processes or min(len(jobs), mp.cpu_count())) as pool:
         return pool.map(_solve_one, jobs)
+
+
+def straight_line_guess(desc, theta):
+    """A deliberately poor primal starting point: positions on the straight line
+    from the start to the goal (through any obstacle on the way), zero velocity
+    and attitude, hover thrust, zero slacks.  Input construction only."""
+    from workloads import theta_layout
+
+    lay = theta_layout(desc)
+    nq, N, nx, nu, ni = desc.nq, desc.horizon, desc.nx, desc.nu, desc.ni
+    x0 = np.zeros(desc.n)
+    pos = 0
+    for k in range(N + 1):
+        t = k / N
+        for q in range(nq):
+            p0 = theta[lay["xbar"] + 12 * q:lay["xbar"] + 12 * q + 3]
+            goal = theta[lay["ref"] + 6 * q:lay["ref"] + 6 * q + 3]
+            x0[pos + 12 * q:pos + 12 * q + 3] = (1 - t) * p0 + t * goal
+        pos += nx
+        if k < N:
+            x0[pos:pos + nu] = 0.5 * 9.81 / 4.0
+            pos += nu
+        if k >= 1:
+            pos += ni
+    return x0
