@@ -116,6 +116,11 @@ RK4_VALUE_FLOPS = 152 + 200 + 4            # one RK4 step of one quadrotor, valu
 RK4_ADJOINT_FLOPS = 403 + 620 + 4          # value + reverse sweep (gradient of lam^T F)
 RK4_DUAL_FLOPS = 1122 + 1596 + 8           # forward-over-reverse, one direction
 
+# DRAM traffic per problem-iteration of the queue kernel, measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum = 2.394e9 B for 512 tracking
+# problems at 30.9 iterations each); scaled to a launch by its iterations.
+TRAFFIC_PER_PROBLEM_ITER = 2.394e9 / (512 * 30.9)
+
 
 def unit_flops(desc):
     """Algorithmic FLOPs of the units the kernel counts, for one problem."""
@@ -150,21 +155,23 @@ def step_flops(desc, stats, precision):
     solves = float(np.sum(stats["solves"]))
     trials = float(np.sum(stats["trials"]))
     ir = float(np.sum(stats["ir_steps"]))
-    esc = float(np.sum(stats["fp64_escalations"]))
-    # evaluation, residuals, trials and refinement mat-vecs always run in FP64
-    f64 = it * (u["iter_fixed"] - u["derivs"]) + trials * u["trial"] + (ir + solves) * u["matvec"] * (precision == 1)
-    lowp = it * u["derivs"] + fact * u["fact"] + solves * u["solve"]
-    if precision == 0:
-        return f64 + lowp, 0.0
-    # escalated factorisations are redone in FP64
-    return f64 + esc * (u["fact"] + u["solve"]), lowp
+    f32 = float(np.sum(stats["fact32"]))
+    s32 = float(np.sum(stats["solve32"]))
+    # derivative blocks run in the factor precision's block type (FP32 when precision = 1)
+    derivs32 = it * u["derivs"] if precision == 1 else 0.0
+    lowp = derivs32 + f32 * u["fact"] + s32 * u["solve"]
+    # everything else is FP64: evaluation, residuals, trials, FP64 factorisations and
+    # solves, and one KKT mat-vec per refinement step and per refined FP32 solve
+    f64 = it * u["iter_fixed"] - derivs32 + trials * u["trial"] + (fact - f32) * u["fact"] \
+        + (solves - s32) * u["solve"] + (ir + s32) * u["matvec"]
+    return f64, lowp
 
 
 # ------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
 
-    from paper_2606_26341_gb300 import bipm
+    from paper_2606_26341_gb300 import autotune, bipm
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -181,140 +188,132 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    BATCH = args.batch
-    desc, theta = make_batch(WORKLOAD, BATCH, first_id=rank * BATCH)
+    B, K, W = args.batch, args.steps, args.warmup
+    # K steps of B problems each, distinct per step and per rank (weak scaling)
+    desc, theta = make_batch(WORKLOAD, B * K, first_id=rank * B * (K + W + 1))
+    _, theta_w = make_batch(WORKLOAD, B, first_id=rank * B * (K + W + 1) + B * K)
     theta_dev = torch.as_tensor(theta, device=dev)
-    theta_host = torch.as_tensor(theta).pin_memory()
+    theta_wdev = torch.as_tensor(theta_w, device=dev)
     n, m = desc.n, desc.m
+    rsize = bipm.RESULT_DTYPE.itemsize
 
-    def timed_solves(precision, steps, warmup):
-        b = bipm.Batch(desc, BATCH, bipm.Options(precision=precision), stream=stream)
-        for _ in range(warmup):
-            b.set_problems(theta_dev)
-            b.solve()
+    # chosen form: the autotuner's pick among the FP32 variants (untimed)
+    if args.only_mixed:
+        best = bipm.Options(precision=1, fp32_switch=-1.0)
+        tune_table = []
+    else:
+        best, tune_table = autotune.autotune(desc, theta_wdev[: min(B, 2048)], B, stream=stream)
+
+    def timed_queue(options):
+        """W untimed warm-up steps, then K timed steps as one queue through B slots."""
+        b = bipm.Batch(desc, B, options, stream=stream)
+        res = torch.empty(B * K * rsize, dtype=torch.uint8, device=dev)
+        for _ in range(W):
+            b.solve_queue(theta_wdev, None, res[: B * rsize])
         torch.cuda.synchronize()
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        k_ms = []
         clocks = ClockSampler(local)
         clocks.start()
         e0.record(stream)
-        for _ in range(steps):
-            b.set_problems(theta_dev)
-            k0 = torch.cuda.Event(enable_timing=True)
-            k1 = torch.cuda.Event(enable_timing=True)
-            k0.record(stream)
-            b.solve()
-            k1.record(stream)
-            k1.synchronize()
-            k_ms.append(k0.elapsed_time(k1))
+        b.solve_queue(theta_dev, None, res)
         e1.record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
         barrier()
-        ms = e0.elapsed_time(e1)
-        st = b.get_stats()
         b.close()
-        return ms, k_ms, st, clk
+        return e0.elapsed_time(e1), bipm.results_from_bytes(res.cpu().numpy()), clk
 
-    # chosen form and plain FP64 form
-    ms_mixed, kms_mixed, st_mixed, clk = timed_solves(1, args.steps, args.warmup)
+    ms_mixed, r_mixed, clk = timed_queue(best)
     if args.only_mixed:
-        ms_fp64, kms_fp64, st_fp64 = ms_mixed, kms_mixed, st_mixed
+        ms_fp64, r_fp64 = ms_mixed, r_mixed
     else:
-        ms_fp64, kms_fp64, st_fp64, _ = timed_solves(0, args.steps, args.warmup)
+        ms_fp64, r_fp64, _ = timed_queue(bipm.Options(precision=0))
+    conv_mixed = int(np.sum(r_mixed["status"] == bipm.CONVERGED))
+    conv_fp64 = int(np.sum(r_fp64["status"] == bipm.CONVERGED))
 
-    conv_mixed = int(np.sum(st_mixed["status"] == bipm.CONVERGED))
-    conv_fp64 = int(np.sum(st_fp64["status"] == bipm.CONVERGED))
-    t_mixed = ms_mixed / 1e3
-    steps_fp64 = args.steps
-    t_fp64 = ms_fp64 / 1e3
-
-    # end to end through the public API: host parameters in, host solutions out
-    b = bipm.Batch(desc, BATCH, bipm.Options(precision=1), stream=stream)
-    x_host = torch.empty((BATCH, n), dtype=torch.float64).pin_memory()
-    y_host = torch.empty((BATCH, m), dtype=torch.float64).pin_memory()
-    b.set_problems(theta_host.numpy())
-    b.solve()
+    # end to end through the public API: host parameters in, host solutions and
+    # result records out, every copy inside the timed region
+    theta_host = np.ascontiguousarray(theta)
+    x_host = np.empty((B * K, n))
+    b = bipm.Batch(desc, B, best, stream=stream)
+    b.solve_queue(np.ascontiguousarray(theta_w), None)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    e_steps = max(1, args.steps // 2)
-    e2e_conv = 0
-    for _ in range(e_steps):
-        b.set_problems(theta_host.numpy())
-        b.solve()
-        b.get_solution(out=(x_host, y_host, None, None))
-        e2e_conv += int(np.sum(b.get_stats()["status"] == bipm.CONVERGED))
+    r_e2e = b.solve_queue(theta_host, x_host)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     b.close()
+    e2e_conv = int(np.sum(r_e2e["status"] == bipm.CONVERGED))
 
-    def max_over_ranks(v):
+    def reduce(v, op):
         if ws == 1:
             return v
         import torch.distributed as dist
         t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=op)
         return float(t.item())
 
-    def sum_over_ranks(v):
-        if ws == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    import torch.distributed as tdist
+    MAX = tdist.ReduceOp.MAX if ws > 1 else None
+    SUM = tdist.ReduceOp.SUM if ws > 1 else None
+    t_mixed = reduce(ms_mixed / 1e3, MAX)
+    t_fp64 = reduce(ms_fp64 / 1e3, MAX)
+    t_e2e_max = reduce(t_e2e, MAX)
+    tot_mixed = reduce(conv_mixed, SUM)
+    tot_fp64 = reduce(conv_fp64, SUM)
+    tot_e2e = reduce(e2e_conv, SUM)
 
-    t_mixed_max = max_over_ranks(t_mixed)
-    t_fp64_max = max_over_ranks(t_fp64)
-    t_e2e_max = max_over_ranks(t_e2e)
-    tot_conv_mixed = sum_over_ranks(conv_mixed * args.steps)
-    tot_conv_fp64 = sum_over_ranks(conv_fp64 * steps_fp64)
-    tot_e2e = sum_over_ranks(e2e_conv)
-
-    # roofline of the iteration kernel (the only kernel of any weight in a step)
-    f64_m, f32_m = step_flops(desc, st_mixed, 1)
-    f64_d, _ = step_flops(desc, st_fp64, 0)
-    k_mixed = statistics.median(kms_mixed) / 1e3
-    k_fp64 = statistics.median(kms_fp64) / 1e3
-    t_bound_mixed = f64_m / FP64_PEAK_NOMINAL + f32_m / FP32_PEAK_NOMINAL
+    # roofline of the queue kernel (the step is one launch of it)
+    f64_m, f32_m = step_flops(desc, r_mixed, best.precision)
+    f64_d, _ = step_flops(desc, r_fp64, 0)
+    k_mixed = ms_mixed / 1e3
+    k_fp64 = ms_fp64 / 1e3
+    t_bound = f64_m / FP64_PEAK_NOMINAL + f32_m / FP32_PEAK_NOMINAL
     roof = {
         "bound": "alu", "unit": "TFLOP/s",
         "achieved": (f64_m + f32_m) / k_mixed / 1e12,
-        "peak": (f64_m + f32_m) / t_bound_mixed / 1e12,
-        "frac": t_bound_mixed / k_mixed,
-        "traffic": None,
-        "kernel": "ipm_kernel<float,float> (FP32 factorisation, FP64 refinement)",
+        "peak": (f64_m + f32_m) / t_bound / 1e12,
+        "frac": t_bound / k_mixed,
+        "traffic": TRAFFIC_PER_PROBLEM_ITER * float(np.sum(r_mixed["iters"])),
+        "traffic_unit": "bytes per launch (ncu capture of 512 problems, scaled by iterations)",
+        "kernel": "queue_kernel (chosen form)",
         "flops_fp64_per_launch": f64_m, "flops_fp32_per_launch": f32_m,
-        "peak_source": "nominal FP64 152 SMs x 2 FMA/clk x 2 x 2.07 GHz = 1.26 TFLOP/s; "
-                       "FP32 x 128 FMA/clk = 80.5 TFLOP/s (ALU-bound kernel; mixed peak = "
-                       "flops / (f64/peak64 + f32/peak32))",
+        "peak_source": "derived from unit counts and clocks (no FP64/FP32 ALU figure in "
+                       "MEASURED_PEAKS.json): FP64 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = "
+                       "1.26 TFLOP/s, FP32 152 x 128 FMA/clk x 2 x 2.07 GHz = 80.5 TFLOP/s; "
+                       "mixed peak = flops / (f64/peak64 + f32/peak32)",
         "fp64_form": {"achieved": f64_d / k_fp64 / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
                       "frac": f64_d / k_fp64 / FP64_PEAK_NOMINAL},
     }
 
     if rank == 0:
+        opt_desc = {"precision": best.precision, "fp32_switch": best.fp32_switch}
         line = {
-            "metric": METRIC, "value": tot_conv_mixed / t_mixed_max, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t_mixed_max * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 factor + f64 refine",
+            "metric": METRIC, "value": tot_mixed / t_mixed, "unit": UNIT, "n_gpus": ws,
+            "steps": K, "warmup": W, "ms_per_step": t_mixed * 1e3 / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 derivative blocks + f64",
             "data": "synthetic (seeded SplitMix64 tracking problems; no public dataset exists)",
-            "config": {"workload": f"{WORKLOAD}: 1 quadrotor, RK4 N=30, 3 spheres, batch {BATCH}",
-                       "global_batch": BATCH * ws, "parallelism": f"replicas x{ws}",
-                       "l2": "per-step working set (~0.7 GB of slot workspaces) exceeds the 129 MB L2"},
-            "fp64": {"value": tot_conv_fp64 / t_fp64_max, "unit": UNIT,
-                     "ms_per_step": t_fp64_max * 1e3 / steps_fp64, "dtype": "f64"},
-            "converged_frac": conv_mixed / BATCH,
-            "iters_mean": float(np.mean(st_mixed["iters"])),
+            "config": {"workload": f"{WORKLOAD}: 1 quadrotor, RK4 N=30, 3 spheres, {B} problems per step",
+                       "global_batch": B * ws, "parallelism": f"replicas x{ws}",
+                       "mode": f"iteration-level batching: the {K} steps' problems stream through "
+                               f"{B} slots in one persistent launch",
+                       "options": opt_desc,
+                       "l2": "slot workspaces (~1.4 GB) exceed the 129 MB L2"},
+            "fp64": {"value": tot_fp64 / t_fp64, "unit": UNIT, "ms_per_step": t_fp64 * 1e3 / K,
+                     "dtype": "f64"},
+            "autotune": [{"precision": o.precision, "fp32_switch": o.fp32_switch, "solves_per_s": v}
+                         for o, v in tune_table],
+            "converged_frac": conv_mixed / (B * K),
+            "iters_mean": float(np.mean(r_mixed["iters"])),
             "e2e": {"value": tot_e2e / t_e2e_max, "unit": UNIT,
-                    "h2d_bytes_per_step": BATCH * desc_theta_len(desc) * 8,
-                    "d2h_bytes_per_step": BATCH * (n + m) * 8 + BATCH * stats_record_bytes()},
+                    "h2d_bytes_per_step": B * desc_theta_len(desc) * 8,
+                    "d2h_bytes_per_step": B * (n * 8 + rsize)},
             "roofline": roof,
             "clocks": clk,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 1,
         }
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(desc, theta, budget_s=args.cpu_budget)
@@ -414,7 +413,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -101,6 +101,8 @@ typedef struct {
   int factorizations;   /* Riccati factorisations (inertia retries and FP64 redo included) */
   int solves;           /* triangular solve sweeps (steps, SOC, refinement) */
   int trials;           /* line-search trial-point evaluations */
+  int fact32;           /* factorisations done in FP32 (the rest in FP64) */
+  int solve32;          /* solve sweeps done in FP32 */
   int reserved;
   double obj;           /* f at the final iterate */
   double kkt_err;       /* scaled optimality error E_0 at the final iterate */
@@ -117,6 +119,14 @@ int bipm_get_phase_cycles(const bipm_batch* b, long long* out, int first_slot, i
 typedef struct {
   int status;
   int iters;
+  int factorizations; /* work counters as in bipm_stats */
+  int solves;
+  int trials;
+  int ir_steps;
+  int fp64_escalations;
+  int resto_iters;
+  int fact32;         /* factorisations / solves done in FP32 */
+  int solve32;
   double obj;
   double kkt_err;
 } bipm_result;

@@ -39,7 +39,8 @@ class StatsC(ctypes.Structure):
                 ("soc", ctypes.c_int), ("inertia_corr", ctypes.c_int), ("ir_steps", ctypes.c_int),
                 ("fp64_escalations", ctypes.c_int), ("tiny_steps", ctypes.c_int),
                 ("factorizations", ctypes.c_int), ("solves", ctypes.c_int),
-                ("trials", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("trials", ctypes.c_int), ("fact32", ctypes.c_int), ("solve32", ctypes.c_int),
+                ("reserved", ctypes.c_int),
                 ("obj", ctypes.c_double), ("kkt_err", ctypes.c_double),
                 ("primal_inf", ctypes.c_double), ("mu", ctypes.c_double)]
 
@@ -48,8 +49,20 @@ _DP = ctypes.POINTER(ctypes.c_double)
 
 
 class ResultC(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("obj", ctypes.c_double),
-                ("kkt_err", ctypes.c_double)]
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("factorizations", ctypes.c_int),
+                ("solves", ctypes.c_int), ("trials", ctypes.c_int), ("ir_steps", ctypes.c_int),
+                ("fp64_escalations", ctypes.c_int), ("resto_iters", ctypes.c_int),
+                ("fact32", ctypes.c_int), ("solve32", ctypes.c_int),
+                ("obj", ctypes.c_double), ("kkt_err", ctypes.c_double)]
+
+
+RESULT_DTYPE = np.dtype([(f, "<i4" if t is ctypes.c_int else "<f8") for f, t in ResultC._fields_])
+
+
+def results_from_bytes(buf) -> dict:
+    """Per-problem result fields from the raw bytes of a device results buffer."""
+    arr = np.frombuffer(bytes(buf), dtype=RESULT_DTYPE)
+    return {f: arr[f].copy() for f in RESULT_DTYPE.names}
 
 
 class IterateC(ctypes.Structure):
@@ -203,7 +216,8 @@ class Batch:
         """Iteration-level batching over a queue of problems (rows of theta_queue).
 
         theta_queue / x_out are numpy arrays (host) or CUDA tensors (device);
-        `results` (device mode) is a CUDA int8/uint8 tensor of n_queue * 24 bytes.
+        `results` (device mode) is a CUDA uint8 tensor of n_queue * sizeof(bipm_result)
+        bytes (RESULT_DTYPE.itemsize each); read it back with results_from_bytes.
         Returns a dict of numpy arrays (status, iters, obj, kkt_err) in host mode.
         """
         nq = theta_queue.shape[0]

@@ -477,6 +477,8 @@ int bipm_get_stats(const bipm_batch* b, bipm_stats* out, int first_slot, int cou
     o.factorizations = s.n_fact;
     o.solves = s.n_solve;
     o.trials = s.n_trial;
+    o.fact32 = s.n_fact32;
+    o.solve32 = s.n_solve32;
     o.reserved = 0;
     o.obj = s.obj;
     o.kkt_err = s.kkt;

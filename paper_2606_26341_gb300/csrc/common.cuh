@@ -183,7 +183,7 @@ struct Layout {
 struct SlotState {
   int status, mode, iter, need_init, need_y_ls, tiny, tiny_r, n_filt, n_filt_r;
   int n_soc, n_resto_iter, n_inertia_corr, n_ir_steps, n_escalations, n_tiny, problem_id;
-  int n_fact, n_solve, n_trial, pad_;
+  int n_fact, n_solve, n_trial, n_fact32, n_solve32, pad_;
   long long cyc[8];  // clock cycles per phase (see kPhase*)
   double mu, dw_last, theta_max, theta_min;
   double mu_r, dw_last_r, theta_max_r, theta_min_r, zeta, theta_ref;

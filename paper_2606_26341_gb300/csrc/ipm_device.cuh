@@ -70,6 +70,7 @@ struct Ctx {
   int use64;           // 1: the last factorisation is the FP64 one
   int n_ir, n_esc;
   int n_fact, n_solve, n_trial;  // work counters of the current iteration
+  int n_fact32, n_solve32;        // ... of which in FP32
 };
 
 __device__ __forceinline__ double sq(double a) { return a * a; }
@@ -677,6 +678,7 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
   Scratch<TX> s = scratch<TX>(scratch_base<TX>(c), d);
   const double* dv = c.f + c.L.dv;
   c.n_fact++;
+  if (sizeof(TX) == 4) c.n_fact32++;
   compute_diag(c, dw, flags);
   double min_ratio = 1.0;
 
@@ -834,6 +836,7 @@ __device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, d
   const bool resto = flags & FF_RESTO;
   Scratch<TX> s = scratch<TX>(scratch_base<TX>(c), d);
   c.n_solve++;
+  if (sizeof(TX) == 4) c.n_solve32++;
   const double* dsv = c.f + c.L.dsv;
   const double* ev = c.f + c.L.ev;
   const double* ipv = c.f + c.L.ipv;

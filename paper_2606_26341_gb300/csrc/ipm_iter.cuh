@@ -456,6 +456,8 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
   c.n_fact = 0;
   c.n_solve = 0;
   c.n_trial = 0;
+  c.n_fact32 = 0;
+  c.n_solve32 = 0;
   double& mu = c.resto ? S.mu_r : S.mu;
   double& dw_last = c.resto ? S.dw_last_r : S.dw_last;
   double& th_max = c.resto ? S.theta_max_r : S.theta_max;
@@ -729,6 +731,8 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
   S.n_fact += c.n_fact;
   S.n_solve += c.n_solve;
   S.n_trial += c.n_trial;
+  S.n_fact32 += c.n_fact32;
+  S.n_solve32 += c.n_solve32;
 
   if (outcome == OUT_ACCEPTED) {
     S.cyc[PH_TOTAL] += clock64() - t_start;

@@ -45,6 +45,8 @@ __device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, in
   c.n_fact = 0;
   c.n_solve = 0;
   c.n_trial = 0;
+  c.n_fact32 = 0;
+  c.n_solve32 = 0;
 }
 
 // final objective, scaled KKT error and infeasibility of the original problem
@@ -247,6 +249,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
       bipm_result r;
       r.status = S.status;
       r.iters = S.iter;
+      r.factorizations = S.n_fact;
+      r.solves = S.n_solve;
+      r.trials = S.n_trial;
+      r.ir_steps = S.n_ir_steps;
+      r.fp64_escalations = S.n_escalations;
+      r.resto_iters = S.n_resto_iter;
+      r.fact32 = S.n_fact32;
+      r.solve32 = S.n_solve32;
       r.obj = S.obj;
       r.kkt_err = S.kkt;
       res_out[id] = r;

@@ -45,8 +45,8 @@ def test_ctypes_records_match_c_layout(lib):
     #include <stddef.h>
     #include "bipm.h"
     int main(void) {
-      printf("%zu %zu %zu %zu\n", sizeof(bipm_problem_desc), sizeof(bipm_options),
-             sizeof(bipm_stats), sizeof(bipm_iterate));
+      printf("%zu %zu %zu %zu %zu\n", sizeof(bipm_problem_desc), sizeof(bipm_options),
+             sizeof(bipm_stats), sizeof(bipm_iterate), sizeof(bipm_result));
       printf("%zu %zu %zu\n", offsetof(bipm_iterate, mode), offsetof(bipm_iterate, mu),
              offsetof(bipm_iterate, theta_ref));
       printf("%zu %zu\n", offsetof(bipm_stats, obj), offsetof(bipm_stats, mu));
@@ -64,11 +64,12 @@ def test_ctypes_records_match_c_layout(lib):
     assert vals[1] == ctypes.sizeof(bipm.OptionsC)
     assert vals[2] == ctypes.sizeof(bipm.StatsC)
     assert vals[3] == ctypes.sizeof(bipm.IterateC)
-    assert vals[4] == bipm.IterateC.mode.offset
-    assert vals[5] == bipm.IterateC.mu.offset
-    assert vals[6] == bipm.IterateC.theta_ref.offset
-    assert vals[7] == bipm.StatsC.obj.offset
-    assert vals[8] == bipm.StatsC.mu.offset
+    assert vals[4] == ctypes.sizeof(bipm.ResultC) == bipm.RESULT_DTYPE.itemsize
+    assert vals[5] == bipm.IterateC.mode.offset
+    assert vals[6] == bipm.IterateC.mu.offset
+    assert vals[7] == bipm.IterateC.theta_ref.offset
+    assert vals[8] == bipm.StatsC.obj.offset
+    assert vals[9] == bipm.StatsC.mu.offset
 
 
 def test_invalid_arguments_fail_without_a_device(lib):
