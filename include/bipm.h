@@ -196,6 +196,34 @@ int bipm_solve(bipm_batch* b);
 int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, double* x_out,
                      bipm_result* results, int on_device);
 
+/* One-shot solve that allocates nothing (the paper has no counterpart; this
+ * is an addition for callers that cannot allocate device memory when they
+ * need a solve: code inside a CUDA stream capture, where cudaMalloc is not
+ * permitted, real-time loops that must stay out of the allocator, and
+ * processes whose device memory budget is fixed in advance).
+ *
+ * Solves `count` problems of structure `desc` (theta: count x n_theta) with
+ * the same queue (iteration-level batching) kernel as bipm_solve_queue, but
+ * with the whole workspace in one 64 MiB file-scope __device__ array of the
+ * library instead of memory owned by a batch.  Every GPU that loads the
+ * library holds that array until the process exits.  theta, x_out
+ * (count x n, may be NULL) and results (count records) are DEVICE pointers;
+ * nothing is allocated or freed (no cudaMalloc, no cudaFree, no allocating
+ * library call).  The number of problems solved concurrently is what fits in
+ * the array (at least one); a problem whose workspace alone exceeds 64 MiB
+ * is rejected with BIPM_EINVAL and a message naming both sizes.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (with it current); make that first call before any stream capture.
+ * All calls share the array and find the previous call's contents in it; the
+ * call resets what must start afresh (the queue counter and each problem's
+ * slot), but calls that overlap on the GPU (other streams, other threads)
+ * race on the array and must be serialised by the caller.  `cuda_stream` is
+ * the stream to run on (NULL = default); the call returns when the solve has
+ * finished.  Errors as for the other calls (bipm_last_error). */
+int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, const double* theta,
+                      int count, double* x_out, bipm_result* results, void* cuda_stream);
+
 /* Runs exactly `n_iterations` iterations on every running slot. */
 int bipm_step(bipm_batch* b, int n_iterations);
 

@@ -80,8 +80,8 @@ class IterateC(ctypes.Structure):
 
 EXPORTS = ["bipm_create_batch", "bipm_dims", "bipm_set_problems", "bipm_set_initial_guess",
            "bipm_solve", "bipm_step", "bipm_get_solution", "bipm_get_stats", "bipm_get_iterate",
-           "bipm_set_iterate", "bipm_get_phase_cycles", "bipm_solve_queue", "bipm_last_error",
-           "bipm_destroy"]
+           "bipm_set_iterate", "bipm_get_phase_cycles", "bipm_solve_queue", "bipm_solve_static",
+           "bipm_last_error", "bipm_destroy"]
 PHASES = ["eval", "derivs", "factor", "solve", "line_search", "other", "lsq_mult", "total"]
 
 _LIB = None
@@ -114,6 +114,8 @@ def load_library(build_if_missing: bool = True):
     lib.bipm_set_iterate.argtypes = [vp, i, ctypes.POINTER(IterateC)]
     lib.bipm_get_phase_cycles.argtypes = [vp, vp, i, i]
     lib.bipm_solve_queue.argtypes = [vp, vp, i, vp, vp, i]
+    lib.bipm_solve_static.argtypes = [ctypes.POINTER(ProblemDescC), ctypes.POINTER(OptionsC), vp, i,
+                                      vp, vp, vp]
     lib.bipm_last_error.restype = ctypes.c_char_p
     lib.bipm_destroy.argtypes = [vp]
     lib.bipm_destroy.restype = None
@@ -126,6 +128,28 @@ def load_library(build_if_missing: bool = True):
 
 class BipmError(RuntimeError):
     pass
+
+
+def solve_static(desc, theta_dev, x_out=None, results=None, options: "Options | None" = None,
+                 stream=None):
+    """bipm_solve_static: solve the rows of theta_dev (CUDA float64 tensor) with the
+    library's fixed static workspace (no device allocation by the library).
+
+    x_out: optional CUDA float64 tensor (count x n); results: CUDA uint8 tensor of
+    count * RESULT_DTYPE.itemsize bytes (read back with results_from_bytes)."""
+    lib = load_library()
+    d = ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist)
+    o = options or Options()
+    oc = OptionsC(o.tol, o.max_iter, o.mu_init, o.precision, o.schedule, o.fp32_switch)
+    sp = None
+    if stream is not None:
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    pt, dev = _ptr(theta_dev)
+    px, _ = _ptr(x_out)
+    if not dev or results is None:
+        raise ValueError("solve_static takes CUDA tensors (theta, results)")
+    _check(lib.bipm_solve_static(ctypes.byref(d), ctypes.byref(oc), pt, theta_dev.shape[0], px,
+                                 ctypes.c_void_p(results.data_ptr()), sp))
 
 
 def _check(rc):

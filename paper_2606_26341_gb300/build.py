@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIBNAME = "libbipm.so"
-UNITS = ["bipm.cu", "kernels_f64.cu", "kernels_f32.cu", "kernels_f64_block.cu", "kernels_f32_block.cu"]
+UNITS = ["bipm.cu", "kernels_f64.cu", "kernels_f32.cu", "kernels_f64_block.cu", "kernels_f32_block.cu",
+         "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + INCLUDE]

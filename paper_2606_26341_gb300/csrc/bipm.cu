@@ -32,6 +32,11 @@ int fail(int code, const std::string& msg) {
 
 }  // namespace
 
+namespace bipm {
+// records the message bipm_last_error() returns (used by every entry point)
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace bipm
+
 struct bipm_batch {
   bipm_problem_desc desc;
   Dims d;
@@ -55,21 +60,7 @@ struct bipm_batch {
   int loaded = 0;
 };
 
-namespace {
-
-__global__ void gather_kernel(const Params* __restrict__ P, int first, int count, long long off,
-                              int len, double* __restrict__ out) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)count * len) return;
-  int j = (int)(t / len), i = (int)(t - (t / len) * len);
-  out[t] = P->f64[(long long)(first + j) * P->L.slot_f64 + off + i];
-}
-
-// ------------------------------------------------------------- host helpers
-void* iter_kernel_ptr(int precision) { return precision ? iter_kernel_f32() : iter_kernel_f64(); }
-void* init_kernel_ptr(int precision) { return precision ? init_kernel_f32() : init_kernel_f64(); }
-void* block_kernel_ptr(int precision) { return precision ? block_kernel_f32() : block_kernel_f64(); }
-void* queue_kernel_ptr(int precision) { return precision ? queue_kernel_f32() : queue_kernel_f64(); }
+namespace bipm {
 
 Layout make_layout(const Dims& d, int precision) {
   Layout L;
@@ -140,6 +131,24 @@ Layout make_layout(const Dims& d, int precision) {
   L.slot_tb = bo;
   return L;
 }
+
+}  // namespace bipm
+
+namespace {
+
+__global__ void gather_kernel(const Params* __restrict__ P, int first, int count, long long off,
+                              int len, double* __restrict__ out) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)count * len) return;
+  int j = (int)(t / len), i = (int)(t - (t / len) * len);
+  out[t] = P->f64[(long long)(first + j) * P->L.slot_f64 + off + i];
+}
+
+// ------------------------------------------------------------- host helpers
+void* iter_kernel_ptr(int precision) { return precision ? iter_kernel_f32() : iter_kernel_f64(); }
+void* init_kernel_ptr(int precision) { return precision ? init_kernel_f32() : init_kernel_f64(); }
+void* block_kernel_ptr(int precision) { return precision ? block_kernel_f32() : block_kernel_f64(); }
+void* queue_kernel_ptr(int precision) { return precision ? queue_kernel_f32() : queue_kernel_f64(); }
 
 int check_slots(const bipm_batch* b, int first, int count) {
   if (!b) return fail(BIPM_EINVAL, "null batch");

@@ -266,6 +266,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
   }
 }
 
+// offsets of the per-slot arrays for problems of dims d (host)
+Layout make_layout(const Dims& d, int precision);
+
 // host-side accessors of the kernel entry points of one precision
 void* iter_kernel_f64();
 void* init_kernel_f64();
