@@ -76,8 +76,12 @@ typedef struct {
   double tol;         /* scaled KKT tolerance E_0 (default 1e-6) */
   int max_iter;       /* iteration cap, restoration iterations included (500) */
   double mu_init;     /* initial barrier parameter (0.1) */
-  int precision;      /* 0: FP64 factorisation; 1: FP32 factorisation with FP64
-                         iterative refinement of the Newton step */
+  int precision;      /* 0: FP64 throughout; 1: FP32 derivative blocks and FP32
+                         factorisation with FP64 iterative refinement of the
+                         Newton step (see fp32_switch); 2: FP32 derivative
+                         blocks, double-float (two-FP32, ~48-bit) factorisation
+                         and solves.  Residuals, acceptance tests and the
+                         inertia (pivot) test are FP64 in every form. */
   int schedule;       /* 0: warp per problem for the first iterations, then a
                          block per remaining problem; 1: warp per problem only;
                          2: block per problem only */

@@ -1,10 +1,10 @@
 """Measured selection of the solver's execution options for one workload.
 
 The library exposes the choices that decide throughput on a given problem
-family: the factorisation precision (FP64, or FP32 with FP64 refinement) and,
-for the FP32 form, the barrier scale above which an iteration falls back to an
-FP64 factorisation (``fp32_switch``; negative = FP32 derivative blocks with an
-FP64 factorisation).  ``autotune`` runs each candidate on a sample of the
+family: the factorisation precision (FP64; FP32 with FP64 refinement;
+double-float) and, for the FP32 form, the barrier scale above which an
+iteration falls back to an FP64 factorisation (``fp32_switch``; negative =
+FP32 derivative blocks with an FP64 factorisation).  ``autotune`` runs each candidate on a sample of the
 workload through the queue (iteration-level batching) path and returns the
 fastest in converged solves per second.  Everything it runs is the CUDA path.
 """
@@ -18,9 +18,9 @@ import numpy as np
 from . import bipm
 
 DEFAULT_CANDIDATES = (
+    bipm.Options(precision=2),
     bipm.Options(precision=1, fp32_switch=-1.0),
     bipm.Options(precision=1, fp32_switch=1e2),
-    bipm.Options(precision=1, fp32_switch=1e4),
 )
 
 

@@ -177,7 +177,7 @@ class Options:
     tol: float = 1e-6
     max_iter: int = 500
     mu_init: float = 0.1
-    precision: int = 0  # 0 FP64 factorisation, 1 FP32 factorisation + FP64 refinement
+    precision: int = 0  # 0 FP64, 1 FP32 factorisation + FP64 refinement, 2 double-float factorisation
     schedule: int = 0   # 0 warp then block teams, 1 warp teams only, 2 block teams only
     fp32_switch: float = 0.0  # barrier scale above which precision 1 factorises in FP64
 

@@ -145,10 +145,18 @@ __global__ void gather_kernel(const Params* __restrict__ P, int first, int count
 }
 
 // ------------------------------------------------------------- host helpers
-void* iter_kernel_ptr(int precision) { return precision ? iter_kernel_f32() : iter_kernel_f64(); }
-void* init_kernel_ptr(int precision) { return precision ? init_kernel_f32() : init_kernel_f64(); }
-void* block_kernel_ptr(int precision) { return precision ? block_kernel_f32() : block_kernel_f64(); }
-void* queue_kernel_ptr(int precision) { return precision ? queue_kernel_f32() : queue_kernel_f64(); }
+void* iter_kernel_ptr(int precision) {
+  return precision == 2 ? iter_kernel_df() : precision ? iter_kernel_f32() : iter_kernel_f64();
+}
+void* init_kernel_ptr(int precision) {
+  return precision == 2 ? init_kernel_df() : precision ? init_kernel_f32() : init_kernel_f64();
+}
+void* block_kernel_ptr(int precision) {
+  return precision == 2 ? block_kernel_df() : precision ? block_kernel_f32() : block_kernel_f64();
+}
+void* queue_kernel_ptr(int precision) {
+  return precision == 2 ? queue_kernel_df() : precision ? queue_kernel_f32() : queue_kernel_f64();
+}
 
 int check_slots(const bipm_batch* b, int first, int count) {
   if (!b) return fail(BIPM_EINVAL, "null batch");
@@ -213,7 +221,7 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
   if (capacity < 0) return fail(BIPM_EINVAL, "capacity must be >= 0");
   bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0, 0, 0.0};
   if (o.fp32_switch == 0.0) o.fp32_switch = kFp32BarrierMax;
-  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || (o.precision != 0 && o.precision != 1) ||
+  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || o.precision < 0 || o.precision > 2 ||
       o.schedule < 0 || o.schedule > 2)
     return fail(BIPM_EINVAL, "bad options");
 
@@ -249,7 +257,7 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
   // shared-memory scratch per warp: the factorisation precision's scratch when
   // it fits in 24 KB, otherwise none (the slot's global scratch is used)
   {
-    size_t need = scratch_bytes(d.nq, d.nx, d.nu, o.precision ? 4 : 8);
+    size_t need = scratch_bytes(d.nq, d.nx, d.nu, o.precision == 1 ? 4 : 8);
     size_t need64 = scratch_bytes(d.nq, d.nx, d.nu, 8);
     size_t cap_b = 24 * 1024;
     b->smem_per_warp = (int)(need64 <= cap_b ? need64 : (need <= cap_b ? need : 128));
@@ -260,12 +268,15 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
     return fail(code, msg);
   };
   size_t cap = (size_t)std::max(capacity, 1);
+  // element sizes: derivative blocks FP32 for precision 1 and 2; factors FP32
+  // for precision 1, double or double-float (8 bytes) otherwise
   size_t tsz = o.precision ? sizeof(float) : sizeof(double);
+  size_t fsz = o.precision == 1 ? sizeof(float) : sizeof(double);
   if (cudaMalloc(&b->f64, cap * b->L.slot_f64 * sizeof(double)) != cudaSuccess)
     return cleanup(BIPM_ENOMEM, "workspace (FP64 vectors)");
   if (cudaMalloc(&b->tb, cap * b->L.slot_tb * tsz) != cudaSuccess)
     return cleanup(BIPM_ENOMEM, "workspace (derivative blocks)");
-  if (cudaMalloc(&b->tf, cap * b->L.fac_size * tsz) != cudaSuccess)
+  if (cudaMalloc(&b->tf, cap * b->L.fac_size * fsz) != cudaSuccess)
     return cleanup(BIPM_ENOMEM, "workspace (factors)");
   if (cudaMalloc(&b->theta, cap * d.n_theta * sizeof(double) + 8) != cudaSuccess)
     return cleanup(BIPM_ENOMEM, "parameters");

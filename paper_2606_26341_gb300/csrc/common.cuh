@@ -7,6 +7,7 @@
 
 #include "../../include/bipm.h"
 #include "scalar.cuh"
+#include "dfloat.cuh"
 
 namespace bipm {
 
@@ -83,7 +84,7 @@ struct Options {
   double tol;
   int max_iter;
   double mu_init;
-  int precision;  // 0 = FP64 factorisation, 1 = FP32 factorisation + FP64 refinement
+  int precision;  // 0 FP64; 1 FP32 factorisation + FP64 refinement; 2 double-float factorisation
   double fp32_switch;  // barrier scale above which precision 1 factorises in FP64
 };
 

@@ -75,6 +75,36 @@ struct Ctx {
 
 __device__ __forceinline__ double sq(double a) { return a * a; }
 
+// 12-term dot product a[r*sa] * b[r*sb] with three independent partial sums
+// (shorter dependency chains for the latency-bound stage products)
+template <class TX>
+__device__ __forceinline__ TX dot12(const TX* a, int sa, const TX* b, int sb) {
+  TX a0 = a[0] * b[0], a1 = a[sa] * b[sb], a2 = a[2 * sa] * b[2 * sb];
+#pragma unroll
+  for (int r = 3; r < 12; r += 3) {
+    a0 += a[r * sa] * b[r * sb];
+    a1 += a[(r + 1) * sa] * b[(r + 1) * sb];
+    a2 += a[(r + 2) * sa] * b[(r + 2) * sb];
+  }
+  return (a0 + a1) + a2;
+}
+
+// strided walk over the entries of an R x C row-major index space without a
+// division per entry: (i, j) of entry e = lane, lane + T, ...
+#define MAT_LOOP_BEGIN(i, j, R, C)                   \
+  {                                                  \
+    const int C_ = (C), RC_ = (R) * (C);             \
+    int i = lane / C_, j = lane - (lane / C_) * C_;  \
+    for (int e = lane; e < RC_; e += c.T) {
+#define MAT_LOOP_END(i, j)     \
+  j += c.T;                    \
+  while (j >= C_) {            \
+    j -= C_;                   \
+    ++i;                       \
+  }                            \
+  }                            \
+  }
+
 // ------------------------------------------------------------ index helpers
 struct VarInfo {
   int kind;   // VK_FREE, VK_BOX, VK_LOWER
@@ -561,8 +591,7 @@ __device__ __noinline__ void add_state_block(Ctx<TB, TF>& c, int k, TX* Q, doubl
   const double* x = c.f + c.L.x;
   const double* ev = c.f + c.L.ev;
   const bool ident = flags & FF_IDENT;
-  LANE_LOOP(e, nx * nx) {
-    int i = e / nx, j = e - (e / nx) * nx;
+  MAT_LOOP_BEGIN(i, j, nx, nx)
     TX v = accumulate ? Q[e] : (TX)0;
     if (i == j) v += (TX)(obj_hdiag(c, off_x(d, k) + i, flags) + (ident ? 0.0 : dw));
     int qi = i / 12, qj = j / 12;
@@ -582,7 +611,7 @@ __device__ __noinline__ void add_state_block(Ctx<TB, TF>& c, int k, TX* Q, doubl
       }
     }
     Q[e] = v;
-  }
+  MAT_LOOP_END(i, j)
 }
 
 // Cholesky of the nxn symmetric matrix in `a` (row-major, double) in place;
@@ -701,69 +730,44 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
     LANE_LOOP(e, 48 * nq) s.Bb[e] = (TX)Bg[e];
     team_sync(c);
     // PA = P~ A, PB = P~ B (block-diagonal A, B; column-major blocks)
-    LANE_LOOP(e, nx * nx) {
-      int i = e / nx, col = e - (e / nx) * nx;
+    MAT_LOOP_BEGIN(i, col, nx, nx)
       int q = col / 12, cc = col - 12 * q;
-      const TX* a = s.Ab + q * 144 + cc * 12;
-      const TX* prow = s.Pb + i * nx + 12 * q;
-      TX acc = 0;
-#pragma unroll
-      for (int r = 0; r < 12; ++r) acc += prow[r] * a[r];
-      s.PA[e] = acc;
-    }
-    LANE_LOOP(e, nx * nu) {
-      int i = e / nu, col = e - (e / nu) * nu;
-      int q = col / 4, cc = col - 4 * q;
-      const TX* b = s.Bb + q * 48 + cc * 12;
-      const TX* prow = s.Pb + i * nx + 12 * q;
-      TX acc = 0;
-#pragma unroll
-      for (int r = 0; r < 12; ++r) acc += prow[r] * b[r];
-      s.PB[e] = acc;
-    }
+      s.PA[e] = dot12(s.Pb + i * nx + 12 * q, 1, s.Ab + q * 144 + cc * 12, 1);
+    MAT_LOOP_END(i, col)
+    MAT_LOOP_BEGIN(i, col, nx, nu)
+      int q = col >> 2, cc = col & 3;
+      s.PB[e] = dot12(s.Pb + i * nx + 12 * q, 1, s.Bb + q * 48 + cc * 12, 1);
+    MAT_LOOP_END(i, col)
     team_sync(c);
     // R^ = R~ + B^T P~ B ; S^ = S + B^T P~ A
-    LANE_LOOP(e, nu * nu) {
-      int a = e / nu, b = e - (e / nu) * nu;
-      int qa = a / 4, ca = a - 4 * qa;
-      const TX* bcol = s.Bb + qa * 48 + ca * 12;
-      TX acc = 0;
-#pragma unroll
-      for (int r = 0; r < 12; ++r) acc += bcol[r] * s.PB[(12 * qa + r) * nu + b];
+    MAT_LOOP_BEGIN(a, b, nu, nu)
+      int qa = a >> 2, ca = a & 3;
+      TX acc = dot12(s.Bb + qa * 48 + ca * 12, 1, s.PB + (12 * qa) * nu + b, nu);
       int ui = off_u(d, k) + a;
       if (a == b) acc += (TX)(obj_hdiag(c, ui, flags) + (ident ? 0.0 : sigma_of(c, ui) + dw));
-      int qb = b / 4;
+      int qb = b >> 2;
       if (!ident && qa == qb) {
         const TB* H = c.blk + c.L.H + ((long long)k * nq + qa) * 100;
-        acc += (TX)H[(6 + (b - 4 * qb)) * 10 + (6 + ca)];
+        acc += (TX)H[(6 + (b & 3)) * 10 + (6 + ca)];
       }
       s.R64[e] = (double)acc;
-    }
-    LANE_LOOP(e, nu * nx) {
-      int a = e / nx, col = e - (e / nx) * nx;
-      int qa = a / 4, ca = a - 4 * qa;
-      const TX* bcol = s.Bb + qa * 48 + ca * 12;
-      TX acc = 0;
-#pragma unroll
-      for (int r = 0; r < 12; ++r) acc += bcol[r] * s.PA[(12 * qa + r) * nx + col];
+    MAT_LOOP_END(a, b)
+    MAT_LOOP_BEGIN(a, col, nu, nx)
+      int qa = a >> 2, ca = a & 3;
+      TX acc = dot12(s.Bb + qa * 48 + ca * 12, 1, s.PA + (12 * qa) * nx + col, nx);
       int qc = col / 12, cc = col - 12 * qc;
       if (!ident && qc == qa && cc >= 6) {
         const TB* H = c.blk + c.L.H + ((long long)k * nq + qa) * 100;
         acc += (TX)H[(cc - 6) * 10 + (6 + ca)];
       }
       s.Sh[e] = acc;
-    }
+    MAT_LOOP_END(a, col)
     team_sync(c);
     // Q^ = A^T P~ A + Q~_k (overwrites Pb)
-    LANE_LOOP(e, nx * nx) {
-      int i = e / nx, col = e - (e / nx) * nx;
+    MAT_LOOP_BEGIN(i, col, nx, nx)
       int q = i / 12, ci = i - 12 * q;
-      const TX* acol = s.Ab + q * 144 + ci * 12;
-      TX acc = 0;
-#pragma unroll
-      for (int r = 0; r < 12; ++r) acc += acol[r] * s.PA[(12 * q + r) * nx + col];
-      s.Pb[e] = acc;
-    }
+      s.Pb[e] = dot12(s.Ab + q * 144 + ci * 12, 1, s.PA + (12 * q) * nx + col, nx);
+    MAT_LOOP_END(i, col)
     team_sync(c);
     add_state_block<TB, TF, TX>(c, k, s.Pb, dw, flags, y, true);
     // Cholesky of R^ in FP64: the inertia test
@@ -793,17 +797,20 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
     }
     team_sync(c);
     // P_k = Q^ + S^T K, symmetrised
-    LANE_LOOP(e, nx * nx) {
-      int i = e / nx, j = e - (e / nx) * nx;
-      TX acc = 0;
-      for (int a = 0; a < nu; ++a) acc += s.Sh[a * nx + i] * s.Kb[a * nx + j];
-      s.PA[e] = s.Pb[e] + acc;
-    }
+    MAT_LOOP_BEGIN(i, j, nx, nx)
+      TX a0 = 0, a1 = 0;
+      int a = 0;
+      for (; a + 1 < nu; a += 2) {
+        a0 += s.Sh[a * nx + i] * s.Kb[a * nx + j];
+        a1 += s.Sh[(a + 1) * nx + i] * s.Kb[(a + 1) * nx + j];
+      }
+      if (a < nu) a0 += s.Sh[a * nx + i] * s.Kb[a * nx + j];
+      s.PA[e] = s.Pb[e] + (a0 + a1);
+    MAT_LOOP_END(i, j)
     team_sync(c);
-    LANE_LOOP(e, nx * nx) {
-      int i = e / nx, j = e - (e / nx) * nx;
+    MAT_LOOP_BEGIN(i, j, nx, nx)
       s.Pb[e] = (TX)0.5 * (s.PA[i * nx + j] + s.PA[j * nx + i]);
-    }
+    MAT_LOOP_END(i, j)
     TX* Kg = F.K + (long long)k * nu * nx;
     LANE_LOOP(e, nu * nx) Kg[e] = s.Kb[e];
     TX* Lg = F.Lr + (long long)k * nu * nu;

@@ -9,6 +9,8 @@
 // works on the restoration problem (variables x, p, n).
 #pragma once
 
+#include <type_traits>
+
 #include "ipm_device.cuh"
 
 namespace bipm {
@@ -199,6 +201,11 @@ template <class TB, class TF>
 __device__ __noinline__ bool factor_any(Ctx<TB, TF>& c, double dw, bool force64) {
   const int flags = c.resto ? FF_RESTO : 0;
   const double* y = c.f + c.L.y;
+  if (HighPrecision<TF>::value && !std::is_same<TF, double>::value && !c.resto && !force64) {
+    // double-float factorisation: accurate enough to need no refinement
+    c.use64 = 0;
+    return factor<TB, TF, TF>(c, c.fac, dw, flags, y) != 0;
+  }
   if (sizeof(TF) == 4 && !c.resto && !force64) {
     // per-problem precision choice: FP32 only while the barrier terms leave
     // the refinement a well-conditioned preconditioned system
@@ -208,7 +215,7 @@ __device__ __noinline__ bool factor_any(Ctx<TB, TF>& c, double dw, bool force64)
       c.n_esc++;
     }
   }
-  if (sizeof(TF) == 8 || c.resto || force64) {
+  if (HighPrecision<TF>::value || c.resto || force64) {
     c.use64 = 1;
     return factor<TB, TF, double>(c, c.fac64, dw, flags, y) != 0;
   }
@@ -236,6 +243,10 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF>& c, const double* r, doub
   const double* y = c.f + c.L.y;
   if (c.use64) {
     solve<TB, TF, double>(c, c.fac64, r, out, flags, y);
+    return true;
+  }
+  if (HighPrecision<TF>::value) {  // double-float factors: no refinement needed
+    solve<TB, TF, TF>(c, c.fac, r, out, flags, y);
     return true;
   }
   const int lane = c.lane;

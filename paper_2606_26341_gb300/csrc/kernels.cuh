@@ -26,7 +26,7 @@ __device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, in
   c.blk = (TB*)P->tb + (long long)slot * P->L.slot_tb;
   TF* fb = (TF*)P->tf + (long long)slot * P->L.fac_size;
   c.fac = make_fac<TF>(fb, P->L);
-  if constexpr (sizeof(TF) == 8)
+  if constexpr (std::is_same<TF, double>::value)
     c.fac64 = make_fac<double>((double*)fb, P->L);
   else
     c.fac64 = make_fac<double>(c.f + P->L.f64_fac, P->L);
@@ -86,7 +86,7 @@ __device__ void run_slot(Ctx<TB, TF>& c, SlotState& S, int n_iter, int visit_cap
 // the work counter and iterates it (iteration-level batching: a warp that
 // finishes a problem immediately starts another one).
 template <class TB, class TF>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     ipm_kernel(const Params* __restrict__ P, int n_iter, int visit_cap) {
   extern __shared__ __align__(16) char smem_all[];
   const int lane = threadIdx.x & 31;
@@ -219,7 +219,7 @@ __global__ void init_kernel(const Params* __restrict__ P, int first, int count,
 // slot with the next problem of the queue, so no slot idles while the queue
 // holds work.
 template <class TB, class TF>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     queue_kernel(const Params* __restrict__ P, const double* __restrict__ theta_q, int n_queue,
                  int n_warps, double* __restrict__ x_out, bipm_result* __restrict__ res_out) {
   extern __shared__ __align__(16) char smem_all[];
@@ -278,5 +278,9 @@ void* block_kernel_f64();
 void* iter_kernel_f32();
 void* init_kernel_f32();
 void* block_kernel_f32();
+void* iter_kernel_df();
+void* init_kernel_df();
+void* block_kernel_df();
+void* queue_kernel_df();
 
 }  // namespace bipm

@@ -78,7 +78,7 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
     return sfail(BIPM_EINVAL, "obstacle counts must be 0..256");
   if (!(desc->pair_dist >= 0.0)) return sfail(BIPM_EINVAL, "pair_dist must be >= 0");
   bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0, 0, 0.0};
-  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || (o.precision != 0 && o.precision != 1))
+  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || o.precision < 0 || o.precision > 2)
     return sfail(BIPM_EINVAL, "bad options");
   if (o.fp32_switch == 0.0) o.fp32_switch = kFp32BarrierMax;
   if (count == 0) return 0;
@@ -105,11 +105,12 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
   d.n_theta = d.th_cyl + 3 * d.n_cyl;
   const Layout L = make_layout(d, o.precision);
   const size_t tsz = o.precision ? sizeof(float) : sizeof(double);
+  const size_t fsz = o.precision == 1 ? sizeof(float) : sizeof(double);
 
   // carve the static array: launch record and counter, then per-slot regions
   const size_t hdr = align256(sizeof(Params)) + 256;
   const size_t per_slot = align256(L.slot_f64 * sizeof(double)) + align256(L.slot_tb * tsz) +
-                          align256(L.fac_size * tsz) + align256(d.n_theta * sizeof(double)) +
+                          align256(L.fac_size * fsz) + align256(d.n_theta * sizeof(double)) +
                           align256(sizeof(SlotState));
   if (hdr + per_slot > kStaticBytes)
     return sfail(BIPM_EINVAL, "problem too large for the static workspace: one problem needs " +
@@ -122,10 +123,10 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
   if (rc) return rc;
 
   // one slot per resident warp, at most one per problem and per what fits
-  void* kfn = o.precision ? queue_kernel_f32() : queue_kernel_f64();
+  void* kfn = o.precision == 2 ? queue_kernel_df() : o.precision ? queue_kernel_f32() : queue_kernel_f64();
   int smem_per_warp;
   {
-    size_t need = scratch_bytes(d.nq, d.nx, d.nu, o.precision ? 4 : 8);
+    size_t need = scratch_bytes(d.nq, d.nx, d.nu, o.precision == 1 ? 4 : 8);
     size_t need64 = scratch_bytes(d.nq, d.nx, d.nu, 8);
     size_t cap_b = 24 * 1024;
     smem_per_warp = (int)(need64 <= cap_b ? need64 : (need <= cap_b ? need : 128));
@@ -159,7 +160,7 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
   P.tb = p;
   p += align256(L.slot_tb * tsz) * slots;
   P.tf = p;
-  p += align256(L.fac_size * tsz) * slots;
+  p += align256(L.fac_size * fsz) * slots;
   P.theta = (double*)p;
   p += align256(d.n_theta * sizeof(double)) * slots;
   P.st = (SlotState*)p;

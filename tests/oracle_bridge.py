@@ -113,3 +113,15 @@ def straight_line_guess(desc, theta):
         if k >= 1:
             pos += ni
     return x0
+
+
+def oracle_kkt_error(desc, theta, x, y, zl, zu, tol=1e-6):
+    """IPOPT's scaled optimality error E_0 of a returned iterate, evaluated with
+    the oracle's own model and autograd derivatives (an independent KKT check)."""
+    nlp = QuadNLP(desc, theta)
+    opt = ipm.Options(tol=tol)
+    g = nlp.grad_f(x)
+    J = nlp.jac_c(x)
+    c = nlp.c(x)
+    return ipm.opt_error(nlp, np.asarray(x), np.asarray(y), np.asarray(zl), np.asarray(zu), g, J, c,
+                         0.0, opt)
