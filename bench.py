@@ -199,7 +199,7 @@ def run_ours(args):
 
     # chosen form: the autotuner's pick among the FP32 variants (untimed)
     if args.only_mixed:
-        best = bipm.Options(precision=1, fp32_switch=-1.0)
+        best = bipm.Options(precision=1, fp32_switch=1e2)
         tune_table = []
     else:
         best, tune_table = autotune.autotune(desc, theta_wdev[: min(B, 2048)], B, stream=stream)
@@ -289,6 +289,8 @@ def run_ours(args):
                       "frac": f64_d / k_fp64 / FP64_PEAK_NOMINAL},
     }
 
+    warm = None if args.no_warm else warm_leg(args, dev, stream, rank, barrier, reduce, MAX, SUM)
+
     if rank == 0:
         opt_desc = {"precision": best.precision, "fp32_switch": best.fp32_switch}
         line = {
@@ -315,12 +317,88 @@ def run_ours(args):
             "clocks": clk,
             "gpu_launches": 1,
         }
+        if warm is not None:
+            line["warm_start"] = warm
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(desc, theta, budget_s=args.cpu_budget)
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ------------------------------------------------- learned warm start leg
+WARM_WORKLOAD = "cyl"
+
+
+def warm_leg(args, dev, stream, rank, barrier, reduce, MAX, SUM):
+    """Cluttered environment (1 quadrotor, N = 40, 20-50 cylinders, 16384 problems):
+    plain FP64 cold start vs the chosen form cold and warm-started by the proposer
+    network, which is first trained (untimed) on this solver's solutions of a
+    disjoint set of problems.  The proposal (features, network, decoding) is
+    inside the warm run's timed region; cold start is its fallback."""
+    import torch
+
+    from paper_2606_26341_gb300 import bipm, warmstart
+    from workloads import mlp_init
+
+    B = args.warm_batch
+    chosen = bipm.Options(precision=1, fp32_switch=1e2)
+    desc, th_train = make_batch(WARM_WORKLOAD, args.warm_train, first_id=1_000_000 + rank * args.warm_train)
+    _, th_test = make_batch(WARM_WORKLOAD, B, first_id=rank * B)
+    tr = torch.as_tensor(th_train, device=dev)
+    te = torch.as_tensor(th_test, device=dev)
+    t0 = time.perf_counter()
+    data = warmstart.make_dataset(desc, tr, chosen, capacity=min(8192, args.warm_train), stream=stream)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    widths = warmstart.widths(desc)
+    net = bipm.MLP(widths, max_rows=1024, stream=stream)
+    net.set_params(mlp_init(widths, 5))
+    t0 = time.perf_counter()
+    hist = warmstart.train(net, data, epochs=args.warm_epochs, batch=512, lr=2e-3, lr_final=5e-5, seed=6)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    rsize = bipm.RESULT_DTYPE.itemsize
+    res = torch.empty(B * rsize, dtype=torch.uint8, device=dev)
+
+    def timed(options, warm_start):
+        with bipm.Batch(desc, B, options, stream=stream) as b:
+            g = warmstart.propose(net, desc, te[:256], stream=stream) if warm_start else None
+            b.solve_queue(te[:256], None, res[: 256 * rsize], x_guess=g)  # warm-up
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g = warmstart.propose(net, desc, te, stream=stream) if warm_start else None
+            b.solve_queue(te, None, res, x_guess=g)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+        r = bipm.results_from_bytes(res.cpu().numpy())
+        conv = int(np.sum(r["status"] == bipm.CONVERGED))
+        t = reduce(e0.elapsed_time(e1) / 1e3, MAX)
+        out = {"value": reduce(conv, SUM) / t, "unit": UNIT, "converged_frac": conv / B,
+               "iters_mean": float(np.mean(r["iters"] + r["warm_iters"])),
+               "max_kkt_err_converged": float(np.max(r["kkt_err"][r["status"] == bipm.CONVERGED]))}
+        if warm_start:
+            out["fallback_frac"] = float(np.mean(r["warm"] == 2))
+        return out
+
+    cold64 = timed(bipm.Options(precision=0), False)
+    cold_mixed = timed(chosen, False)
+    warm_mixed = timed(chosen, True)
+    net.close()
+    return {"workload": f"{WARM_WORKLOAD}: 1 quadrotor, RK4 N=40, 20-50 cylinders (padded to 50), "
+                        f"{B} problems",
+            "cold_fp64": cold64, "cold_chosen": cold_mixed, "warm_chosen": warm_mixed,
+            "warm_vs_cold_fp64": warm_mixed["value"] / cold64["value"],
+            "network": {"widths": list(widths), "dtype": "bf16 operands, f32 accumulation",
+                        "train_problems": args.warm_train, "usable": int(len(data.usable)),
+                        "epochs": args.warm_epochs, "loss_first_last": [hist[0], hist[-1]],
+                        "dataset_s": t_data, "train_s": t_train}}
 
 
 def stats_record_bytes():
@@ -420,6 +498,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--batch", type=int, default=BATCH, help="problems per GPU (profiling runs only)")
     ap.add_argument("--only-mixed", action="store_true", help="skip the FP64 form (profiling runs only)")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--warm-train", type=int, default=16384, help="training problems of the warm-start leg")
+    ap.add_argument("--warm-epochs", type=int, default=30)
+    ap.add_argument("--warm-batch", type=int, default=16384, help="problems of the warm-start leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -90,6 +90,12 @@ typedef struct {
                          (input Sigma, slack condensation weight) is at most
                          this; above it the factorisation is FP64.  0 selects
                          the default (1e5); negative: always FP64. */
+  double warm_mu_init;    /* mu_0 of a warm-started problem (0 = default 1e-2) */
+  double warm_bound_push; /* bound push and bound fraction of a warm start
+                             (0 = default 1e-3) */
+  int warm_max_iter;      /* iteration budget of a warm-started run before the
+                             cold fallback (0 = default 60; capped by max_iter) */
+  int reserved_;          /* must be 0 */
 } bipm_options;
 
 /* Per-slot outcome and counters. */
@@ -131,6 +137,9 @@ typedef struct {
   int resto_iters;
   int fact32;         /* factorisations / solves done in FP32 */
   int solve32;
+  int warm;           /* 0 cold start; 1 warm start accepted; 2 warm start
+                         rejected by the KKT test, problem re-solved cold */
+  int warm_iters;     /* iterations of a rejected warm-started run (warm = 2) */
   double obj;
   double kkt_err;
 } bipm_result;
@@ -200,6 +209,19 @@ int bipm_solve(bipm_batch* b);
 int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, double* x_out,
                      bipm_result* results, int on_device);
 
+/* Iteration-level batching with a learned warm start (Sec. V; the warm-start
+ * proposer of the method): as bipm_solve_queue, but problem i starts from the
+ * primal point x_guess row i (n_queue x n, e.g. from bipm_warm_decode) pushed
+ * inside the bounds by warm_bound_push, with mu_0 = warm_mu_init and bound
+ * multipliers centred on the barrier (z = mu_0 / distance to the bound); y by
+ * least squares.  Cold start is the fallback and the KKT residual the judge:
+ * a warm-started run that has not terminated converged (E_0 <= tol) within
+ * warm_max_iter iterations is rerun from the cold start in the same slot
+ * (bipm_result.warm = 2).  Pointers as
+ * for bipm_solve_queue (x_guess on the same side as theta_queue). */
+int bipm_solve_queue_warm(bipm_batch* b, const double* theta_queue, const double* x_guess, int n_queue,
+                          double* x_out, bipm_result* results, int on_device);
+
 /* One-shot solve that allocates nothing (the paper has no counterpart; this
  * is an addition for callers that cannot allocate device memory when they
  * need a solve: code inside a CUDA stream capture, where cudaMalloc is not
@@ -227,6 +249,67 @@ int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, doub
  * finished.  Errors as for the other calls (bipm_last_error). */
 int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, const double* theta,
                       int count, double* x_out, bipm_result* results, void* cuda_stream);
+
+/* ---------------------------------------------------------------- warm start
+ * Encodings of the learned warm start for the cluttered-environment family
+ * (one quadrotor, n_cylinders vertical cylinders, no spheres, no pairs, a fixed
+ * goal in the reference slot).  All pointers are DEVICE pointers on
+ * `cuda_stream` (NULL = default stream); the calls return after launching.
+ *
+ * bipm_warm_features: network input of each problem, count x (12 + 3 k_near)
+ *   floats: (p0 - goal)/10, v0/2, eta0, omega0/2, then the k_near cylinders
+ *   nearest to p0 in the horizontal plane (centre distance, ties by index):
+ *   (cx - p0x)/10, (cy - p0y)/10, r; zeros past 30 m or past n_cylinders.
+ * bipm_warm_encode: training targets from primal trajectories x (count x n):
+ *   count x (12 (N+1) + 4 N) floats, (x_k - xbar)/S with
+ *   S = (2,2,2, 2,2,2, .5,.5,.5, 2,2,2), then (u_k - u_hover)/u_hover.
+ * bipm_warm_decode: primal starting points (count x n doubles) from network
+ *   outputs in the target encoding: x_0 = xbar, x_k = xbar + S o_k (k >= 1),
+ *   u_k = u_hover (1 + o), slacks at the cylinder inequality values g(x_k).
+ * Errors: BIPM_EINVAL for another problem family or bad sizes. */
+int bipm_warm_features(const bipm_problem_desc* desc, const double* theta, int count, int k_near,
+                       float* features, void* cuda_stream);
+int bipm_warm_encode(const bipm_problem_desc* desc, const double* theta, const double* x, int count,
+                     float* targets, void* cuda_stream);
+int bipm_warm_decode(const bipm_problem_desc* desc, const double* theta, const float* net_out, int count,
+                     double* x_guess, void* cuda_stream);
+
+/* ------------------------------------------------------------ warm-start network
+ * The proposer: a tanh multilayer perceptron
+ *     a_0 = x,  a_l = tanh(a_{l-1} W_l^T + b_l) (hidden),  out = a_{L-1} W_L^T + b_L,
+ * trained on solutions of this solver with loss 1/(2B) sum |out - t|^2 and
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected moments).
+ * Precision: matrix-product operands (inputs, weights, activations, errors)
+ * are bfloat16, products accumulate in FP32 on the tensor cores; biases,
+ * activations kept for the derivative, gradients and Adam's master weights
+ * and moments are FP32.
+ * Parameters are one flat FP32 vector: per layer W_l (width_l x width_{l-1},
+ * row-major) then b_l.  x: rows x widths[0], t and out: rows x widths[last],
+ * row-major FP32.  The network owns its device memory; `on_device` selects
+ * device (1) or host (0) pointers for the caller's buffers. */
+typedef struct bipm_mlp bipm_mlp;
+
+/* widths: n_widths layer widths (input, hidden..., output), 2 <= n_widths <= 9;
+ * max_rows: largest batch of a gradient or training call.  Parameters start
+ * at zero (set them with bipm_mlp_set_params). */
+int bipm_mlp_create(const int* widths, int n_widths, int max_rows, void* cuda_stream, bipm_mlp** out);
+int bipm_mlp_param_count(const bipm_mlp* net, long long* count);
+/* Loads the FP32 master parameters and resets Adam's moments and step count. */
+int bipm_mlp_set_params(bipm_mlp* net, const float* params, int on_device);
+int bipm_mlp_get_params(const bipm_mlp* net, float* params, int on_device);
+/* out = network(x) for any number of rows (processed max_rows at a time). */
+int bipm_mlp_forward(bipm_mlp* net, const float* x, int rows, float* out, int on_device);
+/* Loss and its gradient with respect to the flat parameters (rows <= max_rows);
+ * grad (n_params floats) and loss (one double) may be NULL. */
+int bipm_mlp_loss_grad(bipm_mlp* net, const float* x, const float* t, int rows, float* grad, double* loss,
+                       int on_device);
+/* One Adam step on the batch of rows idx[0..rows) of x and t (DEVICE pointers;
+ * idx NULL = the first `rows` rows) with learning rate lr.  loss (host, may be
+ * NULL) receives the batch loss before the step; without it the call returns
+ * after launching. */
+int bipm_mlp_train_step(bipm_mlp* net, const float* x, const float* t, const int* idx, int rows, float lr,
+                        double* loss);
+void bipm_mlp_destroy(bipm_mlp* net);
 
 /* Runs exactly `n_iterations` iterations on every running slot. */
 int bipm_step(bipm_batch* b, int n_iterations);

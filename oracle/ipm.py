@@ -71,6 +71,7 @@ class Options:
     bound_frac: float = 1e-2
     y_max: float = 1e3
     z_init: float = 1.0
+    z_centred: bool = False  # warm start: z = mu_init / (distance to the bound) instead of z_init
     rho: float = 1000.0
     kappa_resto: float = 0.9
     filter_cap: int = 64
@@ -289,7 +290,8 @@ class RestoNLP:
 # ------------------------------------------------------------- the solver --
 
 def initial_state(nlp, x0, opt: Options) -> SolverState:
-    """Starting point: x pushed inside its bounds, z = 1, y set at the first iteration."""
+    """Starting point: x pushed inside its bounds, z = 1 (or centred on mu_init for a
+    warm start), y set at the first iteration."""
     x = np.asarray(x0, dtype=np.float64).copy()
     has_l, has_u = bound_sets(nlp)
     k1, k2 = opt.bound_push, opt.bound_frac
@@ -303,8 +305,13 @@ def initial_state(nlp, x0, opt: Options) -> SolverState:
             x[i] = max(x[i], nlp.xl[i] + k1 * max(1.0, abs(nlp.xl[i])))
         elif has_u[i]:
             x[i] = min(x[i], nlp.xu[i] - k1 * max(1.0, abs(nlp.xu[i])))
-    zl = np.where(has_l, opt.z_init, 0.0)
-    zu = np.where(has_u, opt.z_init, 0.0)
+    if opt.z_centred:
+        sl, su = slacks(nlp, x)
+        zl = np.where(has_l, opt.mu_init / np.where(has_l, sl, 1.0), 0.0)
+        zu = np.where(has_u, opt.mu_init / np.where(has_u, su, 1.0), 0.0)
+    else:
+        zl = np.where(has_l, opt.z_init, 0.0)
+        zu = np.where(has_u, opt.z_init, 0.0)
     ph = Phase(x=x, y=np.zeros(nlp.m), zl=zl, zu=zu, mu=opt.mu_init, filt=[])
     return SolverState(normal=ph)
 

@@ -31,7 +31,9 @@ class ProblemDescC(ctypes.Structure):
 class OptionsC(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mu_init", ctypes.c_double),
                 ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
-                ("fp32_switch", ctypes.c_double)]
+                ("fp32_switch", ctypes.c_double), ("warm_mu_init", ctypes.c_double),
+                ("warm_bound_push", ctypes.c_double), ("warm_max_iter", ctypes.c_int),
+                ("reserved_", ctypes.c_int)]
 
 
 class StatsC(ctypes.Structure):
@@ -52,8 +54,8 @@ class ResultC(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("factorizations", ctypes.c_int),
                 ("solves", ctypes.c_int), ("trials", ctypes.c_int), ("ir_steps", ctypes.c_int),
                 ("fp64_escalations", ctypes.c_int), ("resto_iters", ctypes.c_int),
-                ("fact32", ctypes.c_int), ("solve32", ctypes.c_int),
-                ("obj", ctypes.c_double), ("kkt_err", ctypes.c_double)]
+                ("fact32", ctypes.c_int), ("solve32", ctypes.c_int), ("warm", ctypes.c_int),
+                ("warm_iters", ctypes.c_int), ("obj", ctypes.c_double), ("kkt_err", ctypes.c_double)]
 
 
 RESULT_DTYPE = np.dtype([(f, "<i4" if t is ctypes.c_int else "<f8") for f, t in ResultC._fields_])
@@ -80,7 +82,10 @@ class IterateC(ctypes.Structure):
 
 EXPORTS = ["bipm_create_batch", "bipm_dims", "bipm_set_problems", "bipm_set_initial_guess",
            "bipm_solve", "bipm_step", "bipm_get_solution", "bipm_get_stats", "bipm_get_iterate",
-           "bipm_set_iterate", "bipm_get_phase_cycles", "bipm_solve_queue", "bipm_solve_static",
+           "bipm_set_iterate", "bipm_get_phase_cycles", "bipm_solve_queue", "bipm_solve_queue_warm",
+           "bipm_solve_static", "bipm_warm_features", "bipm_warm_encode", "bipm_warm_decode",
+           "bipm_mlp_create", "bipm_mlp_param_count", "bipm_mlp_set_params", "bipm_mlp_get_params",
+           "bipm_mlp_forward", "bipm_mlp_loss_grad", "bipm_mlp_train_step", "bipm_mlp_destroy",
            "bipm_last_error", "bipm_destroy"]
 PHASES = ["eval", "derivs", "factor", "solve", "line_search", "other", "lsq_mult", "total"]
 
@@ -116,11 +121,25 @@ def load_library(build_if_missing: bool = True):
     lib.bipm_solve_queue.argtypes = [vp, vp, i, vp, vp, i]
     lib.bipm_solve_static.argtypes = [ctypes.POINTER(ProblemDescC), ctypes.POINTER(OptionsC), vp, i,
                                       vp, vp, vp]
+    lib.bipm_solve_queue_warm.argtypes = [vp, vp, vp, i, vp, vp, i]
+    pd = ctypes.POINTER(ProblemDescC)
+    lib.bipm_warm_features.argtypes = [pd, vp, i, i, vp, vp]
+    lib.bipm_warm_encode.argtypes = [pd, vp, vp, i, vp, vp]
+    lib.bipm_warm_decode.argtypes = [pd, vp, vp, i, vp, vp]
+    lib.bipm_mlp_create.argtypes = [vp, i, i, vp, ctypes.POINTER(vp)]
+    lib.bipm_mlp_param_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.bipm_mlp_set_params.argtypes = [vp, vp, i]
+    lib.bipm_mlp_get_params.argtypes = [vp, vp, i]
+    lib.bipm_mlp_forward.argtypes = [vp, vp, i, vp, i]
+    lib.bipm_mlp_loss_grad.argtypes = [vp, vp, vp, i, vp, vp, i]
+    lib.bipm_mlp_train_step.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, vp]
+    lib.bipm_mlp_destroy.argtypes = [vp]
+    lib.bipm_mlp_destroy.restype = None
     lib.bipm_last_error.restype = ctypes.c_char_p
     lib.bipm_destroy.argtypes = [vp]
     lib.bipm_destroy.restype = None
     for name in EXPORTS:
-        if name != "bipm_last_error" and name != "bipm_destroy":
+        if name not in ("bipm_last_error", "bipm_destroy", "bipm_mlp_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -140,10 +159,8 @@ def solve_static(desc, theta_dev, x_out=None, results=None, options: "Options | 
     lib = load_library()
     d = ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist)
     o = options or Options()
-    oc = OptionsC(o.tol, o.max_iter, o.mu_init, o.precision, o.schedule, o.fp32_switch)
-    sp = None
-    if stream is not None:
-        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    oc = o.to_c()
+    sp = _stream_ptr(stream)
     pt, dev = _ptr(theta_dev)
     px, _ = _ptr(x_out)
     if not dev or results is None:
@@ -180,6 +197,19 @@ class Options:
     precision: int = 0  # 0 FP64, 1 FP32 factorisation + FP64 refinement, 2 double-float factorisation
     schedule: int = 0   # 0 warp then block teams, 1 warp teams only, 2 block teams only
     fp32_switch: float = 0.0  # barrier scale above which precision 1 factorises in FP64
+    warm_mu_init: float = 0.0     # mu_0 of a warm start (0: library default 1e-2)
+    warm_bound_push: float = 0.0  # bound push of a warm start (0: library default 1e-3)
+    warm_max_iter: int = 0        # iteration budget of a warm start (0: library default 60)
+
+    def to_c(self):
+        return OptionsC(self.tol, self.max_iter, self.mu_init, self.precision, self.schedule,
+                        self.fp32_switch, self.warm_mu_init, self.warm_bound_push, self.warm_max_iter, 0)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
 class Batch:
@@ -189,11 +219,9 @@ class Batch:
         self.lib = load_library()
         d = ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist)
         o = options or Options()
-        oc = OptionsC(o.tol, o.max_iter, o.mu_init, o.precision, o.schedule, o.fp32_switch)
+        oc = o.to_c()
         h = ctypes.c_void_p()
-        sp = None
-        if stream is not None:
-            sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        sp = _stream_ptr(stream)
         _check(self.lib.bipm_create_batch(ctypes.byref(d), capacity, ctypes.byref(oc), sp,
                                           ctypes.byref(h)))
         self.h = h
@@ -236,24 +264,32 @@ class Batch:
     def solve(self):
         _check(self.lib.bipm_solve(self.h))
 
-    def solve_queue(self, theta_queue, x_out=None, results=None):
+    def solve_queue(self, theta_queue, x_out=None, results=None, x_guess=None):
         """Iteration-level batching over a queue of problems (rows of theta_queue).
 
-        theta_queue / x_out are numpy arrays (host) or CUDA tensors (device);
-        `results` (device mode) is a CUDA uint8 tensor of n_queue * sizeof(bipm_result)
-        bytes (RESULT_DTYPE.itemsize each); read it back with results_from_bytes.
-        Returns a dict of numpy arrays (status, iters, obj, kkt_err) in host mode.
+        theta_queue / x_out / x_guess are numpy arrays (host) or CUDA tensors
+        (device); with x_guess (n_queue x n) every problem is warm-started from
+        its row (bipm_solve_queue_warm).  `results` (device mode) is a CUDA uint8
+        tensor of n_queue * RESULT_DTYPE.itemsize bytes; read it back with
+        results_from_bytes.  Returns a dict of numpy arrays in host mode.
         """
         nq = theta_queue.shape[0]
         pt, dev = _ptr(theta_queue)
         px, _ = _ptr(x_out)
+        pg, _ = _ptr(x_guess)
+
+        def call(res_ptr, on_dev):
+            if x_guess is None:
+                return self.lib.bipm_solve_queue(self.h, pt, nq, px, res_ptr, on_dev)
+            return self.lib.bipm_solve_queue_warm(self.h, pt, pg, nq, px, res_ptr, on_dev)
+
         if dev:
             if results is None:
                 raise ValueError("device mode needs a results buffer")
-            _check(self.lib.bipm_solve_queue(self.h, pt, nq, px, ctypes.c_void_p(results.data_ptr()), 1))
+            _check(call(ctypes.c_void_p(results.data_ptr()), 1))
             return None
         arr = (ResultC * max(nq, 1))()
-        _check(self.lib.bipm_solve_queue(self.h, pt, nq, px, arr, 0))
+        _check(call(arr, 0))
         return {f: np.array([getattr(arr[j], f) for j in range(nq)]) for f, _ in ResultC._fields_}
 
     def step(self, n_iterations: int = 1):
@@ -334,3 +370,136 @@ class Batch:
                 continue
             setattr(it, f, state.get(f, 0))
         _check(self.lib.bipm_set_iterate(self.h, slot, ctypes.byref(it)))
+
+
+# ------------------------------------------------------------------ warm start
+def _desc_c(desc):
+    return ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist)
+
+
+def _dev_ptr(t, dtype_name):
+    import torch
+    if not (hasattr(t, "data_ptr") and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    if t.dtype != getattr(torch, dtype_name):
+        raise ValueError(f"expected a {dtype_name} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def warm_features(desc, theta_dev, k_near, out, stream=None):
+    """bipm_warm_features: out (count x (12 + 3 k_near), float32 CUDA tensor)."""
+    lib = load_library()
+    _check(lib.bipm_warm_features(ctypes.byref(_desc_c(desc)), _dev_ptr(theta_dev, "float64"),
+                                  theta_dev.shape[0], k_near, _dev_ptr(out, "float32"), _stream_ptr(stream)))
+    return out
+
+
+def warm_encode(desc, theta_dev, x_dev, out, stream=None):
+    """bipm_warm_encode: out (count x (12 (N+1) + 4 N), float32 CUDA tensor)."""
+    lib = load_library()
+    _check(lib.bipm_warm_encode(ctypes.byref(_desc_c(desc)), _dev_ptr(theta_dev, "float64"),
+                                _dev_ptr(x_dev, "float64"), theta_dev.shape[0], _dev_ptr(out, "float32"),
+                                _stream_ptr(stream)))
+    return out
+
+
+def warm_decode(desc, theta_dev, net_out, x_guess, stream=None):
+    """bipm_warm_decode: x_guess (count x n, float64 CUDA tensor)."""
+    lib = load_library()
+    _check(lib.bipm_warm_decode(ctypes.byref(_desc_c(desc)), _dev_ptr(theta_dev, "float64"),
+                                _dev_ptr(net_out, "float32"), theta_dev.shape[0], _dev_ptr(x_guess, "float64"),
+                                _stream_ptr(stream)))
+    return x_guess
+
+
+def _fptr(arr):
+    """(pointer, on_device) of a contiguous float32 numpy array or torch tensor."""
+    if arr is None:
+        return None, 0
+    if hasattr(arr, "data_ptr"):
+        import torch
+        if arr.dtype != torch.float32 or not arr.is_contiguous():
+            raise ValueError("tensor must be contiguous float32")
+        return ctypes.c_void_p(arr.data_ptr()), int(arr.is_cuda)
+    if arr.dtype != np.float32 or not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous float32")
+    return arr.ctypes.data_as(ctypes.c_void_p), 0
+
+
+class MLP:
+    """The warm-start network (bipm_mlp_*): widths = (input, hidden..., output)."""
+
+    def __init__(self, widths, max_rows: int, stream=None):
+        self.lib = load_library()
+        self.widths = tuple(int(w) for w in widths)
+        arr = (ctypes.c_int * len(self.widths))(*self.widths)
+        h = ctypes.c_void_p()
+        _check(self.lib.bipm_mlp_create(arr, len(self.widths), max_rows, _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+        self.max_rows = max_rows
+        cnt = ctypes.c_longlong()
+        _check(self.lib.bipm_mlp_param_count(h, ctypes.byref(cnt)))
+        self.n_params = cnt.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bipm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_params(self, flat):
+        p, dev = _fptr(flat)
+        if flat.shape[0] != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        _check(self.lib.bipm_mlp_set_params(self.h, p, dev))
+
+    def get_params(self, out=None):
+        out = np.empty(self.n_params, dtype=np.float32) if out is None else out
+        p, dev = _fptr(out)
+        _check(self.lib.bipm_mlp_get_params(self.h, p, dev))
+        return out
+
+    def forward(self, x, out=None):
+        rows = x.shape[0]
+        if out is None:
+            out = np.empty((rows, self.widths[-1]), dtype=np.float32)
+        px, dev = _fptr(x)
+        po, _ = _fptr(out)
+        _check(self.lib.bipm_mlp_forward(self.h, px, rows, po, dev))
+        return out
+
+    def loss_grad(self, x, t):
+        """(loss, flat gradient) of one batch (host arrays)."""
+        rows = x.shape[0]
+        grad = np.empty(self.n_params, dtype=np.float32)
+        loss = np.zeros(1)
+        px, dev = _fptr(x)
+        pt, _ = _fptr(t)
+        if dev:
+            raise ValueError("loss_grad takes host arrays")
+        _check(self.lib.bipm_mlp_loss_grad(self.h, px, pt, rows, grad.ctypes.data_as(ctypes.c_void_p),
+                                           loss.ctypes.data_as(ctypes.c_void_p), 0))
+        return float(loss[0]), grad
+
+    def train_step(self, x_dev, t_dev, idx_dev, rows: int, lr: float, want_loss=False):
+        """One Adam step on rows idx_dev[:rows] of the CUDA tensors x_dev, t_dev."""
+        import torch
+        if idx_dev is not None and idx_dev.dtype != torch.int32:
+            raise ValueError("idx must be int32")
+        loss = np.zeros(1)
+        pl = loss.ctypes.data_as(ctypes.c_void_p) if want_loss else None
+        pi = ctypes.c_void_p(idx_dev.data_ptr()) if idx_dev is not None else None
+        _check(self.lib.bipm_mlp_train_step(self.h, _dev_ptr(x_dev, "float32"), _dev_ptr(t_dev, "float32"), pi,
+                                            rows, ctypes.c_float(lr), pl))
+        return float(loss[0]) if want_loss else None

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIBNAME = "libbipm.so"
 UNITS = ["bipm.cu", "kernels_f64.cu", "kernels_f32.cu", "kernels_f64_block.cu", "kernels_f32_block.cu",
-         "kernels_df.cu", "kernels_df_block.cu", "noalloc.cu"]
+         "kernels_df.cu", "kernels_df_block.cu", "noalloc.cu", "mlp.cu", "warm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + INCLUDE]

@@ -219,8 +219,14 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
     return fail(BIPM_EINVAL, "obstacle counts must be 0..256");
   if (!(desc->pair_dist >= 0.0)) return fail(BIPM_EINVAL, "pair_dist must be >= 0");
   if (capacity < 0) return fail(BIPM_EINVAL, "capacity must be >= 0");
-  bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0, 0, 0.0};
+  bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0, 0, 0.0, 0.0, 0.0, 0, 0};
   if (o.fp32_switch == 0.0) o.fp32_switch = kFp32BarrierMax;
+  if (o.warm_mu_init == 0.0) o.warm_mu_init = 1e-2;
+  if (o.warm_bound_push == 0.0) o.warm_bound_push = 1e-3;
+  if (o.warm_max_iter == 0) o.warm_max_iter = 60;
+  if (o.warm_max_iter < 0) return fail(BIPM_EINVAL, "warm_max_iter must be >= 0");
+  if (!(o.warm_mu_init > 0.0) || !(o.warm_bound_push > 0.0) || !(o.warm_bound_push < 0.5))
+    return fail(BIPM_EINVAL, "warm_mu_init must be > 0 and warm_bound_push in (0, 0.5)");
   if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || o.precision < 0 || o.precision > 2 ||
       o.schedule < 0 || o.schedule > 2)
     return fail(BIPM_EINVAL, "bad options");
@@ -250,6 +256,9 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
   b->opt.mu_init = o.mu_init;
   b->opt.precision = o.precision;
   b->opt.fp32_switch = o.fp32_switch;
+  b->opt.warm_mu = o.warm_mu_init;
+  b->opt.warm_push = o.warm_bound_push;
+  b->opt.warm_max_iter = std::min(o.warm_max_iter, o.max_iter);
   b->schedule = o.schedule;
   b->capacity = capacity;
   b->stream = (cudaStream_t)cuda_stream;
@@ -403,8 +412,8 @@ int bipm_solve(bipm_batch* b) {
   return run_iterations(b, 0);
 }
 
-int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, double* x_out,
-                     bipm_result* results, int on_device) {
+static int solve_queue_impl(bipm_batch* b, const double* theta_queue, const double* x_guess, int n_queue,
+                            double* x_out, bipm_result* results, int on_device) {
   if (!b) return fail(BIPM_EINVAL, "null batch");
   if (n_queue < 0) return fail(BIPM_EINVAL, "n_queue must be >= 0");
   if (n_queue == 0) return 0;
@@ -413,24 +422,28 @@ int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, doub
   const Dims& d = b->d;
   size_t tb = (size_t)n_queue * d.n_theta * sizeof(double);
   size_t xb = x_out ? (size_t)n_queue * d.n * sizeof(double) : 0;
+  size_t gb = x_guess ? (size_t)n_queue * d.n * sizeof(double) : 0;
   size_t rb = (size_t)n_queue * sizeof(bipm_result);
   const double* th_dev = theta_queue;
+  const double* g_dev = x_guess;
   double* x_dev = x_out;
   bipm_result* r_dev = results;
   int rc;
   if (!on_device) {
-    if ((rc = ensure_stage(b, tb + xb + rb + 256))) return rc;
+    if ((rc = ensure_stage(b, tb + xb + gb + rb + 256))) return rc;
     char* base = (char*)b->stage;
     th_dev = (const double*)base;
     x_dev = x_out ? (double*)(base + tb) : nullptr;
-    r_dev = (bipm_result*)(base + ((tb + xb + 15) & ~(size_t)15));
+    g_dev = x_guess ? (const double*)(base + tb + xb) : nullptr;
+    r_dev = (bipm_result*)(base + ((tb + xb + gb + 15) & ~(size_t)15));
     CUDA_TRY(cudaMemcpyAsync((void*)th_dev, theta_queue, tb, cudaMemcpyHostToDevice, b->stream));
+    if (x_guess) CUDA_TRY(cudaMemcpyAsync((void*)g_dev, x_guess, gb, cudaMemcpyHostToDevice, b->stream));
   }
   // one slot per resident warp
   int warps = std::min(b->capacity, b->blocks * kWarpsPerBlock);
   int blocks = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
   CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
-  void* args[] = {&b->dparams, &th_dev, &n_queue, &warps, &x_dev, &r_dev};
+  void* args[] = {&b->dparams, &th_dev, &n_queue, &warps, &x_dev, &r_dev, &g_dev};
   CUDA_TRY(cudaLaunchKernel(queue_kernel_ptr(b->opt.precision), dim3(blocks), dim3(32 * kWarpsPerBlock),
                             args, (size_t)b->smem_per_warp * kWarpsPerBlock, b->stream));
   if (!on_device) {
@@ -440,6 +453,17 @@ int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, doub
   CUDA_TRY(cudaStreamSynchronize(b->stream));
   b->loaded = 1;
   return 0;
+}
+
+int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, double* x_out,
+                     bipm_result* results, int on_device) {
+  return solve_queue_impl(b, theta_queue, nullptr, n_queue, x_out, results, on_device);
+}
+
+int bipm_solve_queue_warm(bipm_batch* b, const double* theta_queue, const double* x_guess, int n_queue,
+                          double* x_out, bipm_result* results, int on_device) {
+  if (n_queue > 0 && !x_guess) return fail(BIPM_EINVAL, "null x_guess");
+  return solve_queue_impl(b, theta_queue, x_guess, n_queue, x_out, results, on_device);
 }
 
 int bipm_step(bipm_batch* b, int n_iterations) {

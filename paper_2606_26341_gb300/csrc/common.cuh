@@ -86,6 +86,9 @@ struct Options {
   double mu_init;
   int precision;  // 0 FP64; 1 FP32 factorisation + FP64 refinement; 2 double-float factorisation
   double fp32_switch;  // barrier scale above which precision 1 factorises in FP64
+  double warm_mu;      // mu_0 of a warm start
+  double warm_push;    // bound push and fraction of a warm start
+  int warm_max_iter;   // iteration budget of a warm-started run
 };
 
 // IPOPT constants (Wachter & Biegler 2006 defaults)

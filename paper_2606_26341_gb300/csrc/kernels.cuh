@@ -136,23 +136,28 @@ __global__ void __launch_bounds__(kBlockTeam)
   }
 }
 
-// default starting point, pushed inside the bounds (IPOPT initialisation)
-__device__ __forceinline__ double push_into_bounds(int kind, double v) {
+// starting point pushed inside the bounds (IPOPT initialisation): k1 is the
+// absolute push, k2 the fraction of the box width
+__device__ __forceinline__ double push_into_bounds(int kind, double v, double k1, double k2) {
   if (kind == VK_BOX) {
     double width = kUmax - 0.0;
-    double pl = fmin(kBoundPush * fmax(1.0, 0.0), kBoundFrac * width);
-    double pu = fmin(kBoundPush * fmax(1.0, kUmax), kBoundFrac * width);
+    double pl = fmin(k1 * fmax(1.0, 0.0), k2 * width);
+    double pu = fmin(k1 * fmax(1.0, kUmax), k2 * width);
     return fmin(fmax(v, 0.0 + pl), kUmax - pu);
   }
-  if (kind == VK_LOWER) return fmax(v, 0.0 + kBoundPush * fmax(1.0, 0.0));
+  if (kind == VK_LOWER) return fmax(v, 0.0 + k1 * fmax(1.0, 0.0));
   return v;
 }
 
 // Resets one slot to the starting point of the problem whose theta the slot
 // holds (warp-level; lanes stride 32).  guess / yguess: optional primal /
-// multiplier rows.  Returns the fresh state record (identical in all lanes).
+// multiplier rows.  warm: a learned warm start (bound push and fraction
+// opt.warm_push, mu_0 = opt.warm_mu, bound multipliers centred on the barrier,
+// z = mu_0 / distance to the bound) instead of the cold start (push 1e-2,
+// z = 1).  Returns the fresh state record (identical in all lanes).
 __device__ __forceinline__ SlotState init_slot(const Params* P, int slot, int lane,
-                                               const double* guess, const double* yguess) {
+                                               const double* guess, const double* yguess,
+                                               int warm = 0) {
   const Dims& d = P->d;
   const Layout& L = P->L;
   double* f = P->f64 + (long long)slot * L.slot_f64;
@@ -175,9 +180,17 @@ __device__ __forceinline__ SlotState init_slot(const Params* P, int slot, int la
       IneqRow row = ineq_row(d, th, th + d.th_x, r);
       v = row.gval;
     }
-    w[i] = push_into_bounds(vi.kind, v);
-    zl[i] = has_lower(vi.kind) ? 1.0 : 0.0;
-    zu[i] = has_upper(vi.kind) ? 1.0 : 0.0;
+    if (warm) {
+      const double mu0 = P->opt.warm_mu, k = P->opt.warm_push;
+      v = push_into_bounds(vi.kind, v, k, k);
+      w[i] = v;
+      zl[i] = has_lower(vi.kind) ? mu0 / (v - 0.0) : 0.0;
+      zu[i] = has_upper(vi.kind) ? mu0 / (kUmax - v) : 0.0;
+    } else {
+      w[i] = push_into_bounds(vi.kind, v, kBoundPush, kBoundFrac);
+      zl[i] = has_lower(vi.kind) ? 1.0 : 0.0;
+      zu[i] = has_upper(vi.kind) ? 1.0 : 0.0;
+    }
     f[L.xr + i] = 0.0;
   }
   for (int i = lane; i < 2 * d.m; i += 32) {
@@ -197,7 +210,7 @@ __device__ __forceinline__ SlotState init_slot(const Params* P, int slot, int la
   S.mode = MODE_NORMAL;
   S.need_init = 1;
   S.need_y_ls = yguess ? 0 : 1;
-  S.mu = P->opt.mu_init;
+  S.mu = warm ? P->opt.warm_mu : P->opt.mu_init;
   S.problem_id = slot;
   return S;
 }
@@ -217,11 +230,15 @@ __global__ void init_kernel(const Params* __restrict__ P, int first, int count,
 // Iteration-level batching over a queue (Sec. V): each warp owns one slot;
 // when its problem terminates it writes the problem's results and refills the
 // slot with the next problem of the queue, so no slot idles while the queue
-// holds work.
+// holds work.  With x_guess (n_queue x n primal rows) every problem starts
+// from its warm starting point; a warm-started run that has not ended
+// converged (the scaled KKT test E_0 <= tol) within opt.warm_max_iter
+// iterations is rerun from the cold start in the same slot.
 template <class TB, class TF>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     queue_kernel(const Params* __restrict__ P, const double* __restrict__ theta_q, int n_queue,
-                 int n_warps, double* __restrict__ x_out, bipm_result* __restrict__ res_out) {
+                 int n_warps, double* __restrict__ x_out, bipm_result* __restrict__ res_out,
+                 const double* __restrict__ x_guess) {
   extern __shared__ __align__(16) char smem_all[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -237,11 +254,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     double* th = P->theta + (long long)slot * d.n_theta;
     for (int i = lane; i < d.n_theta; i += 32) th[i] = theta_q[(long long)id * d.n_theta + i];
     __syncwarp();
-    SlotState S = init_slot(P, slot, lane, nullptr, nullptr);
+    const double* gq = x_guess ? x_guess + (long long)id * d.n : nullptr;
+    SlotState S = init_slot(P, slot, lane, gq, nullptr, gq != nullptr);
     S.problem_id = id;
     Ctx<TB, TF> c;
     make_ctx(c, P, slot, lane, 32, nullptr, smem);
-    run_slot(c, S, 0, 0);
+    run_slot(c, S, 0, gq ? P->opt.warm_max_iter : 0);
+    int warm = gq ? 1 : 0, warm_iters = 0;
+    if (gq && S.status != BIPM_CONVERGED) {
+      warm = 2;
+      warm_iters = S.iter;
+      S = init_slot(P, slot, lane, nullptr, nullptr, 0);
+      S.problem_id = id;
+      make_ctx(c, P, slot, lane, 32, nullptr, smem);
+      run_slot(c, S, 0, 0);
+    }
     const double* w = c.f + P->L.x;
     if (x_out)
       for (int i = lane; i < d.n; i += 32) x_out[(long long)id * d.n + i] = w[i];
@@ -257,6 +284,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
       r.resto_iters = S.n_resto_iter;
       r.fact32 = S.n_fact32;
       r.solve32 = S.n_solve32;
+      r.warm = warm;
+      r.warm_iters = warm_iters;
       r.obj = S.obj;
       r.kkt_err = S.kkt;
       res_out[id] = r;

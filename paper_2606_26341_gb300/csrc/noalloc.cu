@@ -175,7 +175,8 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
   int n_queue = count;
   int n_warps = slots;
   int blocks = (slots + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  void* args[] = {&dP, &theta, &n_queue, &n_warps, &x_out, &results};
+  const double* no_guess = nullptr;
+  void* args[] = {&dP, &theta, &n_queue, &n_warps, &x_out, &results, &no_guess};
   cudaError_t e = cudaLaunchKernel(kfn, dim3(blocks), dim3(32 * kWarpsPerBlock), args, smem, stream);
   if (e != cudaSuccess) return sfail(BIPM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   e = cudaStreamSynchronize(stream);

@@ -125,3 +125,22 @@ def oracle_kkt_error(desc, theta, x, y, zl, zu, tol=1e-6):
     c = nlp.c(x)
     return ipm.opt_error(nlp, np.asarray(x), np.asarray(y), np.asarray(zl), np.asarray(zu), g, J, c,
                          0.0, opt)
+
+
+def oracle_warm_case(job):
+    """Oracle cold solve of one problem, a perturbed encoding of its solution
+    decoded to a warm starting point, and the oracle's warm-started solve from
+    it.  Returns (guess, status, iterations, x, cold iterations)."""
+    import torch
+
+    from oracle import warm
+
+    desc, theta, j = job
+    nlp = QuadNLP(desc, theta)
+    cold, _ = ipm.solve(nlp)
+    o = warm.encode(desc, theta, cold.normal.x)
+    rng = np.random.default_rng(100 + j)
+    o = (o + 0.05 * rng.standard_normal(o.size)).astype(np.float32).astype(np.float64)
+    guess = warm.decode(desc, theta, o, lambda s: nlp.ineq(torch.as_tensor(s)).numpy())
+    st, _ = ipm.solve(nlp, x0=guess, opt=warm.warm_options())
+    return guess, st.status, st.iter, st.normal.x, cold.iter

@@ -10,6 +10,7 @@ Every problem is drawn from its own counter-based SplitMix64 stream keyed by
 (workload seed, problem id), so problem j can be regenerated alone.
 """
 
+from .mlp_init import mlp_init  # noqa: F401
 from .quadrotor import (  # noqa: F401
     WORKLOADS,
     ProblemDesc,
