@@ -199,10 +199,12 @@ def run_ours(args):
 
     # chosen form: the autotuner's pick among the FP32 variants (untimed)
     if args.only_mixed:
-        best = bipm.Options(precision=1, fp32_switch=1e2)
+        best = bipm.Options(precision=1, fp32_switch=args.fp32_switch)
         tune_table = []
     else:
-        best, tune_table = autotune.autotune(desc, theta_wdev[: min(B, 2048)], B, stream=stream)
+        # the sample runs in the timed regime: a queue of twice the slot count
+        _, theta_t = make_batch(WORKLOAD, 2 * B, first_id=10_000_000 + rank * 2 * B)
+        best, tune_table = autotune.autotune(desc, torch.as_tensor(theta_t, device=dev), B, stream=stream)
 
     def timed_queue(options):
         """W untimed warm-up steps, then K timed steps as one queue through B slots."""
@@ -499,6 +501,8 @@ def main():
     ap.add_argument("--batch", type=int, default=BATCH, help="problems per GPU (profiling runs only)")
     ap.add_argument("--only-mixed", action="store_true", help="skip the FP64 form (profiling runs only)")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--fp32-switch", type=float, default=1e2,
+                    help="fp32_switch of the form --only-mixed runs (profiling runs only)")
     ap.add_argument("--warm-train", type=int, default=16384, help="training problems of the warm-start leg")
     ap.add_argument("--warm-epochs", type=int, default=30)
     ap.add_argument("--warm-batch", type=int, default=16384, help="problems of the warm-start leg")

@@ -6,7 +6,10 @@ double-float) and, for the FP32 form, the barrier scale above which an
 iteration falls back to an FP64 factorisation (``fp32_switch``; negative =
 FP32 derivative blocks with an FP64 factorisation).  ``autotune`` runs each candidate on a sample of the
 workload through the queue (iteration-level batching) path and returns the
-fastest in converged solves per second.  Everything it runs is the CUDA path.
+fastest in converged solves per second.  The sample should hold at least twice
+as many problems as the batch has slots, so that it runs in the same regime as
+a long queue (every resident warp busy, spare slots for stragglers) rather
+than in the ramp-down at its end.  Everything it runs is the CUDA path.
 """
 
 from __future__ import annotations

@@ -90,6 +90,13 @@ Layout make_layout(const Dims& d, int precision) {
   L.sig = take(L.nw);
   L.dsv = take(N * d.ni);
   L.ev = take(N * d.ni);
+  L.rds = take(N * d.ni);
+  L.evr = take(N * d.ni);
+  L.qpos = take(N * 9LL * d.nq * d.nq);
+  L.qin = take(N * 3LL * d.nq);
+  L.wrow = take(N * d.ni);
+  L.igr = take(N * 3LL * d.ni);
+  L.fdg = take((N + 1) * nx + N * nu);
   L.ipv = take(m);
   L.inv = take(m);
   L.dv = take(m);
@@ -290,7 +297,7 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
   if (cudaMalloc(&b->theta, cap * d.n_theta * sizeof(double) + 8) != cudaSuccess)
     return cleanup(BIPM_ENOMEM, "parameters");
   if (cudaMalloc(&b->st, cap * sizeof(SlotState)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "states");
-  if (cudaMalloc(&b->counter, sizeof(int)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "counter");
+  if (cudaMalloc(&b->counter, 2 * sizeof(int)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "counter");
   if (cudaMalloc(&b->dparams, sizeof(Params)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "params");
   if (cudaMemset(b->f64, 0, cap * b->L.slot_f64 * sizeof(double)) != cudaSuccess)
     return cleanup(BIPM_ECUDA, "memset");
@@ -346,6 +353,16 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
         per_sm_b < 1)
       return cleanup(BIPM_ECUDA, "block kernel does not fit on an SM");
     b->block_blocks = std::max(1, std::min((int)cap, sms * per_sm_b));
+  }
+  // queue schedule: one slot per resident warp, the remaining slots are spares
+  // for parking stragglers (finished by block teams after the queue drains)
+  {
+    const int warps = std::min(capacity, b->blocks * kWarpsPerBlock);
+    P.spare_counter = b->counter + 1;
+    P.n_spare = std::max(0, capacity - warps);
+    P.visit_cap = P.n_spare > 0 ? kQueueVisit : 0;
+    if (cudaMemcpy(b->dparams, &P, sizeof(P), cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup(BIPM_ECUDA, "params copy");
   }
   *out = b;
   g_err.clear();
@@ -412,6 +429,32 @@ int bipm_solve(bipm_batch* b) {
   return run_iterations(b, 0);
 }
 
+// every slot empty before a queue solve (spare slots must not look running)
+__global__ void reset_states(const Params* __restrict__ P) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P->n_slots; i += gridDim.x * blockDim.x) {
+    P->st[i].status = BIPM_EMPTY;
+    P->st[i].parked = 0;
+  }
+}
+
+// results of the parked stragglers the block teams finished (one warp per slot)
+__global__ void queue_writeout(const Params* __restrict__ P, double* __restrict__ x_out,
+                               bipm_result* __restrict__ res_out) {
+  const int lane = threadIdx.x & 31;
+  const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (slot >= P->n_slots) return;
+  const SlotState S = P->st[slot];
+  if (!S.parked) return;
+  const int n = P->d.n;
+  const double* w = P->f64 + (long long)slot * P->L.slot_f64 + P->L.x;
+  if (x_out)
+    for (int i = lane; i < n; i += 32) x_out[(long long)S.problem_id * n + i] = w[i];
+  if (lane == 0) {
+    res_out[S.problem_id] = make_result(S, S.warm_flag, S.warm_it);
+    P->st[slot].parked = 0;
+  }
+}
+
 static int solve_queue_impl(bipm_batch* b, const double* theta_queue, const double* x_guess, int n_queue,
                             double* x_out, bipm_result* results, int on_device) {
   if (!b) return fail(BIPM_EINVAL, "null batch");
@@ -439,13 +482,28 @@ static int solve_queue_impl(bipm_batch* b, const double* theta_queue, const doub
     CUDA_TRY(cudaMemcpyAsync((void*)th_dev, theta_queue, tb, cudaMemcpyHostToDevice, b->stream));
     if (x_guess) CUDA_TRY(cudaMemcpyAsync((void*)g_dev, x_guess, gb, cudaMemcpyHostToDevice, b->stream));
   }
-  // one slot per resident warp
+  // one slot per resident warp; the other slots take parked stragglers
   int warps = std::min(b->capacity, b->blocks * kWarpsPerBlock);
   int blocks = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
+  const bool spares = b->capacity > warps;
+  CUDA_TRY(cudaMemsetAsync(b->counter, 0, 2 * sizeof(int), b->stream));
+  if (spares) {
+    reset_states<<<std::max(1, std::min(1024, (b->capacity + 255) / 256)), 256, 0, b->stream>>>(b->dparams);
+    CUDA_TRY(cudaGetLastError());
+  }
   void* args[] = {&b->dparams, &th_dev, &n_queue, &warps, &x_dev, &r_dev, &g_dev};
   CUDA_TRY(cudaLaunchKernel(queue_kernel_ptr(b->opt.precision), dim3(blocks), dim3(32 * kWarpsPerBlock),
                             args, (size_t)b->smem_per_warp * kWarpsPerBlock, b->stream));
+  if (spares) {
+    // block teams finish the parked stragglers, then their results go out
+    int n_iter = 0;
+    CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
+    void* args2[] = {&b->dparams, &n_iter};
+    CUDA_TRY(cudaLaunchKernel(block_kernel_ptr(b->opt.precision), dim3(b->block_blocks), dim3(kBlockTeam),
+                              args2, (size_t)b->smem_per_warp + 128, b->stream));
+    queue_writeout<<<(b->capacity * 32 + 255) / 256, 256, 0, b->stream>>>(b->dparams, x_dev, r_dev);
+    CUDA_TRY(cudaGetLastError());
+  }
   if (!on_device) {
     if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, x_dev, xb, cudaMemcpyDeviceToHost, b->stream));
     CUDA_TRY(cudaMemcpyAsync(results, r_dev, rb, cudaMemcpyDeviceToHost, b->stream));

@@ -171,6 +171,10 @@ struct Layout {
   // FP64 arrays
   long long x, zl, zu, y, xt, c, ct, csoc, gf, jty, gphi, xr, xref, sig;
   long long dsv, ev, ipv, inv, dv;  // condensation diagonals (slacks / rows)
+  long long rds, evr;               // 1 / D_s and E / D_s per slack
+  long long qpos, qin, wrow;        // condensed inequality terms (factorisation / solve)
+  long long igr;                    // inequality-row position gradients at the iterate (3 per row)
+  long long fdg;                    // diagonal terms of an FP64 factorisation ((N+1) nx + N nu)
   long long rhs, sol, rhs2, sol2, res, corr, rct;
   long long filt, filt_r;
   long long f64_fac;  // FP64 factor arrays (mixed precision: escalation and LS)
@@ -187,7 +191,10 @@ struct Layout {
 struct SlotState {
   int status, mode, iter, need_init, need_y_ls, tiny, tiny_r, n_filt, n_filt_r;
   int n_soc, n_resto_iter, n_inertia_corr, n_ir_steps, n_escalations, n_tiny, problem_id;
-  int n_fact, n_solve, n_trial, n_fact32, n_solve32, pad_;
+  int n_fact, n_solve, n_trial, n_fact32, n_solve32;
+  int parked;              // queue straggler left to the block teams (results pending)
+  int warm_flag, warm_it;  // warm-start outcome of a parked problem (bipm_result.warm / warm_iters)
+  int pad_;
   long long cyc[8];  // clock cycles per phase (see kPhase*)
   double mu, dw_last, theta_max, theta_min;
   double mu_r, dw_last_r, theta_max_r, theta_min_r, zeta, theta_ref;
@@ -206,6 +213,12 @@ struct Params {
   SlotState* st;      // n_slots
   int* work_counter;  // persistent scheduling counter
   int smem_per_warp;  // bytes of dynamic shared memory per warp
+  // queue stragglers: a problem still running after visit_cap iterations in a
+  // warp is parked in its slot (finished later by block teams) while the warp
+  // continues in one of the n_spare spare slots (spare_counter hands them out)
+  int* spare_counter;
+  int n_spare;
+  int visit_cap;
 };
 
 }  // namespace bipm

@@ -138,6 +138,32 @@ __device__ __forceinline__ int wkind(const Dims& d, int i) {
 __device__ __forceinline__ bool has_lower(int kind) { return kind != VK_FREE; }
 __device__ __forceinline__ bool has_upper(int kind) { return kind == VK_BOX; }
 
+// Bounded entries among the first `len` entries of a W-sized vector (len = n,
+// or n + 2m in restoration), numbered densely: b < N nu are the inputs (box
+// bounds), then the N ni slacks, then the elastics p, n (lower bounds).  FP64
+// instructions cost the same whatever the number of active lanes, so loops
+// over bounds run over this numbering with every lane busy instead of
+// skipping the free entries of a W-sized loop.
+__device__ __forceinline__ int n_bounded(const Dims& d, int len) {
+  return d.N * d.nu + d.N * d.ni + (len - d.n);
+}
+__device__ __forceinline__ int bnd_index(const Dims& d, int b, int& kind) {
+  const int nu_all = d.N * d.nu;
+  if (b < nu_all) {
+    const int k = b / d.nu;
+    kind = VK_BOX;
+    return off_u(d, k) + (b - k * d.nu);
+  }
+  b -= nu_all;
+  const int ni_all = d.N * d.ni;
+  kind = VK_LOWER;
+  if (b < ni_all) {
+    const int k = b / d.ni;
+    return off_s(d, k + 1) + (b - k * d.ni);
+  }
+  return d.n + (b - ni_all);
+}
+
 // ------------------------------------------------------ reference trajectory
 // reference state component j of quad q at stage k: circle position and
 // velocity, zero attitude and body rates (evaluated once per problem)
@@ -233,6 +259,88 @@ __device__ __forceinline__ double ineq_hess_at(const IneqRow& r, int i, int j) {
   double si = qi == r.q0 ? 1.0 : (qi == r.q1 ? -1.0 : 0.0);
   double sj = qj == r.q0 ? 1.0 : (qj == r.q1 ? -1.0 : 0.0);
   return r.hdiag * si * sj;
+}
+
+// Gradient of inequality j with respect to the positions (value not formed):
+// d g / d p_q0 = g[0..ncomp), and for a pair row d g / d p_q1 = -g.
+struct IneqGrad {
+  int q0, q1, ncomp;
+  double g[3];
+};
+__device__ __forceinline__ IneqGrad ineq_grad(const Dims& d, const double* th, const double* xk, int j) {
+  IneqGrad r;
+  r.q1 = -1;
+  const int nsq = d.nq * d.n_sph, ncq = d.nq * d.n_cyl;
+  if (j < nsq) {
+    const int q = j / d.n_sph, o = j - q * d.n_sph;
+    const double* s = th + d.th_sph + 4 * o;
+    const double* p = xk + 12 * q;
+    r.q0 = q;
+    r.ncomp = 3;
+    r.g[0] = 2 * (p[0] - s[0]); r.g[1] = 2 * (p[1] - s[1]); r.g[2] = 2 * (p[2] - s[2]);
+  } else if (j < nsq + ncq) {
+    const int jj = j - nsq;
+    const int q = jj / d.n_cyl, o = jj - q * d.n_cyl;
+    const double* s = th + d.th_cyl + 3 * o;
+    const double* p = xk + 12 * q;
+    r.q0 = q;
+    r.ncomp = 2;
+    r.g[0] = 2 * (p[0] - s[0]); r.g[1] = 2 * (p[1] - s[1]); r.g[2] = 0.0;
+  } else {
+    int rem = j - nsq - ncq;
+    int a = 0;
+    while (rem >= d.nq - 1 - a) { rem -= d.nq - 1 - a; ++a; }
+    const int b = a + 1 + rem;
+    const double* pa = xk + 12 * a;
+    const double* pb = xk + 12 * b;
+    r.q0 = a;
+    r.q1 = b;
+    r.ncomp = 3;
+    r.g[0] = 2 * (pa[0] - pb[0]); r.g[1] = 2 * (pa[1] - pb[1]); r.g[2] = 2 * (pa[2] - pb[2]);
+  }
+  return r;
+}
+// The same gradient read from the table fill_ineq_grad wrote for the iterate
+// (row t = (k - 1) ni + j of stage k >= 1).
+__device__ __forceinline__ IneqGrad ineq_grad_tab(const Dims& d, const double* igr, int t, int j) {
+  IneqGrad r;
+  r.q1 = -1;
+  const int nsq = d.nq * d.n_sph, ncq = d.nq * d.n_cyl;
+  if (j < nsq) {
+    r.q0 = j / d.n_sph;
+    r.ncomp = 3;
+  } else if (j < nsq + ncq) {
+    r.q0 = (j - nsq) / d.n_cyl;
+    r.ncomp = 2;
+  } else {
+    int rem = j - nsq - ncq;
+    int a = 0;
+    while (rem >= d.nq - 1 - a) { rem -= d.nq - 1 - a; ++a; }
+    r.q0 = a;
+    r.q1 = a + 1 + rem;
+    r.ncomp = 3;
+  }
+  const double* g = igr + 3LL * t;
+  r.g[0] = g[0];
+  r.g[1] = g[1];
+  r.g[2] = g[2];
+  return r;
+}
+
+// component comp (< 3) of quad q of that gradient
+__device__ __forceinline__ double grad_pos(const IneqGrad& r, int q, int comp) {
+  if (comp >= r.ncomp) return 0.0;
+  if (q == r.q0) return r.g[comp];
+  if (q == r.q1) return -r.g[comp];
+  return 0.0;
+}
+// Hessian of inequality row r (squared distances: 2 I, pairs +-2 I) at
+// position components (qa, ca), (qb, cb)
+__device__ __forceinline__ double hess_pos(const IneqGrad& r, int qa, int ca, int qb, int cb) {
+  if (ca != cb || ca >= r.ncomp) return 0.0;
+  const double sa = qa == r.q0 ? 1.0 : (qa == r.q1 ? -1.0 : 0.0);
+  const double sb = qb == r.q0 ? 1.0 : (qb == r.q1 ? -1.0 : 0.0);
+  return 2.0 * sa * sb;
 }
 
 // ---------------------------------------------------------------- evaluation
@@ -464,10 +572,13 @@ __device__ __noinline__ void fill_sigma(Ctx<TB, TF>& c) {
   const double* zl = c.f + c.L.zl;
   const double* zu = c.f + c.L.zu;
   double* sg = c.f + c.L.sig;
-  for (int i = c.lane; i < c.nw; i += c.T) {
-    int kind = wkind(c.d, i);
-    double v = 0.0;
-    if (kind != VK_FREE) v = zl[i] / x[i];
+  for (int i = c.lane; i < c.nw; i += c.T) sg[i] = 0.0;
+  team_sync(c);
+  const int nb = n_bounded(c.d, c.nw);
+  for (int b = c.lane; b < nb; b += c.T) {
+    int kind;
+    const int i = bnd_index(c.d, b, kind);
+    double v = zl[i] / x[i];
     if (kind == VK_BOX) v += zu[i] / (kUmax - x[i]);
     sg[i] = v;
   }
@@ -492,6 +603,22 @@ __device__ __forceinline__ double obj_hdiag(Ctx<TB, TF>& c, int i, int flags) {
   return 0.0;
 }
 
+// Position gradients of every inequality row at the point x (the iterate),
+// one pass over all rows; factorisation, solves and the KKT mat-vec read them.
+template <class TB, class TF>
+__device__ __noinline__ void fill_ineq_grad(Ctx<TB, TF>& c, const double* x) {
+  const Dims& d = c.d;
+  double* igr = c.f + c.L.igr;
+  for (int t = c.lane; t < d.N * d.ni; t += c.T) {
+    const int k = 1 + t / d.ni, j = t - (k - 1) * d.ni;
+    const IneqGrad g = ineq_grad(d, c.th, x + off_x(d, k), j);
+    igr[3 * t] = g.g[0];
+    igr[3 * t + 1] = g.g[1];
+    igr[3 * t + 2] = g.g[2];
+  }
+  team_sync(c);
+}
+
 // Condensation diagonals for regularisation dw:
 //   slack (k, r):  D_s = H_ss + Sigma_s + dw,  E = D_s / (1 + D_s D_g)
 //   row i (restoration): 1/(Sigma_p + dw), 1/(Sigma_n + dw), D = their sum
@@ -504,6 +631,8 @@ __device__ __noinline__ void compute_diag(Ctx<TB, TF>& c, double dw, int flags) 
   double* ipv = c.f + c.L.ipv;
   double* inv = c.f + c.L.inv;
   double* dv = c.f + c.L.dv;
+  double* rds = c.f + c.L.rds;
+  double* evr = c.f + c.L.evr;
   const double* w = c.f + c.L.x;
   const double* zl = c.f + c.L.zl;
   LANE_LOOP(i, d.m) {
@@ -526,7 +655,47 @@ __device__ __noinline__ void compute_diag(Ctx<TB, TF>& c, double dw, int flags) 
     double ds = (flags & FF_IDENT) ? 1.0 : obj_hdiag(c, vi, flags) + sigma_of(c, vi) + dw;
     double dg = dv[row_ineq(d, k) + r];
     dsv[t] = ds;
-    ev[t] = ds / (1.0 + ds * dg);
+    rds[t] = 1.0 / ds;
+    if (c.resto) {
+      const double wr = 1.0 / (1.0 + ds * dg);
+      evr[t] = wr;
+      ev[t] = ds * wr;
+    } else {
+      evr[t] = 1.0;  // E = D_s when the row has no elastic term
+      ev[t] = ds;
+    }
+  }
+  team_sync(c);
+}
+
+
+
+// Position blocks of the condensed inequality rows for every stage at once,
+// with the condensation weights of the last compute_diag:
+//   qpos_k(a, b) = sum_r E_r g_r(a) g_r(b) + y_r H_r(a, b),
+// a, b over the 3 nq position components of stage k (no Hessian term in the
+// least-squares multiplier system).
+template <class TB, class TF>
+__device__ __noinline__ void ineq_blocks(Ctx<TB, TF>& c, int flags) {
+  const Dims& d = c.d;
+  const int lane = c.lane;
+  const double* ev = c.f + c.L.ev;
+  const int np = 3 * d.nq, npp = np * np;
+  const double* igr = c.f + c.L.igr;
+  const double* y = c.f + c.L.y;
+  double* qpos = c.f + c.L.qpos;
+  for (int e = lane; e < d.N * npp; e += c.T) {
+    const int k = 1 + e / npp, ab = e - (k - 1) * npp;
+    const int a = ab / np, b = ab - a * np;
+    const int qa = a / 3, ca = a - 3 * qa, qb = b / 3, cb = b - 3 * qb;
+    const double* yk = y + row_ineq(d, k);
+    double v = 0.0;
+    for (int r = 0; r < d.ni; ++r) {
+      const IneqGrad g = ineq_grad_tab(d, igr, (k - 1) * d.ni + r, r);
+      v += ev[(k - 1) * d.ni + r] * grad_pos(g, qa, ca) * grad_pos(g, qb, cb);
+      if (!(flags & FF_IDENT)) v += yk[r] * hess_pos(g, qa, ca, qb, cb);
+    }
+    qpos[e] = v;
   }
   team_sync(c);
 }
@@ -584,31 +753,30 @@ __device__ __forceinline__ char* scratch_base(const Ctx<TB, TF>& c) {
 // Q~_k (state block, written to Pb as TX), including the inequality terms.
 template <class TB, class TF, class TX>
 __device__ __noinline__ void add_state_block(Ctx<TB, TF>& c, int k, TX* Q, double dw, int flags,
-                                const double* y, bool accumulate) {
+                                const double* y, bool accumulate, const TX* xdg = nullptr) {
   const Dims& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx;
-  const double* x = c.f + c.L.x;
-  const double* ev = c.f + c.L.ev;
+  const double* qpos = c.f + c.L.qpos;
   const bool ident = flags & FF_IDENT;
+  (void)y;
   MAT_LOOP_BEGIN(i, j, nx, nx)
     TX v = accumulate ? Q[e] : (TX)0;
-    if (i == j) v += (TX)(obj_hdiag(c, off_x(d, k) + i, flags) + (ident ? 0.0 : dw));
+    if (i == j) {
+      if (xdg)
+        v += xdg[k * nx + i];
+      else
+        v += (TX)(obj_hdiag(c, off_x(d, k) + i, flags) + (ident ? 0.0 : dw));
+    }
     int qi = i / 12, qj = j / 12;
     int ci = i - 12 * qi, cj = j - 12 * qj;
     if (!ident && k < d.N && qi == qj && ci >= 6 && cj >= 6) {
       const TB* H = c.blk + c.L.H + ((long long)k * d.nq + qi) * 100;
       v += (TX)H[(cj - 6) * 10 + (ci - 6)];
     }
-    if (k >= 1 && ci < 3 && cj < 3) {
-      const double* xk = x + off_x(d, k);
-      const double* yi = y + row_ineq(d, k);
-      for (int r = 0; r < d.ni; ++r) {
-        IneqRow row = ineq_row(d, c.th, xk, r);
-        TX gi = (TX)ineq_grad_at(row, i), gj = (TX)ineq_grad_at(row, j);
-        v += (TX)ev[(k - 1) * d.ni + r] * gi * gj;
-        if (!ident) v += (TX)(yi[r] * ineq_hess_at(row, i, j));
-      }
+    if (k >= 1 && ci < 3 && cj < 3 && d.ni > 0) {
+      const int np = 3 * d.nq;
+      v += (TX)qpos[(long long)(k - 1) * np * np + (3 * qi + ci) * np + 3 * qj + cj];
     }
     Q[e] = v;
   MAT_LOOP_END(i, j)
@@ -640,6 +808,69 @@ __device__ inline double warp_cholesky(const C& c, double* a, int n) {
   }
   team_sync(c);
   return ratio;
+}
+
+// Cholesky of the nxn matrix in `a` (row-major, precision TX) in place by
+// the team; lower triangle holds L.  Returns false if a pivot is not positive
+// and finite (every thread reads the same pivot, so the return is uniform).
+template <class C, class TX>
+__device__ inline bool team_cholesky(const C& c, TX* a, int n) {
+  const int lane = c.lane;
+  for (int j = 0; j < n; ++j) {
+    team_sync(c);
+    const TX piv = a[j * n + j];
+    if (!(piv > (TX)0) || !isfinite(piv)) return false;
+    const TX l = sqrt(piv);
+    const TX il = (TX)1 / l;
+    team_sync(c);
+    if (lane == 0) a[j * n + j] = l;
+    for (int i = j + 1 + lane; i < n; i += c.T) a[i * n + j] *= il;
+    team_sync(c);
+    const int rem = n - j - 1;
+    for (int e = lane; e < rem * rem; e += c.T) {
+      const int i = j + 1 + e / rem, t = j + 1 + (e - (e / rem) * rem);
+      if (t <= i) a[i * n + t] -= a[i * n + j] * a[t * n + j];
+    }
+  }
+  team_sync(c);
+  return true;
+}
+
+// FP64 inertia test of the pivot blocks R^_k, k in [k0, N), that an FP32
+// factorisation assembled (stored as TX at R + k nu^2): one stage per thread,
+// LDL^T in FP64 in the scratch a64 (N nu^2 doubles).  Returns 0 if a pivot is
+// not positive, else 1, and the smallest ratio pivot / original diagonal.
+template <class C, class TX>
+__device__ inline int stage_pivot_check(const C& c, const TX* R, double* a64, int k0, int N, int nu,
+                                        double& ratio) {
+  int bad = 0;
+  double rmin = 1.0;
+  const int nn = nu * nu;
+  for (int k = k0 + c.lane; k < N; k += c.T) {
+    double* a = a64 + (long long)k * nn;
+    const TX* r = R + (long long)k * nn;
+    for (int e = 0; e < nn; ++e) a[e] = (double)r[e];
+    for (int j = 0; j < nu && !bad; ++j) {
+      // pivot d_j = a_jj - sum_t l_jt^2 d_t (d_t on the diagonal, l_jt below it)
+      double dj = a[j * nu + j];
+      for (int t = 0; t < j; ++t) dj -= a[j * nu + t] * a[j * nu + t] * a[t * nu + t];
+      if (!(dj > 0.0) || !isfinite(dj)) {
+        bad = 1;
+        break;
+      }
+      rmin = fmin(rmin, dj / (double)r[j * nu + j]);
+      const double inv = 1.0 / dj;
+      for (int i = j + 1; i < nu; ++i) {
+        double v = a[i * nu + j];
+        for (int t = 0; t < j; ++t) v -= a[i * nu + t] * a[j * nu + t] * a[t * nu + t];
+        a[i * nu + j] = v * inv;
+      }
+      a[j * nu + j] = dj;
+    }
+  }
+  bad = team_or(c, bad);
+  ratio = team_min(c, rmin);
+  return bad ? 0 : 1;
 }
 
 // Pivot ratio of a factorised matrix: min_j L_jj^2 / orig_jj
@@ -709,10 +940,41 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
   c.n_fact++;
   if (sizeof(TX) == 4) c.n_fact32++;
   compute_diag(c, dw, flags);
+  if (d.ni > 0) ineq_blocks(c, flags);
   double min_ratio = 1.0;
+  // FP32 factorisation (never in restoration): the stage loop runs without
+  // FP64 instructions.  The diagonal terms are formed once in FP64 and stored
+  // in TX, the pivot blocks R^_k are kept for one FP64 inertia test of all
+  // stages after the recursion; both live in the restoration-only arrays
+  // LM (R^_k) and Yr (diagonals), which an FP32 factorisation never uses.
+  constexpr bool f32 = sizeof(TX) == 4;
+  constexpr bool pre_diag = f32 || std::is_same<TX, double>::value;
+  const TX* xdg = nullptr;
+  const TX* udg = nullptr;
+  int k_fail32 = -1;
+  if constexpr (pre_diag) {
+    // FP32: the restoration-only array Yr; FP64: a workspace array of its own
+    TX* dg;
+    if constexpr (f32)
+      dg = F.Yr;
+    else
+      dg = c.f + c.L.fdg;
+    LANE_LOOP(e, (N + 1) * nx) {
+      const int k = e / nx, i = e - k * nx;
+      dg[e] = (TX)(obj_hdiag(c, off_x(d, k) + i, flags) + (ident ? 0.0 : dw));
+    }
+    LANE_LOOP(e, N * nu) {
+      const int k = e / nu, a = e - k * nu;
+      const int ui = off_u(d, k) + a;
+      dg[(N + 1) * nx + e] = (TX)(obj_hdiag(c, ui, flags) + (ident ? 0.0 : sigma_of(c, ui) + dw));
+    }
+    team_sync(c);
+    xdg = dg;
+    udg = dg + (N + 1) * nx;
+  }
 
   // terminal block P_N = Q~_N
-  add_state_block<TB, TF, TX>(c, N, s.Pb, dw, flags, y, false);
+  add_state_block<TB, TF, TX>(c, N, s.Pb, dw, flags, y, false, xdg);
   team_sync(c);
   if (resto) {
     if (!resto_transform<TB, TF, TX>(c, s.Pb, dv + row_dyn(d, N - 1), F.LM + (long long)N * nx * nx,
@@ -729,11 +991,22 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
     LANE_LOOP(e, 144 * nq) s.Ab[e] = (TX)Ag[e];
     LANE_LOOP(e, 48 * nq) s.Bb[e] = (TX)Bg[e];
     team_sync(c);
-    // PA = P~ A, PB = P~ B (block-diagonal A, B; column-major blocks)
-    MAT_LOOP_BEGIN(i, col, nx, nx)
-      int q = col / 12, cc = col - 12 * q;
-      s.PA[e] = dot12(s.Pb + i * nx + 12 * q, 1, s.Ab + q * 144 + cc * 12, 1);
-    MAT_LOOP_END(i, col)
+    // PA = P~ A, PB = P~ B (block-diagonal A, B; column-major blocks).  The
+    // first six columns of each A block are constant (p and v enter F
+    // affinely): column c < 3 is e_c, column c in 3..5 is e_c + dt e_(c-3),
+    // with dt read from the stored block.  They cost a copy or one FMA; the
+    // twelve-term products run over the other six columns only, in passes of
+    // their own.
+    const int n6 = 6 * nq;
+    for (int e = lane; e < nx * n6; e += c.T) {
+      const int i = e / n6, r6 = e - i * n6, q = r6 / 6, cc = r6 - 6 * q;
+      const TX* prow = s.Pb + i * nx + 12 * q;
+      s.PA[i * nx + 12 * q + cc] = cc < 3 ? prow[cc] : prow[cc - 3] * s.Ab[q * 144 + cc * 12 + cc - 3] + prow[cc];
+    }
+    for (int e = lane; e < nx * n6; e += c.T) {
+      const int i = e / n6, r6 = e - i * n6, q = r6 / 6, cc = 6 + r6 - 6 * q;
+      s.PA[i * nx + 12 * q + cc] = dot12(s.Pb + i * nx + 12 * q, 1, s.Ab + q * 144 + cc * 12, 1);
+    }
     MAT_LOOP_BEGIN(i, col, nx, nu)
       int q = col >> 2, cc = col & 3;
       s.PB[e] = dot12(s.Pb + i * nx + 12 * q, 1, s.Bb + q * 48 + cc * 12, 1);
@@ -743,14 +1016,25 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
     MAT_LOOP_BEGIN(a, b, nu, nu)
       int qa = a >> 2, ca = a & 3;
       TX acc = dot12(s.Bb + qa * 48 + ca * 12, 1, s.PB + (12 * qa) * nu + b, nu);
-      int ui = off_u(d, k) + a;
-      if (a == b) acc += (TX)(obj_hdiag(c, ui, flags) + (ident ? 0.0 : sigma_of(c, ui) + dw));
+      if (a == b) {
+        if constexpr (pre_diag) {
+          acc += udg[k * nu + a];
+        } else {
+          const int ui = off_u(d, k) + a;
+          acc += (TX)(obj_hdiag(c, ui, flags) + (ident ? 0.0 : sigma_of(c, ui) + dw));
+        }
+      }
       int qb = b >> 2;
       if (!ident && qa == qb) {
         const TB* H = c.blk + c.L.H + ((long long)k * nq + qa) * 100;
         acc += (TX)H[(6 + (b & 3)) * 10 + (6 + ca)];
       }
-      s.R64[e] = (double)acc;
+      if constexpr (f32) {
+        s.Rh[e] = acc;
+        F.LM[(long long)k * nu * nu + e] = acc;
+      } else {
+        s.R64[e] = (double)acc;
+      }
     MAT_LOOP_END(a, b)
     MAT_LOOP_BEGIN(a, col, nu, nx)
       int qa = a >> 2, ca = a & 3;
@@ -763,54 +1047,76 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
       s.Sh[e] = acc;
     MAT_LOOP_END(a, col)
     team_sync(c);
-    // Q^ = A^T P~ A + Q~_k (overwrites Pb)
-    MAT_LOOP_BEGIN(i, col, nx, nx)
-      int q = i / 12, ci = i - 12 * q;
-      s.Pb[e] = dot12(s.Ab + q * 144 + ci * 12, 1, s.PA + (12 * q) * nx + col, nx);
-    MAT_LOOP_END(i, col)
+    // Q^ = A^T P~ A + Q~_k (overwrites Pb); rows of the constant columns of A
+    // are a copy or one FMA, the others twelve-term products
+    for (int e = lane; e < n6 * nx; e += c.T) {
+      const int r6 = e / nx, col = e - r6 * nx, q = r6 / 6, ci = r6 - 6 * q;
+      const TX* pa = s.PA + (12 * q) * nx + col;
+      s.Pb[(12 * q + ci) * nx + col] =
+          ci < 3 ? pa[ci * nx] : pa[(ci - 3) * nx] * s.Ab[q * 144 + ci * 12 + ci - 3] + pa[ci * nx];
+    }
+    for (int e = lane; e < n6 * nx; e += c.T) {
+      const int r6 = e / nx, col = e - r6 * nx, q = r6 / 6, ci = 6 + r6 - 6 * q;
+      s.Pb[(12 * q + ci) * nx + col] = dot12(s.Ab + q * 144 + ci * 12, 1, s.PA + (12 * q) * nx + col, nx);
+    }
     team_sync(c);
-    add_state_block<TB, TF, TX>(c, k, s.Pb, dw, flags, y, true);
-    // Cholesky of R^ in FP64: the inertia test
-    double* R64 = s.R64;
-    team_sync(c);
-    double diag_j[32];
-    for (int j = 0; j < nu && j < 32; ++j) diag_j[j] = R64[j * nu + j];
-    if (warp_cholesky(c, R64, nu) < 0.0) return 0;
-    if (sizeof(TX) == 4) min_ratio = fmin(min_ratio, pivot_ratio(R64, diag_j, nu < 32 ? nu : 32));
-    // Cholesky factor in the factorisation precision (stored, and used for K)
-    LANE_LOOP(e, nu * nu) s.Rh[e] = (TX)R64[e];
-    team_sync(c);
+    add_state_block<TB, TF, TX>(c, k, s.Pb, dw, flags, y, true, xdg);
+    if constexpr (f32) {
+      // FP32 Cholesky of R^ for the gains; the FP64 inertia test follows the
+      // recursion.  A pivot FP32 cannot factor ends the recursion here.
+      if (!team_cholesky(c, s.Rh, nu)) {
+        k_fail32 = k;
+        break;
+      }
+      LANE_LOOP(e, nu * nu) if (e % (nu + 1) == 0) s.Rh[e] = (TX)1 / s.Rh[e];
+      team_sync(c);
+    } else {
+      // Cholesky of R^ in FP64: the inertia test
+      double* R64 = s.R64;
+      team_sync(c);
+      if (warp_cholesky(c, R64, nu) < 0.0) return 0;
+      // Cholesky factor in the factorisation precision (stored, and used for K);
+      // the diagonal is stored as its reciprocal: every use of L_ii divides by it
+      LANE_LOOP(e, nu * nu) s.Rh[e] = (TX)(e % (nu + 1) == 0 ? 1.0 / R64[e] : R64[e]);
+      team_sync(c);
+    }
     // K = -R^{-1} S^: one column per lane
     for (int col = lane; col < nx; col += c.T) {
       TX z[32];
       for (int i = 0; i < nu; ++i) {
         TX acc = s.Sh[i * nx + col];
         for (int t = 0; t < i; ++t) acc -= s.Rh[i * nu + t] * z[t];
-        z[i] = acc / s.Rh[i * nu + i];
+        z[i] = acc * s.Rh[i * nu + i];
       }
       for (int i = nu - 1; i >= 0; --i) {
         TX acc = z[i];
         for (int t = i + 1; t < nu; ++t) acc -= s.Rh[t * nu + i] * z[t];
-        z[i] = acc / s.Rh[i * nu + i];
+        z[i] = acc * s.Rh[i * nu + i];
       }
       for (int i = 0; i < nu; ++i) s.Kb[i * nx + col] = -z[i];
     }
     team_sync(c);
-    // P_k = Q^ + S^T K, symmetrised
-    MAT_LOOP_BEGIN(i, j, nx, nx)
-      TX a0 = 0, a1 = 0;
-      int a = 0;
-      for (; a + 1 < nu; a += 2) {
-        a0 += s.Sh[a * nx + i] * s.Kb[a * nx + j];
-        a1 += s.Sh[(a + 1) * nx + i] * s.Kb[(a + 1) * nx + j];
+    // P_k = Q^ + S^T K on the lower triangle, mirrored (exactly symmetric);
+    // in place: each thread reads lower entries and writes their mirror images
+    {
+      const int ntri = nx * (nx + 1) / 2;
+      for (int e = lane; e < ntri; e += c.T) {
+        int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (i * (i + 1) / 2 > e) --i;
+        while ((i + 1) * (i + 2) / 2 <= e) ++i;
+        const int j = e - i * (i + 1) / 2;
+        TX a0 = 0, a1 = 0;
+        int a = 0;
+        for (; a + 1 < nu; a += 2) {
+          a0 += s.Sh[a * nx + i] * s.Kb[a * nx + j];
+          a1 += s.Sh[(a + 1) * nx + i] * s.Kb[(a + 1) * nx + j];
+        }
+        if (a < nu) a0 += s.Sh[a * nx + i] * s.Kb[a * nx + j];
+        const TX v = s.Pb[i * nx + j] + (a0 + a1);
+        s.Pb[i * nx + j] = v;
+        s.Pb[j * nx + i] = v;
       }
-      if (a < nu) a0 += s.Sh[a * nx + i] * s.Kb[a * nx + j];
-      s.PA[e] = s.Pb[e] + (a0 + a1);
-    MAT_LOOP_END(i, j)
-    team_sync(c);
-    MAT_LOOP_BEGIN(i, j, nx, nx)
-      s.Pb[e] = (TX)0.5 * (s.PA[i * nx + j] + s.PA[j * nx + i]);
-    MAT_LOOP_END(i, j)
+    }
     TX* Kg = F.K + (long long)k * nu * nx;
     LANE_LOOP(e, nu * nx) Kg[e] = s.Kb[e];
     TX* Lg = F.Lr + (long long)k * nu * nu;
@@ -825,7 +1131,13 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
     LANE_LOOP(e, nx * nx) F.Pt[(long long)k * nx * nx + e] = s.Pb[e];
     team_sync(c);
   }
-  if (sizeof(TX) == 4 && min_ratio < 1e-5) return 2;
+  if constexpr (f32) {
+    // FP64 inertia test of every stage the recursion reached
+    team_sync(c);
+    const int k0 = k_fail32 >= 0 ? k_fail32 : 0;
+    if (!stage_pivot_check(c, F.LM, c.fac64.Lr, k0, N, nu, min_ratio)) return 0;
+    if (k_fail32 >= 0 || min_ratio < 1e-5) return 2;
+  }
   return 1;
 }
 
@@ -844,8 +1156,9 @@ __device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, d
   Scratch<TX> s = scratch<TX>(scratch_base<TX>(c), d);
   c.n_solve++;
   if (sizeof(TX) == 4) c.n_solve32++;
-  const double* dsv = c.f + c.L.dsv;
   const double* ev = c.f + c.L.ev;
+  const double* evr = c.f + c.L.evr;
+  const double* rds = c.f + c.L.rds;
   const double* ipv = c.f + c.L.ipv;
   const double* inv = c.f + c.L.inv;
   const double* dv = c.f + c.L.dv;
@@ -863,6 +1176,28 @@ __device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, d
   double* rct = c.f + c.L.rct;  // condensed constraint residual (m)
   LANE_LOOP(i, m) rct[i] = resto ? rc[i] + rp[i] * ipv[i] - rn[i] * inv[i] : rc[i];
   team_sync(c);
+  // inequality rows folded into q~ at the position components, every stage at
+  // once: qin_k(a) = sum_r g_r(a) w_r, w_r = E_r (r_s / D_s + r~_g)
+  const int np = 3 * d.nq;
+  double* wrow = c.f + c.L.wrow;
+  double* qin = c.f + c.L.qin;
+  const double* igr = c.f + c.L.igr;
+  if (d.ni > 0) {
+    for (int t = lane; t < N * d.ni; t += c.T) {
+      const int k = 1 + t / d.ni, rr = t - (k - 1) * d.ni;
+      wrow[t] = evr[t] * rx[off_s(d, k) + rr] + ev[t] * rct[row_ineq(d, k) + rr];
+    }
+    team_sync(c);
+    for (int e = lane; e < N * np; e += c.T) {
+      const int k = 1 + e / np, a = e - (k - 1) * np;
+      const int q = a / 3, comp = a - 3 * q;
+      double v = 0.0;
+      for (int rr = 0; rr < d.ni; ++rr)
+        v += grad_pos(ineq_grad_tab(d, igr, (k - 1) * d.ni + rr, rr), q, comp) * wrow[(k - 1) * d.ni + rr];
+      qin[e] = v;
+    }
+    team_sync(c);
+  }
   TX* pv = s.v0;  // p_k / p~_k
   TX* tv = s.v1;
   TX* gv = s.v2;  // nu entries (nu <= nx)
@@ -871,18 +1206,8 @@ __device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, d
   auto qtilde = [&](int k) {
     LANE_LOOP(i, nx) {
       double v = rx[off_x(d, k) + i];
-      int ci = i - 12 * (i / 12);
-      if (k >= 1 && ci < 3) {
-        const double* xk = x + off_x(d, k);
-        for (int rr = 0; rr < d.ni; ++rr) {
-          IneqRow row = ineq_row(d, c.th, xk, rr);
-          double g = ineq_grad_at(row, i);
-          if (g != 0.0) {
-            int t = (k - 1) * d.ni + rr;
-            v += g * ev[t] * (rx[off_s(d, k) + rr] / dsv[t] + rct[row_ineq(d, k) + rr]);
-          }
-        }
-      }
+      const int q = i / 12, ci = i - 12 * q;
+      if (k >= 1 && ci < 3 && d.ni > 0) v += qin[(k - 1) * np + 3 * q + ci];
       pv[i] = (TX)v;
     }
     team_sync(c);
@@ -914,50 +1239,69 @@ __device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, d
   if (resto) ptransform(N, dv + row_dyn(d, N - 1));
   LANE_LOOP(i, nx) F.ptv[(long long)N * nx + i] = pv[i];
   team_sync(c);
-  for (int k = N - 1; k >= 0; --k) {
-    const TX* Pt = F.Pt + (long long)(k + 1) * nx * nx;
+  // stage Jacobian blocks in the factorisation precision (converted once per
+  // stage when the blocks are stored in another precision)
+  auto stage_blocks = [&](int k, const TX*& Ab, const TX*& Bb) {
     const TB* Ag = c.blk + c.L.A + (long long)k * d.nq * 144;
     const TB* Bg = c.blk + c.L.B + (long long)k * d.nq * 48;
-    // t = P~_{k+1} d~_k + p~_{k+1},  d~_k = -r~_c(dyn_k)
+    if constexpr (std::is_same<TB, TX>::value) {
+      Ab = Ag;
+      Bb = Bg;
+    } else {
+      LANE_LOOP(e, 144 * d.nq) s.Ab[e] = (TX)Ag[e];
+      LANE_LOOP(e, 48 * d.nq) s.Bb[e] = (TX)Bg[e];
+      Ab = s.Ab;
+      Bb = s.Bb;
+    }
+  };
+  for (int k = N - 1; k >= 0; --k) {
+    const TX* Pt = F.Pt + (long long)(k + 1) * nx * nx;
+    const TX* Ab;
+    const TX* Bb;
+    stage_blocks(k, Ab, Bb);
+    // d~_k = -r~_c(dyn_k) into wv (free until p_k is formed)
+    LANE_LOOP(j, nx) wv[j] = (TX)(-rct[row_dyn(d, k) + j]);
+    team_sync(c);
+    // t = P~_{k+1} d~_k + p~_{k+1}
     LANE_LOOP(i, nx) {
       TX acc = pv[i];
-      for (int j = 0; j < nx; ++j) acc += Pt[i * nx + j] * (TX)(-rct[row_dyn(d, k) + j]);
+      for (int j = 0; j < nx; ++j) acc += Pt[i * nx + j] * wv[j];
       tv[i] = acc;
     }
     team_sync(c);
     // g^ = r_u + B^T t
     LANE_LOOP(a, nu) {
       int q = a / 4, ca = a - 4 * q;
-      const TB* b = Bg + q * 48 + ca * 12;
+      const TX* b = Bb + q * 48 + ca * 12;
       TX acc = (TX)rx[off_u(d, k) + a];
-      for (int rr = 0; rr < 12; ++rr) acc += (TX)b[rr] * tv[12 * q + rr];
+      for (int rr = 0; rr < 12; ++rr) acc += b[rr] * tv[12 * q + rr];
       gv[a] = acc;
     }
     team_sync(c);
-    // k_k = -R^{-1} g^ (lane 0)
+    // k_k = -R^{-1} g^ (lane 0; the stored factor holds 1 / L_ii on its diagonal)
     const TX* Lr = F.Lr + (long long)k * nu * nu;
     TX* kf = F.kff + (long long)k * nu;
     if (lane == 0) {
-      double z[32];
+      TX z[32];
       for (int i = 0; i < nu; ++i) {
-        double acc = (double)gv[i];
-        for (int t = 0; t < i; ++t) acc -= (double)Lr[i * nu + t] * z[t];
-        z[i] = acc / (double)Lr[i * nu + i];
+        TX acc = gv[i];
+        for (int t = 0; t < i; ++t) acc -= Lr[i * nu + t] * z[t];
+        z[i] = acc * Lr[i * nu + i];
       }
       for (int i = nu - 1; i >= 0; --i) {
-        double acc = z[i];
-        for (int t = i + 1; t < nu; ++t) acc -= (double)Lr[t * nu + i] * z[t];
-        z[i] = acc / (double)Lr[i * nu + i];
+        TX acc = z[i];
+        for (int t = i + 1; t < nu; ++t) acc -= Lr[t * nu + i] * z[t];
+        z[i] = acc * Lr[i * nu + i];
       }
-      for (int i = 0; i < nu; ++i) kf[i] = (TX)(-z[i]);
+      for (int i = 0; i < nu; ++i) kf[i] = -z[i];
     }
     // p_k = q~_k + A^T t + K^T g^
     const TX* Kg = F.K + (long long)k * nu * nx;
     LANE_LOOP(i, nx) {
       int q = i / 12, ci = i - 12 * q;
-      const TB* a = Ag + q * 144 + ci * 12;
+      const TX* a = Ab + q * 144 + ci * 12;
       TX acc = 0;
-      for (int rr = 0; rr < 12; ++rr) acc += (TX)a[rr] * tv[12 * q + rr];
+      for (int rr = 0; rr < 12; ++rr) acc += a[rr] * tv[12 * q + rr];
       for (int aa = 0; aa < nu; ++aa) acc += Kg[aa * nx + i] * gv[aa];
       wv[i] = acc;
     }
@@ -993,8 +1337,9 @@ __device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, d
     team_sync(c);
   }
   for (int k = 0; k < N; ++k) {
-    const TB* Ag = c.blk + c.L.A + (long long)k * d.nq * 144;
-    const TB* Bg = c.blk + c.L.B + (long long)k * d.nq * 48;
+    const TX* Ab;
+    const TX* Bb;
+    stage_blocks(k, Ab, Bb);
     const TX* Kg = F.K + (long long)k * nu * nx;
     const TX* kf = F.kff + (long long)k * nu;
     LANE_LOOP(a, nu) {
@@ -1008,8 +1353,8 @@ __device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, d
     LANE_LOOP(i, nx) {
       int q = i / 12, ri = i - 12 * q;
       TX acc = (TX)(-rct[row_dyn(d, k) + i]);
-      for (int j = 0; j < 12; ++j) acc += (TX)Ag[q * 144 + j * 12 + ri] * pv[12 * q + j];
-      for (int j = 0; j < 4; ++j) acc += (TX)Bg[q * 48 + j * 12 + ri] * gv[4 * q + j];
+      for (int j = 0; j < 12; ++j) acc += Ab[q * 144 + j * 12 + ri] * pv[12 * q + j];
+      for (int j = 0; j < 4; ++j) acc += Bb[q * 48 + j * 12 + ri] * gv[4 * q + j];
       wv[i] = acc;
     }
     team_sync(c);
@@ -1033,17 +1378,18 @@ __device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, d
   // inequality multipliers and slacks
   for (int t = lane; t < N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, rr = t - (t / d.ni) * d.ni;
-    IneqRow row = ineq_row(d, c.th, x + off_x(d, k), rr);
+    const IneqGrad g = ineq_grad_tab(d, igr, t, rr);
     double gdx = 0.0;
     const double* dxk = ox + off_x(d, k);
-    for (int comp = 0; comp < row.ncomp; ++comp) {
-      gdx += row.grad[comp] * dxk[12 * row.q0 + comp];
-      if (row.q1 >= 0) gdx += row.grad[3 + comp] * dxk[12 * row.q1 + comp];
+    for (int comp = 0; comp < g.ncomp; ++comp) {
+      gdx += g.g[comp] * dxk[12 * g.q0 + comp];
+      if (g.q1 >= 0) gdx -= g.g[comp] * dxk[12 * g.q1 + comp];
     }
     double rs = rx[off_s(d, k) + rr];
-    double dyi = ev[t] * (gdx + rs / dsv[t] + rct[row_ineq(d, k) + rr]);
+    // E (g dx + r_s / D_s + r~_g) with E / D_s = evr
+    double dyi = ev[t] * (gdx + rct[row_ineq(d, k) + rr]) + evr[t] * rs;
     oy[row_ineq(d, k) + rr] = dyi;
-    ox[off_s(d, k) + rr] = (dyi - rs) / dsv[t];
+    ox[off_s(d, k) + rr] = (dyi - rs) * rds[t];
   }
   if (resto) {
     team_sync(c);
@@ -1065,7 +1411,7 @@ __device__ __noinline__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double*
   const int lane = c.lane;
   const int nx = d.nx, nu = d.nu, N = d.N, n = d.n, m = d.m;
   const long long nwk = c.L.nw;
-  const double* x = c.f + c.L.x;
+  const double* igr = c.f + c.L.igr;
   const double* vy = v + nwk;
   double* oy = out + nwk;
   const int flags = c.resto ? FF_RESTO : 0;
@@ -1112,20 +1458,19 @@ __device__ __noinline__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double*
     int pc = t - (t / (3 * d.nq)) * (3 * d.nq);
     int q = pc / 3, comp = pc - 3 * (pc / 3);
     int i = 12 * q + comp;
-    const double* xk = x + off_x(d, k);
     const double* yi = y + row_ineq(d, k);
     const double* vyi = vy + row_ineq(d, k);
     const double* vx = v + off_x(d, k);
     double acc = 0.0;
     for (int r = 0; r < d.ni; ++r) {
-      IneqRow row = ineq_row(d, c.th, xk, r);
-      double g = ineq_grad_at(row, i);
-      acc += g * vyi[r];
-      for (int jq = 0; jq < d.nq; ++jq)
-        for (int jc = 0; jc < 3; ++jc) {
-          double h = ineq_hess_at(row, i, 12 * jq + jc);
-          if (h != 0.0) acc += yi[r] * h * vx[12 * jq + jc];
-        }
+      const IneqGrad g = ineq_grad_tab(d, igr, (k - 1) * d.ni + r, r);
+      const double gi = grad_pos(g, q, comp);
+      if (gi == 0.0 && q != g.q0 && q != g.q1) continue;
+      acc += gi * vyi[r];
+      // Hessian 2 I (pairs +-2 I) couples equal components of the row's quads
+      double hv = hess_pos(g, q, comp, g.q0, comp) * vx[12 * g.q0 + comp];
+      if (g.q1 >= 0) hv += hess_pos(g, q, comp, g.q1, comp) * vx[12 * g.q1 + comp];
+      acc += yi[r] * hv;
     }
     out[off_x(d, k) + i] += acc;
   }
@@ -1158,12 +1503,12 @@ __device__ __noinline__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double*
   }
   for (int t = lane; t < N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
-    IneqRow row = ineq_row(d, c.th, x + off_x(d, k), r);
+    const IneqGrad g = ineq_grad_tab(d, igr, t, r);
     const double* vx = v + off_x(d, k);
     double acc = -v[off_s(d, k) + r];
-    for (int comp = 0; comp < row.ncomp; ++comp) {
-      acc += row.grad[comp] * vx[12 * row.q0 + comp];
-      if (row.q1 >= 0) acc += row.grad[3 + comp] * vx[12 * row.q1 + comp];
+    for (int comp = 0; comp < g.ncomp; ++comp) {
+      acc += g.g[comp] * vx[12 * g.q0 + comp];
+      if (g.q1 >= 0) acc -= g.g[comp] * vx[12 * g.q1 + comp];
     }
     oy[row_ineq(d, k) + r] = acc;
   }

@@ -43,9 +43,10 @@ template <class TB, class TF>
 __device__ __noinline__ double barrier_phi(Ctx<TB, TF>& c, const double* w, double f, double mu, int len) {
   double acc = 0.0;
   int bad = 0;
-  for (int i = c.lane; i < len; i += c.T) {
-    int kind = wkind(c.d, i);
-    if (kind == VK_FREE) continue;
+  const int nb = n_bounded(c.d, len);
+  for (int b = c.lane; b < nb; b += c.T) {
+    int kind;
+    const int i = bnd_index(c.d, b, kind);
     double sl = w[i];
     if (!(sl > 0.0)) bad = 1;
     acc -= mu * log(sl);
@@ -103,10 +104,12 @@ __device__ __noinline__ double opt_error(Ctx<TB, TF>& c, const ErrParts& e, doub
   const double* zl = c.f + c.L.zl;
   const double* zu = c.f + c.L.zu;
   double comp = 0.0;
-  for (int i = c.lane; i < c.nw; i += c.T) {
-    int kind = wkind(c.d, i);
-    if (has_lower(kind)) comp = fmax(comp, fabs(w[i] * zl[i] - mu));
-    if (has_upper(kind)) comp = fmax(comp, fabs((kUmax - w[i]) * zu[i] - mu));
+  const int nbnd = n_bounded(c.d, c.nw);
+  for (int b = c.lane; b < nbnd; b += c.T) {
+    int kind;
+    const int i = bnd_index(c.d, b, kind);
+    comp = fmax(comp, fabs(w[i] * zl[i] - mu));
+    if (kind == VK_BOX) comp = fmax(comp, fabs((kUmax - w[i]) * zu[i] - mu));
   }
   comp = team_max(c, comp);
   double nb = fmax(1.0, e.nb);
@@ -120,9 +123,10 @@ __device__ __noinline__ double opt_error(Ctx<TB, TF>& c, const ErrParts& e, doub
 template <class TB, class TF>
 __device__ __noinline__ double ftb_primal(Ctx<TB, TF>& c, const double* w, const double* dw, double tau) {
   double a = 1.0;
-  for (int i = c.lane; i < c.nw; i += c.T) {
-    int kind = wkind(c.d, i);
-    if (kind == VK_FREE) continue;
+  const int nb = n_bounded(c.d, c.nw);
+  for (int b = c.lane; b < nb; b += c.T) {
+    int kind;
+    const int i = bnd_index(c.d, b, kind);
     if (dw[i] < 0.0) a = fmin(a, -tau * w[i] / dw[i]);
     if (kind == VK_BOX && dw[i] > 0.0) a = fmin(a, tau * (kUmax - w[i]) / dw[i]);
   }
@@ -290,7 +294,8 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF>& c, const double* r, doub
     if (rs == kGmresRestarts) break;
     double beta = norm2(res);
     double H[kGmresM + 1][kGmresM], cs[kGmresM], sn[kGmresM], g[kGmresM + 1];
-    for (int i = lane; i < len; i += c.T) V[at(i)] = res[at(i)] / beta;
+    const double ibeta = 1.0 / beta;
+    for (int i = lane; i < len; i += c.T) V[at(i)] = res[at(i)] * ibeta;
     g[0] = beta;
     team_sync(c);
     int jm = 0;
@@ -312,7 +317,8 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF>& c, const double* r, doub
       double hn = norm2(vn);
       H[j + 1][j] = hn;
       if (hn > 0.0) {
-        for (int t = lane; t < len; t += c.T) vn[at(t)] /= hn;
+        const double ihn = 1.0 / hn;
+        for (int t = lane; t < len; t += c.T) vn[at(t)] *= ihn;
         team_sync(c);
       }
       for (int i = 0; i < j; ++i) {  // previous Givens rotations
@@ -389,14 +395,14 @@ __device__ __noinline__ void kappa_sigma_reset(Ctx<TB, TF>& c, int len, double m
   double* w = c.f + c.L.x;
   double* zl = c.f + c.L.zl;
   double* zu = c.f + c.L.zu;
-  for (int i = c.lane; i < len; i += c.T) {
-    int kind = wkind(c.d, i);
-    if (has_lower(kind)) {
-      double s = w[i];
-      zl[i] = fmax(fmin(zl[i], kKappaSigma * mu / s), mu / (kKappaSigma * s));
-    }
-    if (has_upper(kind)) {
-      double s = kUmax - w[i];
+  const int nb = n_bounded(c.d, len);
+  for (int b = c.lane; b < nb; b += c.T) {
+    int kind;
+    const int i = bnd_index(c.d, b, kind);
+    double s = w[i];
+    zl[i] = fmax(fmin(zl[i], kKappaSigma * mu / s), mu / (kKappaSigma * s));
+    if (kind == VK_BOX) {
+      s = kUmax - w[i];
       zu[i] = fmax(fmin(zu[i], kKappaSigma * mu / s), mu / (kKappaSigma * s));
     }
   }
@@ -494,6 +500,7 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
     fph = resto_objective(c, w);
   }
   eval_grad(c, w, gf);
+  if (d.ni > 0) fill_ineq_grad(c, w);
   lap(PH_EVAL);
   if (!(isfinite(fph) && all_finite(c, cv, m) && all_finite(c, gf, c.nw))) {
     S.status = BIPM_EVAL_ERROR;
@@ -563,15 +570,26 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
   lap(PH_MISC);
   eval_blocks(c, w, y, true);
   lap(PH_DERIV);
+  LANE_LOOP(i, c.nw) gphi[i] = gf[i];
+  team_sync(c);
+  {
+    const int nb = n_bounded(d, c.nw);
+    for (int b = lane; b < nb; b += c.T) {
+      int kind;
+      const int i = bnd_index(d, b, kind);
+      double g = gf[i] - mu / w[i];
+      if (kind == VK_BOX)
+        g += mu / (kUmax - w[i]);
+      else
+        g += kKappaD * mu;
+      gphi[i] = g;
+    }
+  }
+  team_sync(c);
   LANE_LOOP(i, c.nw) {
-    int kind = wkind(d, i);
-    double g = gf[i];
-    if (has_lower(kind)) g -= mu / w[i];
-    if (has_upper(kind)) g += mu / (kUmax - w[i]);
-    if (kind == VK_LOWER) g += kKappaD * mu;
-    gphi[i] = g;
-    rhs[i] = g + jty[i];
-    rhs2[i] = g + jty[i];
+    double g = gphi[i] + jty[i];
+    rhs[i] = g;
+    rhs2[i] = g;
   }
   LANE_LOOP(i, m) rhs[nwk + i] = cv[i];
   team_sync(c);
@@ -627,26 +645,27 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
       const double* ddx = dir;
       const double* ddy = dir + nwk;
       double az = 1.0;
-      for (int i = lane; i < c.nw; i += c.T) {
-        int kind = wkind(d, i);
-        if (has_lower(kind)) {
-          double dzl = dz_lower(w[i], zl[i], mu, ddx[i]);
-          if (dzl < 0.0) az = fmin(az, -tau * zl[i] / dzl);
-        }
-        if (has_upper(kind)) {
+      const int nb = n_bounded(d, c.nw);
+      for (int b = lane; b < nb; b += c.T) {
+        int kind;
+        const int i = bnd_index(d, b, kind);
+        double dzl = dz_lower(w[i], zl[i], mu, ddx[i]);
+        if (dzl < 0.0) az = fmin(az, -tau * zl[i] / dzl);
+        if (kind == VK_BOX) {
           double dzu = dz_upper(kUmax - w[i], zu[i], mu, ddx[i]);
           if (dzu < 0.0) az = fmin(az, -tau * zu[i] / dzu);
         }
       }
       az = team_min(c, az);
-      for (int i = lane; i < c.nw; i += c.T) {
-        int kind = wkind(d, i);
-        double dzl = has_lower(kind) ? dz_lower(w[i], zl[i], mu, ddx[i]) : 0.0;
-        double dzu = has_upper(kind) ? dz_upper(kUmax - w[i], zu[i], mu, ddx[i]) : 0.0;
-        w[i] += alpha * ddx[i];
-        if (has_lower(kind)) zl[i] += az * dzl;
-        if (has_upper(kind)) zu[i] += az * dzu;
+      // bound multipliers from the step at the current point, then the primal step
+      for (int b = lane; b < nb; b += c.T) {
+        int kind;
+        const int i = bnd_index(d, b, kind);
+        zl[i] += az * dz_lower(w[i], zl[i], mu, ddx[i]);
+        if (kind == VK_BOX) zu[i] += az * dz_upper(kUmax - w[i], zu[i], mu, ddx[i]);
       }
+      team_sync(c);
+      LANE_LOOP(i, c.nw) w[i] += alpha * ddx[i];
       LANE_LOOP(i, m) y[i] += alpha * ddy[i];
       team_sync(c);
       kappa_sigma_reset(c, c.nw, mu);
@@ -655,10 +674,10 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
     };
 
     // tiny step (Table I row 4)
-    double rel = 0.0;
-    for (int i = lane; i < c.nw; i += c.T) rel = fmax(rel, fabs(dx[i]) / (1.0 + fabs(w[i])));
-    rel = team_max(c, rel);
-    if (rel < 10.0 * kEpsMach) {
+    // max_i |dx_i| / (1 + |w_i|) < 10 eps, tested without a division per entry
+    int big = 0;
+    for (int i = lane; i < c.nw; i += c.T) big |= fabs(dx[i]) >= 10.0 * kEpsMach * (1.0 + fabs(w[i]));
+    if (!team_or(c, big)) {
       accept(a_max, sol, false);
       tiny = 1;
       S.n_tiny++;

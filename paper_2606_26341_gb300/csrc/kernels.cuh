@@ -11,6 +11,7 @@ namespace bipm {
 constexpr int kWarpsPerBlock = 4;
 constexpr int kBlockTeam = 256;    // threads of a block team
 constexpr int kBulkVisit = 64;     // iterations per problem in the warp kernel
+constexpr int kQueueVisit = 96;    // iterations before a queue problem is parked for block teams
 
 template <class TB, class TF>
 __device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, int T, double* red,
@@ -234,6 +235,26 @@ __global__ void init_kernel(const Params* __restrict__ P, int first, int count,
 // from its warm starting point; a warm-started run that has not ended
 // converged (the scaled KKT test E_0 <= tol) within opt.warm_max_iter
 // iterations is rerun from the cold start in the same slot.
+// result record of a terminated problem
+__device__ __forceinline__ bipm_result make_result(const SlotState& S, int warm, int warm_iters) {
+  bipm_result r;
+  r.status = S.status;
+  r.iters = S.iter;
+  r.factorizations = S.n_fact;
+  r.solves = S.n_solve;
+  r.trials = S.n_trial;
+  r.ir_steps = S.n_ir_steps;
+  r.fp64_escalations = S.n_escalations;
+  r.resto_iters = S.n_resto_iter;
+  r.fact32 = S.n_fact32;
+  r.solve32 = S.n_solve32;
+  r.warm = warm;
+  r.warm_iters = warm_iters;
+  r.obj = S.obj;
+  r.kkt_err = S.kkt;
+  return r;
+}
+
 template <class TB, class TF>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     queue_kernel(const Params* __restrict__ P, const double* __restrict__ theta_q, int n_queue,
@@ -242,7 +263,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
   extern __shared__ __align__(16) char smem_all[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int slot = blockIdx.x * kWarpsPerBlock + warp;  // this warp's slot
+  int slot = blockIdx.x * kWarpsPerBlock + warp;  // this warp's slot
   if (slot >= n_warps) return;
   char* smem = smem_all + (size_t)warp * P->smem_per_warp;
   const Dims& d = P->d;
@@ -259,36 +280,47 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     S.problem_id = id;
     Ctx<TB, TF> c;
     make_ctx(c, P, slot, lane, 32, nullptr, smem);
-    run_slot(c, S, 0, gq ? P->opt.warm_max_iter : 0);
     int warm = gq ? 1 : 0, warm_iters = 0;
-    if (gq && S.status != BIPM_CONVERGED) {
-      warm = 2;
-      warm_iters = S.iter;
-      S = init_slot(P, slot, lane, nullptr, nullptr, 0);
-      S.problem_id = id;
-      make_ctx(c, P, slot, lane, 32, nullptr, smem);
-      run_slot(c, S, 0, 0);
+    bool done = false;
+    if (gq) {
+      run_slot(c, S, 0, P->opt.warm_max_iter);
+      if (S.status == BIPM_CONVERGED) {
+        done = true;
+      } else {
+        warm = 2;
+        warm_iters = S.iter;
+        S = init_slot(P, slot, lane, nullptr, nullptr, 0);
+        S.problem_id = id;
+        make_ctx(c, P, slot, lane, 32, nullptr, smem);
+      }
+    }
+    if (!done) {
+      run_slot(c, S, 0, P->visit_cap);
+      if (S.status == BIPM_RUNNING) {
+        // straggler: park it for the block teams when a spare slot is free
+        int ns = 0;
+        if (lane == 0) ns = atomicAdd(P->spare_counter, 1);
+        ns = __shfl_sync(0xffffffffu, ns, 0);
+        if (ns < P->n_spare) {
+          if (lane == 0) {
+            S.parked = 1;
+            S.warm_flag = warm;
+            S.warm_it = warm_iters;
+            P->st[slot] = S;
+          }
+          __syncwarp();
+          slot = n_warps + ns;
+          continue;
+        }
+        run_slot(c, S, 0, 0);
+      }
     }
     const double* w = c.f + P->L.x;
     if (x_out)
       for (int i = lane; i < d.n; i += 32) x_out[(long long)id * d.n + i] = w[i];
     if (lane == 0) {
-      bipm_result r;
-      r.status = S.status;
-      r.iters = S.iter;
-      r.factorizations = S.n_fact;
-      r.solves = S.n_solve;
-      r.trials = S.n_trial;
-      r.ir_steps = S.n_ir_steps;
-      r.fp64_escalations = S.n_escalations;
-      r.resto_iters = S.n_resto_iter;
-      r.fact32 = S.n_fact32;
-      r.solve32 = S.n_solve32;
-      r.warm = warm;
-      r.warm_iters = warm_iters;
-      r.obj = S.obj;
-      r.kkt_err = S.kkt;
-      res_out[id] = r;
+      res_out[id] = make_result(S, warm, warm_iters);
+      S.parked = 0;
       P->st[slot] = S;
     }
     __syncwarp();

@@ -289,3 +289,38 @@ def test_queue_matches_batch_solve(bipm, nav_oracle, precision):
         assert e_v(x_q[j].cpu().numpy(), x_b[j]) <= 1e-9
         assert e_v(x_h[j], x_b[j]) <= 1e-9
     assert np.all(rq["kkt_err"][conv] <= 1e-6)
+
+
+def test_queue_parks_stragglers_for_block_teams(bipm):
+    """The benchmark's queue shape (more slots than resident warps): problems
+    still running after the warp visit are parked and finished by block teams.
+    Every problem gets a result; the long-running (parked) ones agree with the
+    batch solve of the same problems and, on a sample, with the oracle."""
+    desc, theta = make_batch("track", 8192)
+    res = bipm.Batch(desc, 4096, bipm.Options(precision=1, fp32_switch=-1.0))
+    x = np.empty((8192, desc.n))
+    r = res.solve_queue(theta, x)
+    res.close()
+    assert np.all(r["status"] != bipm.RUNNING) and np.all(r["status"] != bipm.EMPTY)
+    conv = r["status"] == bipm.CONVERGED
+    assert conv.mean() >= 0.95
+    assert np.all(r["kkt_err"][conv] <= 1e-6)
+    long_ids = np.nonzero(r["iters"] > 96)[0]
+    assert len(long_ids) >= 20, len(long_ids)
+    sel = long_ids[:256]
+    with bipm.Batch(desc, len(sel), bipm.Options(precision=1, fp32_switch=-1.0)) as b:
+        b.set_problems(np.ascontiguousarray(theta[sel]))
+        b.solve()
+        st = b.get_stats()
+        xb, _, _, _ = b.get_solution()
+    same = r["status"][sel] == st["status"]
+    assert same.mean() >= 0.95
+    both = same & (st["status"] == bipm.CONVERGED) & (r["iters"][sel] == st["iters"])
+    for j in np.nonzero(both)[0]:
+        assert e_v(x[sel[j]], xb[j]) <= 1e-6
+    ids = [int(i) for i in long_ids[np.linspace(0, len(long_ids) - 1, 4).astype(int)]]
+    ores = oracle_solve_batch(desc, theta[ids])
+    for o, j in zip(ores, ids):
+        assert _same_outcome(bipm, r["status"][j], o["status"]), (j, r["status"][j], o["status"])
+        if o["status"] == ipm.CONVERGED and r["status"][j] == bipm.CONVERGED:
+            assert e_v(x[j], o["x"]) <= 1e-4, (j, e_v(x[j], o["x"]))
