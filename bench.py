@@ -292,6 +292,7 @@ def run_ours(args):
     }
 
     warm = None if args.no_warm else warm_leg(args, dev, stream, rank, barrier, reduce, MAX, SUM)
+    mixed = mixed_leg(args, dev, stream, barrier, reduce, MAX, SUM) if args.mixed > 0 else None
 
     if rank == 0:
         opt_desc = {"precision": best.precision, "fp32_switch": best.fp32_switch}
@@ -321,6 +322,8 @@ def run_ours(args):
         }
         if warm is not None:
             line["warm_start"] = warm
+        if mixed is not None:
+            line["uneven_queue"] = mixed
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(desc, theta, budget_s=args.cpu_budget)
         print(json.dumps(line), flush=True)
@@ -401,6 +404,45 @@ def warm_leg(args, dev, stream, rank, barrier, reduce, MAX, SUM):
                         "train_problems": args.warm_train, "usable": int(len(data.usable)),
                         "epochs": args.warm_epochs, "loss_first_last": [hist[0], hist[-1]],
                         "dataset_s": t_data, "train_s": t_train}}
+
+
+# ------------------------------------------------ uneven queue leg (opt-in)
+def mixed_leg(args, dev, stream, barrier, reduce, MAX, SUM):
+    """Problems of 1-8 quadrotors and horizons 10/20/30/50 (32 structure
+    classes, drawn uniformly) in one persistent launch of the mixed queue,
+    chosen form; args.mixed problems through args.mixed_slots slots.  Inputs
+    are device-resident; the call sizes its workspace before the timed launch
+    sequence, so the rate is taken from the host clock around the whole call
+    and includes that allocation."""
+    import torch
+
+    from paper_2606_26341_gb300 import bipm
+    from workloads import make_mixed
+
+    ws, rank, _ = dist_env()
+    classes, cls, theta = make_mixed(args.mixed, first_id=rank * args.mixed)
+    th = torch.as_tensor(theta, device=dev)
+    res = torch.empty(args.mixed * bipm.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    opts = bipm.Options(precision=1, fp32_switch=-1.0)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    bipm.solve_mixed(classes, cls, th, n_slots=args.mixed_slots, options=opts, results=res, stream=stream)
+    torch.cuda.synchronize()
+    dt = reduce(time.perf_counter() - t0, MAX)
+    barrier()
+    r = bipm.results_from_bytes(res.cpu().numpy())
+    conv = r["status"] == bipm.CONVERGED
+    per_nq = {}
+    for nq in range(1, 9):
+        sel = np.array([classes[k].nq == nq for k in cls])
+        per_nq[str(nq)] = {"problems": int(sel.sum()), "converged_frac": float(conv[sel].mean()),
+                           "iters_mean": float(r["iters"][sel].mean())}
+    return {"workload": f"uneven queue: {args.mixed} problems, 1-8 quadrotors (pairwise distance 0.4; one "
+                        f"sphere for a single quadrotor), N in 10/20/30/50, {args.mixed_slots} slots",
+            "value": reduce(float(conv.sum()), SUM) / dt, "unit": UNIT, "seconds": dt,
+            "converged_frac": float(conv.mean()), "iters_mean": float(r["iters"].mean()),
+            "per_quad_count": per_nq}
 
 
 def stats_record_bytes():
@@ -506,6 +548,8 @@ def main():
     ap.add_argument("--warm-train", type=int, default=16384, help="training problems of the warm-start leg")
     ap.add_argument("--warm-epochs", type=int, default=30)
     ap.add_argument("--warm-batch", type=int, default=16384, help="problems of the warm-start leg")
+    ap.add_argument("--mixed", type=int, default=0, help="problems of the uneven-queue leg (0: skip)")
+    ap.add_argument("--mixed-slots", type=int, default=3072, help="slots of the uneven-queue leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -222,6 +222,23 @@ int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, doub
 int bipm_solve_queue_warm(bipm_batch* b, const double* theta_queue, const double* x_guess, int n_queue,
                           double* x_out, bipm_result* results, int on_device);
 
+/* Iteration-level batching over problems of different structures (Sec. V:
+ * problems of uneven horizon and agent count in one persistent launch).
+ * classes[0..n_classes) are the structure classes (1 <= n_classes <= 64);
+ * problem i (0 <= i < n_queue) has class cls[i] (host array) and its
+ * parameter row (n_theta of its class) packed after those of problems 0..i-1
+ * in `theta`; its solution row (n of its class) goes to the same packed
+ * position in x_out (may be NULL) and its record to results[i].  All
+ * `n_slots` slots are sized for the largest class: one per resident warp,
+ * the rest take stragglers, which 256-thread block teams finish after the
+ * queue drains.  Precision 0 or 1 (options as for bipm_create_batch; NULL =
+ * defaults).  theta, x_out and results are device pointers (on_device = 1) or
+ * host pointers (0).  The call allocates its workspace, runs on cuda_stream
+ * (NULL = default stream) and returns when the solve has finished. */
+int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm_options* opt, int n_slots,
+                     const int* cls, const double* theta, int n_queue, double* x_out, bipm_result* results,
+                     int on_device, void* cuda_stream);
+
 /* One-shot solve that allocates nothing (the paper has no counterpart; this
  * is an addition for callers that cannot allocate device memory when they
  * need a solve: code inside a CUDA stream capture, where cudaMalloc is not

@@ -82,7 +82,7 @@ class IterateC(ctypes.Structure):
 
 EXPORTS = ["bipm_create_batch", "bipm_dims", "bipm_set_problems", "bipm_set_initial_guess",
            "bipm_solve", "bipm_step", "bipm_get_solution", "bipm_get_stats", "bipm_get_iterate",
-           "bipm_set_iterate", "bipm_get_phase_cycles", "bipm_solve_queue", "bipm_solve_queue_warm",
+           "bipm_set_iterate", "bipm_get_phase_cycles", "bipm_solve_queue", "bipm_solve_queue_warm", "bipm_solve_mixed",
            "bipm_solve_static", "bipm_warm_features", "bipm_warm_encode", "bipm_warm_decode",
            "bipm_mlp_create", "bipm_mlp_param_count", "bipm_mlp_set_params", "bipm_mlp_get_params",
            "bipm_mlp_forward", "bipm_mlp_loss_grad", "bipm_mlp_train_step", "bipm_mlp_destroy",
@@ -122,6 +122,8 @@ def load_library(build_if_missing: bool = True):
     lib.bipm_solve_static.argtypes = [ctypes.POINTER(ProblemDescC), ctypes.POINTER(OptionsC), vp, i,
                                       vp, vp, vp]
     lib.bipm_solve_queue_warm.argtypes = [vp, vp, vp, i, vp, vp, i]
+    lib.bipm_solve_mixed.argtypes = [ctypes.POINTER(ProblemDescC), i, ctypes.POINTER(OptionsC), i, vp, vp, i,
+                                     vp, vp, i, vp]
     pd = ctypes.POINTER(ProblemDescC)
     lib.bipm_warm_features.argtypes = [pd, vp, i, i, vp, vp]
     lib.bipm_warm_encode.argtypes = [pd, vp, vp, i, vp, vp]
@@ -503,3 +505,32 @@ class MLP:
         _check(self.lib.bipm_mlp_train_step(self.h, _dev_ptr(x_dev, "float32"), _dev_ptr(t_dev, "float32"), pi,
                                             rows, ctypes.c_float(lr), pl))
         return float(loss[0]) if want_loss else None
+
+
+def solve_mixed(classes, cls, theta, n_slots: int, options: "Options | None" = None, x_out=None,
+                results=None, stream=None):
+    """bipm_solve_mixed: problems of different structure classes in one queue.
+
+    classes: list of ProblemDesc; cls: int array (class of each problem);
+    theta: packed parameter rows (numpy float64, or a CUDA float64 tensor);
+    x_out: packed solution rows or None.  Host mode returns the result records
+    as a dict of arrays; device mode fills `results` (CUDA uint8 tensor)."""
+    lib = load_library()
+    arr = (ProblemDescC * len(classes))(*[ProblemDescC(c.nq, c.horizon, c.dt, c.n_sph, c.n_cyl, c.pair_dist)
+                                           for c in classes])
+    oc = (options or Options()).to_c()
+    cls = np.ascontiguousarray(cls, dtype=np.int32)
+    nq = int(cls.shape[0])
+    pt, dev = _ptr(theta)
+    px, _ = _ptr(x_out)
+    pc = cls.ctypes.data_as(ctypes.c_void_p)
+    if dev:
+        if results is None:
+            raise ValueError("device mode needs a results buffer")
+        _check(lib.bipm_solve_mixed(arr, len(classes), ctypes.byref(oc), n_slots, pc, pt, nq, px,
+                                    ctypes.c_void_p(results.data_ptr()), 1, _stream_ptr(stream)))
+        return None
+    res = (ResultC * max(nq, 1))()
+    _check(lib.bipm_solve_mixed(arr, len(classes), ctypes.byref(oc), n_slots, pc, pt, nq, px, res, 0,
+                                _stream_ptr(stream)))
+    return {f: np.array([getattr(res[j], f) for j in range(nq)]) for f, _ in ResultC._fields_}

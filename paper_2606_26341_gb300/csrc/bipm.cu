@@ -215,32 +215,16 @@ extern "C" {
 
 const char* bipm_last_error(void) { return g_err.c_str(); }
 
-int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_options* opt,
-                      void* cuda_stream, bipm_batch** out) {
-  if (!desc || !out) return fail(BIPM_EINVAL, "null argument");
-  *out = nullptr;
+// Validated dims of one problem structure (0, or an error code with message).
+static int dims_from_desc(const bipm_problem_desc* desc, Dims* out) {
   if (desc->n_quads < 1 || desc->n_quads > 8) return fail(BIPM_EINVAL, "n_quads must be 1..8");
   if (desc->horizon < 1 || desc->horizon > 1000) return fail(BIPM_EINVAL, "horizon must be 1..1000");
   if (!(desc->dt > 0.0) || !std::isfinite(desc->dt)) return fail(BIPM_EINVAL, "dt must be > 0");
   if (desc->n_spheres < 0 || desc->n_cylinders < 0 || desc->n_spheres > 256 || desc->n_cylinders > 256)
     return fail(BIPM_EINVAL, "obstacle counts must be 0..256");
   if (!(desc->pair_dist >= 0.0)) return fail(BIPM_EINVAL, "pair_dist must be >= 0");
-  if (capacity < 0) return fail(BIPM_EINVAL, "capacity must be >= 0");
-  bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0, 0, 0.0, 0.0, 0.0, 0, 0};
-  if (o.fp32_switch == 0.0) o.fp32_switch = kFp32BarrierMax;
-  if (o.warm_mu_init == 0.0) o.warm_mu_init = 1e-2;
-  if (o.warm_bound_push == 0.0) o.warm_bound_push = 1e-3;
-  if (o.warm_max_iter == 0) o.warm_max_iter = 60;
-  if (o.warm_max_iter < 0) return fail(BIPM_EINVAL, "warm_max_iter must be >= 0");
-  if (!(o.warm_mu_init > 0.0) || !(o.warm_bound_push > 0.0) || !(o.warm_bound_push < 0.5))
-    return fail(BIPM_EINVAL, "warm_mu_init must be > 0 and warm_bound_push in (0, 0.5)");
-  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || o.precision < 0 || o.precision > 2 ||
-      o.schedule < 0 || o.schedule > 2)
-    return fail(BIPM_EINVAL, "bad options");
-
-  bipm_batch* b = new bipm_batch();
-  b->desc = *desc;
-  Dims& d = b->d;
+  Dims d;
+  std::memset(&d, 0, sizeof(d));
   d.nq = desc->n_quads;
   d.N = desc->horizon;
   d.nx = 12 * d.nq;
@@ -258,14 +242,53 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
   d.th_sph = d.th_ref + 6 * d.nq;
   d.th_cyl = d.th_sph + 4 * d.n_sph;
   d.n_theta = d.th_cyl + 3 * d.n_cyl;
-  b->opt.tol = o.tol;
-  b->opt.max_iter = o.max_iter;
-  b->opt.mu_init = o.mu_init;
-  b->opt.precision = o.precision;
-  b->opt.fp32_switch = o.fp32_switch;
-  b->opt.warm_mu = o.warm_mu_init;
-  b->opt.warm_push = o.warm_bound_push;
-  b->opt.warm_max_iter = std::min(o.warm_max_iter, o.max_iter);
+  *out = d;
+  return 0;
+}
+
+// Options with defaults filled in, validated; device options in *dev.
+static int options_from(const bipm_options* opt, bipm_options* o_out, Options* dev) {
+  bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0, 0, 0.0, 0.0, 0.0, 0, 0};
+  if (o.fp32_switch == 0.0) o.fp32_switch = kFp32BarrierMax;
+  if (o.warm_mu_init == 0.0) o.warm_mu_init = 1e-2;
+  if (o.warm_bound_push == 0.0) o.warm_bound_push = 1e-3;
+  if (o.warm_max_iter == 0) o.warm_max_iter = 60;
+  if (o.warm_max_iter < 0) return fail(BIPM_EINVAL, "warm_max_iter must be >= 0");
+  if (!(o.warm_mu_init > 0.0) || !(o.warm_bound_push > 0.0) || !(o.warm_bound_push < 0.5))
+    return fail(BIPM_EINVAL, "warm_mu_init must be > 0 and warm_bound_push in (0, 0.5)");
+  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || o.precision < 0 || o.precision > 2 ||
+      o.schedule < 0 || o.schedule > 2)
+    return fail(BIPM_EINVAL, "bad options");
+  dev->tol = o.tol;
+  dev->max_iter = o.max_iter;
+  dev->mu_init = o.mu_init;
+  dev->precision = o.precision;
+  dev->fp32_switch = o.fp32_switch;
+  dev->warm_mu = o.warm_mu_init;
+  dev->warm_push = o.warm_bound_push;
+  dev->warm_max_iter = std::min(o.warm_max_iter, o.max_iter);
+  *o_out = o;
+  return 0;
+}
+
+int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_options* opt,
+                      void* cuda_stream, bipm_batch** out) {
+  if (!desc || !out) return fail(BIPM_EINVAL, "null argument");
+  *out = nullptr;
+  Dims dd;
+  int rc = dims_from_desc(desc, &dd);
+  if (rc) return rc;
+  if (capacity < 0) return fail(BIPM_EINVAL, "capacity must be >= 0");
+  bipm_options o;
+  Options dopt;
+  rc = options_from(opt, &o, &dopt);
+  if (rc) return rc;
+
+  bipm_batch* b = new bipm_batch();
+  b->desc = *desc;
+  Dims& d = b->d;
+  d = dd;
+  b->opt = dopt;
   b->schedule = o.schedule;
   b->capacity = capacity;
   b->stream = (cudaStream_t)cuda_stream;
@@ -522,6 +545,178 @@ int bipm_solve_queue_warm(bipm_batch* b, const double* theta_queue, const double
                           double* x_out, bipm_result* results, int on_device) {
   if (n_queue > 0 && !x_guess) return fail(BIPM_EINVAL, "null x_guess");
   return solve_queue_impl(b, theta_queue, x_guess, n_queue, x_out, results, on_device);
+}
+
+// results of the parked stragglers of a mixed queue (one warp per slot)
+__global__ void mixed_writeout(const Params* __restrict__ Pc, const long long* __restrict__ x_off,
+                               double* __restrict__ x_out, bipm_result* __restrict__ res_out) {
+  const int lane = threadIdx.x & 31;
+  const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (slot >= Pc->n_slots) return;
+  const SlotState S = Pc->st[slot];
+  if (!S.parked) return;
+  const Params* P = Pc + S.cls;
+  const double* w = P->f64 + (long long)slot * P->L.slot_f64 + P->L.x;
+  if (x_out)
+    for (int i = lane; i < P->d.n; i += 32) x_out[x_off[S.problem_id] + i] = w[i];
+  if (lane == 0) {
+    res_out[S.problem_id] = make_result(S, 0, 0);
+    Pc->st[slot].parked = 0;
+  }
+}
+
+namespace {
+// device allocations of one call, freed on every return path
+struct DevAllocs {
+  std::vector<void*> ptrs;
+  void* take(size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    return p;
+  }
+  ~DevAllocs() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+}  // namespace
+
+int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm_options* opt, int n_slots,
+                     const int* cls, const double* theta, int n_queue, double* x_out, bipm_result* results,
+                     int on_device, void* cuda_stream) {
+  if (!classes || n_classes < 1 || n_classes > kMaxClasses)
+    return fail(BIPM_EINVAL, "n_classes must be 1.." + std::to_string(kMaxClasses));
+  if (n_slots < 1) return fail(BIPM_EINVAL, "n_slots must be >= 1");
+  if (n_queue < 0) return fail(BIPM_EINVAL, "n_queue must be >= 0");
+  if (n_queue == 0) return 0;
+  if (!cls || !theta || !results) return fail(BIPM_EINVAL, "null cls, theta or results");
+  bipm_options o;
+  Options dopt;
+  int rc = options_from(opt, &o, &dopt);
+  if (rc) return rc;
+  if (o.precision == 2) return fail(BIPM_EINVAL, "mixed queues support precision 0 and 1");
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  // per-class structure and layout; slots are sized for the largest class
+  std::vector<Dims> dims(n_classes);
+  std::vector<Layout> lays(n_classes);
+  std::vector<int> smem_c(n_classes);
+  long long mf64 = 0, mtb = 0, mfac = 0, mth = 0;
+  int smem_stride = 0;
+  for (int k = 0; k < n_classes; ++k) {
+    if ((rc = dims_from_desc(classes + k, &dims[k]))) return rc;
+    lays[k] = make_layout(dims[k], o.precision);
+    mf64 = std::max(mf64, lays[k].slot_f64);
+    mtb = std::max(mtb, lays[k].slot_tb);
+    mfac = std::max(mfac, lays[k].fac_size);
+    mth = std::max(mth, (long long)dims[k].n_theta);
+    const Dims& d = dims[k];
+    size_t need = scratch_bytes(d.nq, d.nx, d.nu, o.precision == 1 ? 4 : 8);
+    size_t need64 = scratch_bytes(d.nq, d.nx, d.nu, 8);
+    const size_t cap_b = 24 * 1024;
+    smem_c[k] = (int)(need64 <= cap_b ? need64 : (need <= cap_b ? need : 128));
+    smem_stride = std::max(smem_stride, smem_c[k]);
+  }
+  // queue offsets (packed rows)
+  std::vector<long long> th_off(n_queue), x_off(n_queue);
+  long long th_tot = 0, x_tot = 0;
+  for (int i = 0; i < n_queue; ++i) {
+    if (cls[i] < 0 || cls[i] >= n_classes)
+      return fail(BIPM_EINVAL, "cls[" + std::to_string(i) + "] = " + std::to_string(cls[i]) + " is not a class");
+    th_off[i] = th_tot;
+    x_off[i] = x_tot;
+    th_tot += dims[cls[i]].n_theta;
+    x_tot += dims[cls[i]].n;
+  }
+  void* qfn = o.precision ? queue_mixed_f32() : queue_mixed_f64();
+  void* bfn = o.precision ? block_mixed_f32() : block_mixed_f64();
+  const size_t qsm = (size_t)smem_stride * kWarpsPerBlock, bsm = (size_t)smem_stride + 128;
+  if (qsm > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(qfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
+  if (bsm > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(bfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+  int dev = 0, sms = 0, per_sm = 0, per_sm_b = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qfn, 32 * kWarpsPerBlock, qsm));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, bfn, kBlockTeam, bsm));
+  if (per_sm < 1 || per_sm_b < 1) return fail(BIPM_ECUDA, "mixed queue kernels do not fit on an SM");
+  const int warps = std::min(n_slots, sms * per_sm * kWarpsPerBlock);
+  const int n_spare = n_slots - warps;
+
+  const size_t tsz = o.precision ? sizeof(float) : sizeof(double);
+  const size_t fsz = o.precision == 1 ? sizeof(float) : sizeof(double);
+  DevAllocs mem;
+  double* f64 = (double*)mem.take((size_t)n_slots * mf64 * sizeof(double));
+  void* tb = mem.take((size_t)n_slots * mtb * tsz);
+  void* tf = mem.take((size_t)n_slots * mfac * fsz);
+  double* th_slots = (double*)mem.take((size_t)n_slots * mth * sizeof(double));
+  SlotState* st = (SlotState*)mem.take((size_t)n_slots * sizeof(SlotState));
+  int* counter = (int*)mem.take(2 * sizeof(int));
+  Params* dP = (Params*)mem.take((size_t)n_classes * sizeof(Params));
+  int* cls_d = (int*)mem.take((size_t)n_queue * sizeof(int));
+  long long* off_d = (long long*)mem.take((size_t)2 * n_queue * sizeof(long long));
+  if (!f64 || !tb || !tf || !th_slots || !st || !counter || !dP || !cls_d || !off_d)
+    return fail(BIPM_ENOMEM, "mixed queue workspace");
+  const double* th_dev = theta;
+  double* x_dev = x_out;
+  bipm_result* r_dev = results;
+  if (!on_device) {
+    th_dev = (const double*)mem.take((size_t)th_tot * sizeof(double));
+    x_dev = x_out ? (double*)mem.take((size_t)x_tot * sizeof(double)) : nullptr;
+    r_dev = (bipm_result*)mem.take((size_t)n_queue * sizeof(bipm_result));
+    if (!th_dev || (x_out && !x_dev) || !r_dev) return fail(BIPM_ENOMEM, "mixed queue staging");
+    CUDA_TRY(cudaMemcpyAsync((void*)th_dev, theta, th_tot * sizeof(double), cudaMemcpyHostToDevice, stream));
+  }
+  std::vector<Params> Ps(n_classes);
+  for (int k = 0; k < n_classes; ++k) {
+    Params& P = Ps[k];
+    std::memset(&P, 0, sizeof(P));
+    P.d = dims[k];
+    P.L = lays[k];
+    P.L.slot_f64 = mf64;  // shared slot strides
+    P.L.slot_tb = mtb;
+    P.L.fac_size = mfac;
+    P.opt = dopt;
+    P.n_slots = n_slots;
+    P.f64 = f64;
+    P.tb = tb;
+    P.tf = tf;
+    P.theta = th_slots;
+    P.st = st;
+    P.work_counter = counter;
+    P.smem_per_warp = smem_c[k];
+    P.spare_counter = counter + 1;
+    P.n_spare = n_spare;
+    P.visit_cap = n_spare > 0 ? kQueueVisit : 0;
+    P.theta_stride = mth;
+  }
+  CUDA_TRY(cudaMemsetAsync(f64, 0, (size_t)n_slots * mf64 * sizeof(double), stream));
+  CUDA_TRY(cudaMemcpyAsync(dP, Ps.data(), n_classes * sizeof(Params), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(cls_d, cls, n_queue * sizeof(int), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(off_d, th_off.data(), n_queue * sizeof(long long), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(off_d + n_queue, x_off.data(), n_queue * sizeof(long long), cudaMemcpyHostToDevice,
+                           stream));
+  CUDA_TRY(cudaMemsetAsync(counter, 0, 2 * sizeof(int), stream));
+  reset_states<<<std::max(1, std::min(1024, (n_slots + 255) / 256)), 256, 0, stream>>>(dP);
+  CUDA_TRY(cudaGetLastError());
+  const long long* thoff_d = off_d;
+  const long long* xoff_d = off_d + n_queue;
+  int nq_arg = n_queue, warps_arg = warps, stride_arg = smem_stride;
+  void* args[] = {&dP, &cls_d, &thoff_d, &xoff_d, &th_dev, &nq_arg, &warps_arg, &stride_arg, &x_dev, &r_dev};
+  CUDA_TRY(cudaLaunchKernel(qfn, dim3((warps + kWarpsPerBlock - 1) / kWarpsPerBlock), dim3(32 * kWarpsPerBlock),
+                            args, qsm, stream));
+  if (n_spare > 0) {
+    CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
+    void* args2[] = {&dP};
+    CUDA_TRY(cudaLaunchKernel(bfn, dim3(std::max(1, std::min(n_slots, sms * per_sm_b))), dim3(kBlockTeam), args2,
+                              bsm, stream));
+    mixed_writeout<<<(int)(((long long)n_slots * 32 + 255) / 256), 256, 0, stream>>>(dP, xoff_d, x_dev, r_dev);
+    CUDA_TRY(cudaGetLastError());
+  }
+  if (!on_device) {
+    if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, x_dev, x_tot * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(results, r_dev, n_queue * sizeof(bipm_result), cudaMemcpyDeviceToHost, stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  return 0;
 }
 
 int bipm_step(bipm_batch* b, int n_iterations) {

@@ -194,7 +194,7 @@ struct SlotState {
   int n_fact, n_solve, n_trial, n_fact32, n_solve32;
   int parked;              // queue straggler left to the block teams (results pending)
   int warm_flag, warm_it;  // warm-start outcome of a parked problem (bipm_result.warm / warm_iters)
-  int pad_;
+  int cls;                 // structure class of the slot's problem (mixed queues)
   long long cyc[8];  // clock cycles per phase (see kPhase*)
   double mu, dw_last, theta_max, theta_min;
   double mu_r, dw_last_r, theta_max_r, theta_min_r, zeta, theta_ref;
@@ -219,6 +219,13 @@ struct Params {
   int* spare_counter;
   int n_spare;
   int visit_cap;
+  // doubles between the parameter rows of consecutive slots (0: d.n_theta);
+  // a mixed queue sizes every slot for its largest structure class
+  long long theta_stride;
 };
+
+__host__ __device__ __forceinline__ long long theta_stride(const Params* P) {
+  return P->theta_stride ? P->theta_stride : (long long)P->d.n_theta;
+}
 
 }  // namespace bipm

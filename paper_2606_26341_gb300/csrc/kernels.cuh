@@ -12,6 +12,7 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kBlockTeam = 256;    // threads of a block team
 constexpr int kBulkVisit = 64;     // iterations per problem in the warp kernel
 constexpr int kQueueVisit = 96;    // iterations before a queue problem is parked for block teams
+constexpr int kMaxClasses = 64;    // structure classes of one mixed queue
 
 template <class TB, class TF>
 __device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, int T, double* red,
@@ -31,7 +32,7 @@ __device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, in
     c.fac64 = make_fac<double>((double*)fb, P->L);
   else
     c.fac64 = make_fac<double>(c.f + P->L.f64_fac, P->L);
-  c.th = P->theta + (long long)slot * P->d.n_theta;
+  c.th = P->theta + (long long)slot * theta_stride(P);
   c.smem = smem;
   c.smem_bytes = P->smem_per_warp;
   c.gscratch = (char*)(c.f + P->L.gscr);
@@ -162,7 +163,7 @@ __device__ __forceinline__ SlotState init_slot(const Params* P, int slot, int la
   const Dims& d = P->d;
   const Layout& L = P->L;
   double* f = P->f64 + (long long)slot * L.slot_f64;
-  const double* th = P->theta + (long long)slot * d.n_theta;
+  const double* th = P->theta + (long long)slot * theta_stride(P);
   double* w = f + L.x;
   double* zl = f + L.zl;
   double* zu = f + L.zu;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     if (lane == 0) id = atomicAdd(P->work_counter, 1);
     id = __shfl_sync(0xffffffffu, id, 0);
     if (id >= n_queue) break;
-    double* th = P->theta + (long long)slot * d.n_theta;
+    double* th = P->theta + (long long)slot * theta_stride(P);
     for (int i = lane; i < d.n_theta; i += 32) th[i] = theta_q[(long long)id * d.n_theta + i];
     __syncwarp();
     const double* gq = x_guess ? x_guess + (long long)id * d.n : nullptr;
@@ -327,6 +328,100 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
   }
 }
 
+// Iteration-level batching over problems of different structures (uneven
+// horizons and quadrotor counts) in one launch.  Pc[c] describes structure
+// class c (its dims and slot layout; every class shares the workspace, whose
+// slots are sized for the largest class).  Problem id has class cls[id], its
+// parameters at theta_q + th_off[id] and its solution row at x_out + x_off[id].
+// smem_stride: shared-memory bytes per warp of the launch.  Stragglers are
+// parked as in queue_kernel and finished by block_mixed_kernel.
+template <class TB, class TF>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
+    queue_mixed_kernel(const Params* __restrict__ Pc, const int* __restrict__ cls,
+                       const long long* __restrict__ th_off, const long long* __restrict__ x_off,
+                       const double* __restrict__ theta_q, int n_queue, int n_warps, int smem_stride,
+                       double* __restrict__ x_out, bipm_result* __restrict__ res_out) {
+  extern __shared__ __align__(16) char smem_all[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  int slot = blockIdx.x * kWarpsPerBlock + warp;
+  if (slot >= n_warps) return;
+  char* smem = smem_all + (size_t)warp * smem_stride;
+  const Params* P0 = Pc;
+  while (true) {
+    int id = 0;
+    if (lane == 0) id = atomicAdd(P0->work_counter, 1);
+    id = __shfl_sync(0xffffffffu, id, 0);
+    if (id >= n_queue) break;
+    const int k = cls[id];
+    const Params* P = Pc + k;
+    const Dims& d = P->d;
+    double* th = P->theta + (long long)slot * theta_stride(P);
+    for (int i = lane; i < d.n_theta; i += 32) th[i] = theta_q[th_off[id] + i];
+    __syncwarp();
+    SlotState S = init_slot(P, slot, lane, nullptr, nullptr, 0);
+    S.problem_id = id;
+    S.cls = k;
+    Ctx<TB, TF> c;
+    make_ctx(c, P, slot, lane, 32, nullptr, smem);
+    run_slot(c, S, 0, P->visit_cap);
+    if (S.status == BIPM_RUNNING) {
+      int ns = 0;
+      if (lane == 0) ns = atomicAdd(P0->spare_counter, 1);
+      ns = __shfl_sync(0xffffffffu, ns, 0);
+      if (ns < P0->n_spare) {
+        if (lane == 0) {
+          S.parked = 1;
+          S.warm_flag = 0;
+          S.warm_it = 0;
+          P->st[slot] = S;
+        }
+        __syncwarp();
+        slot = n_warps + ns;
+        continue;
+      }
+      run_slot(c, S, 0, 0);
+    }
+    const double* w = c.f + P->L.x;
+    if (x_out)
+      for (int i = lane; i < d.n; i += 32) x_out[x_off[id] + i] = w[i];
+    if (lane == 0) {
+      res_out[id] = make_result(S, 0, 0);
+      S.parked = 0;
+      P->st[slot] = S;
+    }
+    __syncwarp();
+  }
+}
+
+// Block teams finish the parked problems of a mixed queue (each slot's class
+// is recorded in its state).
+template <class TB, class TF>
+__global__ void __launch_bounds__(kBlockTeam)
+    block_mixed_kernel(const Params* __restrict__ Pc) {
+  extern __shared__ __align__(16) char smem_all[];
+  double* red = (double*)smem_all;
+  char* smem = smem_all + 128;
+  __shared__ int s_slot;
+  const Params* P0 = Pc;
+  while (true) {
+    if (threadIdx.x == 0) s_slot = atomicAdd(P0->work_counter, 1);
+    __syncthreads();
+    const int slot = s_slot;
+    __syncthreads();
+    if (slot >= P0->n_slots) break;
+    SlotState S = P0->st[slot];
+    if (S.status != BIPM_RUNNING) continue;
+    const Params* P = Pc + S.cls;
+    Ctx<TB, TF> c;
+    make_ctx(c, P, slot, (int)threadIdx.x, (int)blockDim.x, red, smem);
+    run_slot(c, S, 0, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) P0->st[slot] = S;
+    __syncthreads();
+  }
+}
+
 // offsets of the per-slot arrays for problems of dims d (host)
 Layout make_layout(const Dims& d, int precision);
 
@@ -343,5 +438,9 @@ void* iter_kernel_df();
 void* init_kernel_df();
 void* block_kernel_df();
 void* queue_kernel_df();
+void* queue_mixed_f64();
+void* queue_mixed_f32();
+void* block_mixed_f64();
+void* block_mixed_f32();
 
 }  // namespace bipm

@@ -16,6 +16,8 @@ from .quadrotor import (  # noqa: F401
     ProblemDesc,
     SplitMix64,
     make_batch,
+    make_mixed,
+    mixed_classes,
     n_theta,
     theta_layout,
 )

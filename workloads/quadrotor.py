@@ -237,3 +237,45 @@ def make_batch(name: str, count: int | None = None, first_id: int = 0,
     th = np.stack([drawer(problem_stream(seed, first_id + j), desc) for j in range(count)]) \
         if count > 0 else np.zeros((0, n_theta(desc)))
     return desc, np.ascontiguousarray(th, dtype=np.float64)
+
+
+# --------------------------------------------------------- uneven queue --
+# Structure classes of the uneven queue: 1-8 quadrotors x horizons 10, 20, 30,
+# 50, configured as the multi-quadrotor workload (pairwise distance 0.4); a
+# single quadrotor flies past one sphere instead.
+MIXED_SEED = 1004
+MIXED_HORIZONS = (10, 20, 30, 50)
+
+
+def mixed_classes(max_quads: int = 8, horizons=MIXED_HORIZONS):
+    """The structure classes (nq, horizon), nq = 1..max_quads, in that order
+    (32 classes for the default arguments)."""
+    out = []
+    for nq in range(1, max_quads + 1):
+        for N in horizons:
+            out.append(ProblemDesc(nq=nq, horizon=N, dt=0.05, n_sph=1 if nq == 1 else 0,
+                                   pair_dist=0.0 if nq == 1 else 0.4))
+    return out
+
+
+def make_mixed(count: int, first_id: int = 0, max_quads: int = 8, horizons=MIXED_HORIZONS):
+    """Draw `count` problems of the uneven queue: each draws its quadrotor count
+    (uniform 1..max_quads) and horizon (uniform over `horizons`) from its own
+    stream, then its parameters as the multi-quadrotor workload.
+
+    Returns (classes, cls, theta_packed): the class list of
+    mixed_classes(max_quads, horizons), the class index of every problem and the
+    concatenated parameter rows."""
+    classes = mixed_classes(max_quads, horizons)
+    index = {(c.nq, c.horizon): k for k, c in enumerate(classes)}
+    cls = np.zeros(count, dtype=np.int32)
+    rows = []
+    for j in range(count):
+        rng = problem_stream(MIXED_SEED, first_id + j)
+        nq = rng.randint(1, max_quads)
+        N = horizons[rng.randint(0, len(horizons) - 1)]
+        k = index[(nq, N)]
+        cls[j] = k
+        rows.append(_multi(rng, classes[k]))
+    theta = np.concatenate(rows) if rows else np.zeros(0)
+    return classes, cls, np.ascontiguousarray(theta, dtype=np.float64)
