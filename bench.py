@@ -116,10 +116,11 @@ RK4_VALUE_FLOPS = 152 + 200 + 4            # one RK4 step of one quadrotor, valu
 RK4_ADJOINT_FLOPS = 403 + 620 + 4          # value + reverse sweep (gradient of lam^T F)
 RK4_DUAL_FLOPS = 1122 + 1596 + 8           # forward-over-reverse, one direction
 
-# DRAM traffic per problem-iteration of the queue kernel, measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum = 2.394e9 B for 512 tracking
-# problems at 30.9 iterations each); scaled to a launch by its iterations.
-TRAFFIC_PER_PROBLEM_ITER = 2.394e9 / (512 * 30.9)
+# DRAM traffic per problem-iteration of the queue kernel, measured by ncu on one
+# timed launch of 4096 tracking problems (dram__bytes_read.sum +
+# dram__bytes_write.sum = 42.13e9 + 33.16e9 B at 30.41 iterations each); scaled
+# to a launch by its iterations.
+TRAFFIC_PER_PROBLEM_ITER = (42.13e9 + 33.16e9) / (4096 * 30.41)
 
 
 def unit_flops(desc):
@@ -280,7 +281,7 @@ def run_ours(args):
         "peak": (f64_m + f32_m) / t_bound / 1e12,
         "frac": t_bound / k_mixed,
         "traffic": TRAFFIC_PER_PROBLEM_ITER * float(np.sum(r_mixed["iters"])),
-        "traffic_unit": "bytes per launch (ncu capture of 512 problems, scaled by iterations)",
+        "traffic_unit": "bytes per launch (ncu capture of one 4096-problem launch, scaled by iterations)",
         "kernel": "queue_kernel (chosen form)",
         "flops_fp64_per_launch": f64_m, "flops_fp32_per_launch": f32_m,
         "peak_source": "derived from unit counts and clocks (no FP64/FP32 ALU figure in "

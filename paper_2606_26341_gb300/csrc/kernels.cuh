@@ -88,7 +88,7 @@ __device__ void run_slot(Ctx<TB, TF>& c, SlotState& S, int n_iter, int visit_cap
 // the work counter and iterates it (iteration-level batching: a warp that
 // finishes a problem immediately starts another one).
 template <class TB, class TF>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     ipm_kernel(const Params* __restrict__ P, int n_iter, int visit_cap) {
   extern __shared__ __align__(16) char smem_all[];
   const int lane = threadIdx.x & 31;
@@ -257,7 +257,7 @@ __device__ __forceinline__ bipm_result make_result(const SlotState& S, int warm,
 }
 
 template <class TB, class TF>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     queue_kernel(const Params* __restrict__ P, const double* __restrict__ theta_q, int n_queue,
                  int n_warps, double* __restrict__ x_out, bipm_result* __restrict__ res_out,
                  const double* __restrict__ x_guess) {
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
 // smem_stride: shared-memory bytes per warp of the launch.  Stragglers are
 // parked as in queue_kernel and finished by block_mixed_kernel.
 template <class TB, class TF>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     queue_mixed_kernel(const Params* __restrict__ Pc, const int* __restrict__ cls,
                        const long long* __restrict__ th_off, const long long* __restrict__ x_off,
                        const double* __restrict__ theta_q, int n_queue, int n_warps, int smem_stride,
