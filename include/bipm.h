@@ -320,12 +320,14 @@ int bipm_mlp_forward(bipm_mlp* net, const float* x, int rows, float* out, int on
  * grad (n_params floats) and loss (one double) may be NULL. */
 int bipm_mlp_loss_grad(bipm_mlp* net, const float* x, const float* t, int rows, float* grad, double* loss,
                        int on_device);
-/* One Adam step on the batch of rows idx[0..rows) of x and t (DEVICE pointers;
- * idx NULL = the first `rows` rows) with learning rate lr.  loss (host, may be
- * NULL) receives the batch loss before the step; without it the call returns
- * after launching. */
-int bipm_mlp_train_step(bipm_mlp* net, const float* x, const float* t, const int* idx, int rows, float lr,
-                        double* loss);
+/* One Adam step on the batch of rows idx[0..rows) of the n_data rows of x and
+ * t (DEVICE pointers; idx NULL = the first `rows` rows) with learning rate lr.
+ * An index outside [0, n_data) is replaced by row 0 and reported by the next
+ * call with a loss pointer (BIPM_EINVAL).  loss (host, may be NULL) receives
+ * the batch loss before the step; without it the call returns after
+ * launching. */
+int bipm_mlp_train_step(bipm_mlp* net, const float* x, const float* t, int n_data, const int* idx, int rows,
+                        float lr, double* loss);
 void bipm_mlp_destroy(bipm_mlp* net);
 
 /* Runs exactly `n_iterations` iterations on every running slot. */

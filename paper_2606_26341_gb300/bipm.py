@@ -134,7 +134,7 @@ def load_library(build_if_missing: bool = True):
     lib.bipm_mlp_get_params.argtypes = [vp, vp, i]
     lib.bipm_mlp_forward.argtypes = [vp, vp, i, vp, i]
     lib.bipm_mlp_loss_grad.argtypes = [vp, vp, vp, i, vp, vp, i]
-    lib.bipm_mlp_train_step.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, vp]
+    lib.bipm_mlp_train_step.argtypes = [vp, vp, vp, i, vp, i, ctypes.c_float, vp]
     lib.bipm_mlp_destroy.argtypes = [vp]
     lib.bipm_mlp_destroy.restype = None
     lib.bipm_last_error.restype = ctypes.c_char_p
@@ -502,8 +502,10 @@ class MLP:
         loss = np.zeros(1)
         pl = loss.ctypes.data_as(ctypes.c_void_p) if want_loss else None
         pi = ctypes.c_void_p(idx_dev.data_ptr()) if idx_dev is not None else None
-        _check(self.lib.bipm_mlp_train_step(self.h, _dev_ptr(x_dev, "float32"), _dev_ptr(t_dev, "float32"), pi,
-                                            rows, ctypes.c_float(lr), pl))
+        if t_dev.shape[0] != x_dev.shape[0]:
+            raise ValueError("x and t must have the same number of rows")
+        _check(self.lib.bipm_mlp_train_step(self.h, _dev_ptr(x_dev, "float32"), _dev_ptr(t_dev, "float32"),
+                                            int(x_dev.shape[0]), pi, rows, ctypes.c_float(lr), pl))
         return float(loss[0]) if want_loss else None
 
 

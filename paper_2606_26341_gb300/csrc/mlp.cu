@@ -197,22 +197,35 @@ __global__ void __launch_bounds__(kGemmThreads)
 }
 
 // ------------------------------------------------------- elementwise kernels
+// row r of a batch: idx[r] (or r without idx) if it lies in [0, n_data); an
+// index outside the data is replaced by row 0 and raises *bad
+__device__ __forceinline__ long long batch_row(const int* idx, int r, int n_data, int* bad) {
+  if (!idx) return r;
+  const int i = idx[r];
+  if (i < 0 || i >= n_data) {
+    *bad = 1;
+    return 0;
+  }
+  return i;
+}
+
 // rows of x (optionally gathered through idx) -> bf16 with leading dimension ld
 __global__ void to_bf16_rows(const float* __restrict__ x, const int* __restrict__ idx, int rows, int cols,
-                             bf16* __restrict__ out, int ld) {
+                             int n_data, bf16* __restrict__ out, int ld, int* __restrict__ bad) {
   long long total = (long long)rows * ld;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     int r = (int)(e / ld), c = (int)(e - (long long)r * ld);
-    long long src = idx ? (long long)idx[r] : r;
+    const long long src = batch_row(idx, r, n_data, bad);
     out[e] = __float2bfloat16(c < cols ? x[src * cols + c] : 0.0f);
   }
 }
 
 // output error (out - t) / B in FP32 and bf16; per-block partial sums of the squared error
 __global__ void loss_grad_kernel(const float* __restrict__ out, const float* __restrict__ t,
-                                 const int* __restrict__ idx, int rows, int cols, float* __restrict__ d32,
-                                 bf16* __restrict__ d16, int ld, double* __restrict__ part) {
+                                 const int* __restrict__ idx, int rows, int cols, int n_data,
+                                 float* __restrict__ d32, bf16* __restrict__ d16, int ld,
+                                 double* __restrict__ part, int* __restrict__ bad) {
   __shared__ double red[256];
   double acc = 0.0;
   const float inv_b = 1.0f / (float)rows;
@@ -220,7 +233,7 @@ __global__ void loss_grad_kernel(const float* __restrict__ out, const float* __r
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     int r = (int)(e / cols), c = (int)(e - (long long)r * cols);
-    long long tr = idx ? (long long)idx[r] : r;
+    const long long tr = batch_row(idx, r, n_data, bad);
     float err = out[(long long)r * cols + c] - t[tr * cols + c];
     acc += (double)err * (double)err;
     float g = err * inv_b;
@@ -329,6 +342,7 @@ struct bipm_mlp {
   long long splitk_elems = 0;
   double* loss_part = nullptr;
   double* loss_dev = nullptr;
+  int* bad_index = nullptr;  // set when a batch index lies outside the data
   float* xin = nullptr;      // staging of host inputs / targets
   float* tin = nullptr;
   int adam_t = 0;
@@ -375,11 +389,11 @@ int forward_rows(bipm_mlp* n, int rows) {
 }
 
 // loss, gradient into n->grad (needs act16[0] filled); t rows selected by idx
-int backward_rows(bipm_mlp* n, const float* t, const int* idx, int rows) {
+int backward_rows(bipm_mlp* n, const float* t, const int* idx, int rows, int n_data) {
   const int L = n->L;
   int cur = 0;
-  loss_grad_kernel<<<kLossBlocks, 256, 0, n->stream>>>(n->out32, t, idx, rows, n->w[L], n->d32[cur],
-                                                       n->d16[cur], n->ld[L], n->loss_part);
+  loss_grad_kernel<<<kLossBlocks, 256, 0, n->stream>>>(n->out32, t, idx, rows, n->w[L], n_data, n->d32[cur],
+                                                       n->d16[cur], n->ld[L], n->loss_part, n->bad_index);
   CUDA_TRY(cudaGetLastError());
   loss_final<<<1, 256, 0, n->stream>>>(n->loss_part, kLossBlocks, rows, n->loss_dev);
   CUDA_TRY(cudaGetLastError());
@@ -429,9 +443,10 @@ int pack_all(bipm_mlp* n) {
   return 0;
 }
 
-int load_inputs(bipm_mlp* n, const float* x, const int* idx, int rows) {
+int load_inputs(bipm_mlp* n, const float* x, const int* idx, int rows, int n_data) {
   long long tot = (long long)rows * n->ld[0];
-  to_bf16_rows<<<grid_for(tot), 256, 0, n->stream>>>(x, idx, rows, n->w[0], n->act16[0], n->ld[0]);
+  to_bf16_rows<<<grid_for(tot), 256, 0, n->stream>>>(x, idx, rows, n->w[0], n_data, n->act16[0], n->ld[0],
+                                                     n->bad_index);
   CUDA_TRY(cudaGetLastError());
   return 0;
 }
@@ -484,7 +499,8 @@ int bipm_mlp_create(const int* widths, int n_widths, int max_rows, void* stream,
   for (int l = 0; l < n->L; ++l) wmax = std::max(wmax, (long long)n->w[l + 1] * n->w[l]);
   n->splitk_elems = wmax * kMaxSplits;
   ok = ok && alloc(n->splitk_elems * 4, (void**)&n->splitk) && alloc(kLossBlocks * 8, (void**)&n->loss_part) &&
-       alloc(8, (void**)&n->loss_dev) && alloc((size_t)max_rows * n->w[0] * 4, (void**)&n->xin) &&
+       alloc(8, (void**)&n->loss_dev) && alloc(sizeof(int), (void**)&n->bad_index) &&
+       alloc((size_t)max_rows * n->w[0] * 4, (void**)&n->xin) &&
        alloc((size_t)max_rows * n->w[n->L] * 4, (void**)&n->tin);
   if (!ok) {
     bipm_mlp_destroy(n);
@@ -492,7 +508,8 @@ int bipm_mlp_create(const int* widths, int n_widths, int max_rows, void* stream,
   }
   if (cudaMemsetAsync(n->master, 0, pos * 4, n->stream) != cudaSuccess ||
       cudaMemsetAsync(n->mom1, 0, pos * 4, n->stream) != cudaSuccess ||
-      cudaMemsetAsync(n->mom2, 0, pos * 4, n->stream) != cudaSuccess) {
+      cudaMemsetAsync(n->mom2, 0, pos * 4, n->stream) != cudaSuccess ||
+      cudaMemsetAsync(n->bad_index, 0, sizeof(int), n->stream) != cudaSuccess) {
     bipm_mlp_destroy(n);
     return fail(BIPM_ECUDA, "cudaMemsetAsync failed");
   }
@@ -544,7 +561,7 @@ int bipm_mlp_forward(bipm_mlp* n, const float* x, int rows, float* out, int on_d
       CUDA_TRY(cudaMemcpyAsync(n->xin, xs, (size_t)rr * win * 4, cudaMemcpyHostToDevice, n->stream));
       xs = n->xin;
     }
-    int rc = load_inputs(n, xs, nullptr, rr);
+    int rc = load_inputs(n, xs, nullptr, rr, rr);
     if (!rc) rc = forward_rows(n, rr);
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(out + (long long)r0 * wout, n->out32, (size_t)rr * wout * 4,
@@ -567,9 +584,9 @@ int bipm_mlp_loss_grad(bipm_mlp* n, const float* x, const float* t, int rows, fl
     xs = n->xin;
     ts = n->tin;
   }
-  int rc = load_inputs(n, xs, nullptr, rows);
+  int rc = load_inputs(n, xs, nullptr, rows, rows);
   if (!rc) rc = forward_rows(n, rows);
-  if (!rc) rc = backward_rows(n, ts, nullptr, rows);
+  if (!rc) rc = backward_rows(n, ts, nullptr, rows, rows);
   if (rc) return rc;
   cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (grad) CUDA_TRY(cudaMemcpyAsync(grad, n->grad, n->n_params * 4, k, n->stream));
@@ -578,14 +595,15 @@ int bipm_mlp_loss_grad(bipm_mlp* n, const float* x, const float* t, int rows, fl
   return 0;
 }
 
-int bipm_mlp_train_step(bipm_mlp* n, const float* x, const float* t, const int* idx, int rows, float lr,
-                        double* loss) {
+int bipm_mlp_train_step(bipm_mlp* n, const float* x, const float* t, int n_data, const int* idx, int rows,
+                        float lr, double* loss) {
   if (!n) return fail(BIPM_EINVAL, "null network");
   if (rows < 1 || rows > n->max_rows) return fail(BIPM_EINVAL, "rows must be in [1, max_rows]");
   if (!x || !t) return fail(BIPM_EINVAL, "null x or t");
-  int rc = load_inputs(n, x, idx, rows);
+  if (n_data < 1 || (!idx && n_data < rows)) return fail(BIPM_EINVAL, "n_data must cover the batch rows");
+  int rc = load_inputs(n, x, idx, rows, n_data);
   if (!rc) rc = forward_rows(n, rows);
-  if (!rc) rc = backward_rows(n, t, idx, rows);
+  if (!rc) rc = backward_rows(n, t, idx, rows, n_data);
   if (rc) return rc;
   n->adam_t += 1;
   const float b1 = 0.9f, b2 = 0.999f;
@@ -597,8 +615,14 @@ int bipm_mlp_train_step(bipm_mlp* n, const float* x, const float* t, const int* 
   rc = pack_all(n);
   if (rc) return rc;
   if (loss) {
+    int bad = 0;
     CUDA_TRY(cudaMemcpyAsync(loss, n->loss_dev, 8, cudaMemcpyDeviceToHost, n->stream));
+    CUDA_TRY(cudaMemcpyAsync(&bad, n->bad_index, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
     CUDA_TRY(cudaStreamSynchronize(n->stream));
+    if (bad) {
+      cudaMemsetAsync(n->bad_index, 0, sizeof(int), n->stream);
+      return fail(BIPM_EINVAL, "a batch index lies outside [0, n_data) (row 0 was used in its place)");
+    }
   }
   return 0;
 }

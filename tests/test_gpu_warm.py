@@ -262,3 +262,20 @@ def test_trained_warm_start_beats_cold_start(bipm):
     assert conv_w.mean() >= conv_c.mean() - 0.005
     assert np.max(r_warm["kkt_err"][conv_w]) <= 1e-6
     assert it_w < 0.9 * it_c
+
+
+def test_training_rejects_indices_outside_the_data(bipm):
+    widths = (12, 16, 8)
+    rng = np.random.default_rng(51)
+    x = torch.as_tensor(rng.standard_normal((64, 12)).astype(np.float32), device="cuda")
+    t = torch.as_tensor(rng.standard_normal((64, 8)).astype(np.float32), device="cuda")
+    with bipm.MLP(widths, max_rows=32) as net:
+        net.set_params(mlp_init(widths, 52))
+        ok = torch.arange(32, dtype=torch.int32, device="cuda")
+        net.train_step(x, t, ok, 32, 1e-3, want_loss=True)
+        bad = ok.clone()
+        bad[5] = 64  # one past the last row
+        with pytest.raises(bipm.BipmError, match="outside"):
+            net.train_step(x, t, bad, 32, 1e-3, want_loss=True)
+        # the flag is cleared: the next valid step succeeds
+        net.train_step(x, t, ok, 32, 1e-3, want_loss=True)
