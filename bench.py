@@ -46,6 +46,23 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_first_id(rank, batch, steps, warmup):
+    """First problem id of a rank's share (weak scaling): the timed problems
+    (steps x batch), then its warm-up problems; ranks draw disjoint ranges."""
+    return rank * batch * (steps + warmup + 1)
+
+
+def reduce_scalar(v, op, world_size, device):
+    """v combined over the ranks ("max" or "sum"); v itself for one rank."""
+    if world_size == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons while running."""
 
@@ -191,8 +208,9 @@ def run_ours(args):
 
     B, K, W = args.batch, args.steps, args.warmup
     # K steps of B problems each, distinct per step and per rank (weak scaling)
-    desc, theta = make_batch(WORKLOAD, B * K, first_id=rank * B * (K + W + 1))
-    _, theta_w = make_batch(WORKLOAD, B, first_id=rank * B * (K + W + 1) + B * K)
+    first = rank_first_id(rank, B, K, W)
+    desc, theta = make_batch(WORKLOAD, B * K, first_id=first)
+    _, theta_w = make_batch(WORKLOAD, B, first_id=first + B * K)
     theta_dev = torch.as_tensor(theta, device=dev)
     theta_wdev = torch.as_tensor(theta_w, device=dev)
     n, m = desc.n, desc.m
@@ -252,16 +270,9 @@ def run_ours(args):
     e2e_conv = int(np.sum(r_e2e["status"] == bipm.CONVERGED))
 
     def reduce(v, op):
-        if ws == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=op)
-        return float(t.item())
+        return reduce_scalar(v, op, ws, dev)
 
-    import torch.distributed as tdist
-    MAX = tdist.ReduceOp.MAX if ws > 1 else None
-    SUM = tdist.ReduceOp.SUM if ws > 1 else None
+    MAX, SUM = "max", "sum"
     t_mixed = reduce(ms_mixed / 1e3, MAX)
     t_fp64 = reduce(ms_fp64 / 1e3, MAX)
     t_e2e_max = reduce(t_e2e, MAX)

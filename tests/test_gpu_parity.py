@@ -259,6 +259,31 @@ def test_multi_quad_sample(bipm):
             assert e_v(x[j], r["x"]) <= 1e-6
 
 
+def test_multi_quad_n12_outcomes_match_stored_oracle(bipm):
+    """Four quadrotors at horizon 12: the oracle's outcomes (two of eight
+    problems end in restoration failure), stored by
+    tests/golden/make_multi4_n12.py, are reproduced problem by problem."""
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "multi4_n12_oracle.json")
+    with open(path) as fh:
+        golden = json.load(fh)
+    desc = ProblemDesc(nq=4, horizon=12, dt=0.05, pair_dist=0.4)
+    _, theta = make_batch("multi4", 8, desc=desc)
+    with bipm.Batch(desc, 8, bipm.Options(precision=0)) as b:
+        b.set_problems(theta)
+        b.solve()
+        st = b.get_stats()
+        x, _, _, _ = b.get_solution()
+    for j in range(8):
+        assert _same_outcome(bipm, st["status"][j], golden["status"][j]), (j, st["status"][j], golden["status"][j])
+        if golden["status"][j] == ipm.CONVERGED:
+            assert st["kkt_err"][j] <= 1e-6
+            if st["iters"][j] == golden["iters"][j]:
+                assert e_v(x[j], np.asarray(golden["x"][j])) <= 1e-6, j
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_queue_matches_batch_solve(bipm, nav_oracle, precision):
     """Iteration-level batching (a queue through fewer slots than problems)
