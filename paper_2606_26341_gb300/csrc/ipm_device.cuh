@@ -242,25 +242,6 @@ __device__ __forceinline__ IneqRow ineq_row(const Dims& d, const double* th, con
   return r;
 }
 
-// gradient component of row r w.r.t. stage-state component i (0..nx-1); also
-// returns whether the row touches that component
-__device__ __forceinline__ double ineq_grad_at(const IneqRow& r, int i) {
-  int q = i / 12, c = i - 12 * (i / 12);
-  if (c >= r.ncomp) return 0.0;
-  if (q == r.q0) return r.grad[c];
-  if (q == r.q1) return r.grad[3 + c];
-  return 0.0;
-}
-// Hessian entry of row r at stage-state components (i, j)
-__device__ __forceinline__ double ineq_hess_at(const IneqRow& r, int i, int j) {
-  int qi = i / 12, ci = i - 12 * qi;
-  int qj = j / 12, cj = j - 12 * qj;
-  if (ci != cj || ci >= r.ncomp) return 0.0;
-  double si = qi == r.q0 ? 1.0 : (qi == r.q1 ? -1.0 : 0.0);
-  double sj = qj == r.q0 ? 1.0 : (qj == r.q1 ? -1.0 : 0.0);
-  return r.hdiag * si * sj;
-}
-
 // Gradient of inequality j with respect to the positions (value not formed):
 // d g / d p_q0 = g[0..ncomp), and for a pair row d g / d p_q1 = -g.
 struct IneqGrad {
@@ -539,10 +520,7 @@ __device__ __noinline__ void eval_jty(Ctx<TB, TF>& c, const double* x, const dou
     const double* xk = x + off_x(d, k);
     const double* yi = y + row_ineq(d, k);
     double acc = 0.0;
-    for (int r = 0; r < d.ni; ++r) {
-      IneqRow row = ineq_row(d, c.th, xk, r);
-      acc += ineq_grad_at(row, i) * yi[r];
-    }
+    for (int r = 0; r < d.ni; ++r) acc += grad_pos(ineq_grad(d, c.th, xk, r), q, comp) * yi[r];
     jty[off_x(d, k) + i] += acc;
   }
   for (int t = lane; t < d.N * d.ni; t += c.T) {
@@ -871,13 +849,6 @@ __device__ inline int stage_pivot_check(const C& c, const TX* R, double* a64, in
   bad = team_or(c, bad);
   ratio = team_min(c, rmin);
   return bad ? 0 : 1;
-}
-
-// Pivot ratio of a factorised matrix: min_j L_jj^2 / orig_jj
-__device__ __forceinline__ double pivot_ratio(const double* L, const double* diag, int n) {
-  double r = 1.0;
-  for (int j = 0; j < n; ++j) r = fmin(r, L[j * n + j] * L[j * n + j] / fmax(diag[j], 1e-300));
-  return r;
 }
 
 // Restoration: P~ = P - Y^T Y with Y = L_M^{-1} D^1/2 P, M = I + D^1/2 P D^1/2 = L_M L_M^T.
