@@ -1,0 +1,76 @@
+"""Host-side logic around the CUDA library (CPU): result-record parsing of the
+binding, the autotuner's choice, the warm-start network's shape, and the
+dense enumeration of bounded variables the kernels iterate over (restated
+here from its definition: inputs, then slacks, then elastics)."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2606_26341_gb300 import autotune, bipm, warmstart
+from workloads import ProblemDesc, make_batch
+
+
+def test_result_records_round_trip_through_bytes():
+    n = 5
+    arr = (bipm.ResultC * n)()
+    for j in range(n):
+        arr[j].status = j % 3
+        arr[j].iters = 10 * j
+        arr[j].warm = j % 2
+        arr[j].warm_iters = 7 * j
+        arr[j].obj = 0.5 * j
+        arr[j].kkt_err = 1e-7 * j
+    raw = ctypes.string_at(ctypes.addressof(arr), ctypes.sizeof(arr))
+    r = bipm.results_from_bytes(raw)
+    assert list(r["status"]) == [j % 3 for j in range(n)]
+    assert list(r["iters"]) == [10 * j for j in range(n)]
+    assert list(r["warm_iters"]) == [7 * j for j in range(n)]
+    np.testing.assert_array_equal(r["obj"], 0.5 * np.arange(n))
+    assert bipm.RESULT_DTYPE.itemsize == ctypes.sizeof(bipm.ResultC)
+
+
+def test_autotuner_picks_the_fastest_candidate(monkeypatch):
+    rates = {(2, 0.0): 10.0, (1, -1.0): 30.0, (1, 100.0): 20.0}
+    monkeypatch.setattr(autotune, "measure",
+                        lambda desc, th, o, cap, stream=None: rates[(o.precision, o.fp32_switch)])
+    best, table = autotune.autotune(None, None, 0)
+    assert (best.precision, best.fp32_switch) == (1, -1.0)
+    assert [v for _, v in table] == [10.0, 30.0, 20.0]
+
+
+def test_warm_start_network_shape_follows_the_family():
+    desc, _ = make_batch("cyl", 1)
+    assert warmstart.widths(desc) == (162, 256, 256, 256, 652)
+    short = ProblemDesc(nq=1, horizon=12, dt=0.05, n_cyl=50)
+    assert warmstart.widths(short, k_near=10) == (42, 256, 256, 256, 12 * 13 + 4 * 12)
+
+
+def _bounded_dense(desc, resto):
+    """Positions of the bounded entries in the order the kernels enumerate them."""
+    N, nx, nu, ni, n, m = desc.horizon, desc.nx, desc.nu, desc.ni, desc.n, desc.m
+
+    def off_x(k):
+        return 0 if k == 0 else (nx + nu) + (k - 1) * (nx + nu + ni)
+
+    out = [off_x(k) + nx + a for k in range(N) for a in range(nu)]
+    out += [off_x(k) + nx + (nu if k < N else 0) + r for k in range(1, N + 1) for r in range(ni)]
+    if resto:
+        out += list(range(n, n + 2 * m))
+    return out
+
+
+@pytest.mark.parametrize("name", ["nav1", "track", "multi4"])
+def test_bounded_entries_are_exactly_the_inputs_and_slacks(name):
+    """The dense numbering covers each bounded variable once and no free one."""
+    from oracle.quadrotor import QuadNLP
+
+    desc, theta = make_batch(name, 1, desc=None if name != "multi4" else
+                             ProblemDesc(nq=4, horizon=6, dt=0.05, pair_dist=0.4))
+    nlp = QuadNLP(desc, theta[0])
+    pos = _bounded_dense(desc, resto=False)
+    assert len(pos) == len(set(pos))
+    bounded = set(np.nonzero(np.isfinite(nlp.xl) | np.isfinite(nlp.xu))[0])
+    assert set(pos) == bounded
+    assert len(_bounded_dense(desc, resto=True)) == len(pos) + 2 * desc.m
