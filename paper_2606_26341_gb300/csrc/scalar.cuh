@@ -41,9 +41,17 @@ __host__ __device__ __forceinline__ double val(double a) { return a; }
 __host__ __device__ __forceinline__ float val(float a) { return a; }
 template <class T> __host__ __device__ __forceinline__ T val(Dual<T> a) { return a.v; }
 
+#ifdef __CUDACC__
+// One out-of-line copy of each trigonometric routine per translation unit: the
+// RK4 routines call them twelve times per step in several scalar types, and
+// inlining every call site multiplies the code the instruction cache must hold
+// (the iteration kernels run 24 warps per SM at different points of the code).
+static __device__ __noinline__ void sincos_out(double a, double* s, double* c) { sincos(a, s, c); }
+static __device__ __noinline__ void sincosf_out(float a, float* s, float* c) { sincosf(a, s, c); }
+#endif
 __host__ __device__ __forceinline__ void sincos_s(double a, double* s, double* c) {
 #ifdef __CUDA_ARCH__
-  sincos(a, s, c);
+  sincos_out(a, s, c);
 #else
   *s = ::sin(a);
   *c = ::cos(a);
@@ -51,7 +59,7 @@ __host__ __device__ __forceinline__ void sincos_s(double a, double* s, double* c
 }
 __host__ __device__ __forceinline__ void sincos_s(float a, float* s, float* c) {
 #ifdef __CUDA_ARCH__
-  sincosf(a, s, c);
+  sincosf_out(a, s, c);
 #else
   *s = ::sinf(a);
   *c = ::cosf(a);
