@@ -21,6 +21,15 @@ one problem at a time:
   notes.  Linear algebra is the dense full-space augmented matrix factorised
   by LAPACK's Bunch-Kaufman LDL^T (scipy.linalg.ldl); inertia is read off D.
 
+* ``mlp``        - the learned warm start's network in FP64 (forward pass,
+  chain-rule gradient, Adam), optionally rounding product operands to
+  bfloat16 at the CUDA kernels' rounding points.
+* ``warm``       - the warm start's encodings (network input features,
+  training targets, decoding of a network output into a starting point) and
+  the warm starting options of the iteration.
+* ``generic``    - small NLPs from PyTorch callables, for the closed-form and
+  brute-force pins.
+
 Parity unpinned: none of the functions here is left without a pin; the pins
 live in tests/test_oracle_*.py.
 """
