@@ -326,6 +326,7 @@ def run_ours(args):
                          for o, v in tune_table],
             "converged_frac": conv_mixed / (B * K),
             "iters_mean": float(np.mean(r_mixed["iters"])),
+            "iterations": iteration_summary(r_mixed),
             "e2e": {"value": tot_e2e / t_e2e_max, "unit": UNIT,
                     "h2d_bytes_per_step": B * desc_theta_len(desc) * 8,
                     "d2h_bytes_per_step": B * (n * 8 + rsize)},
@@ -456,6 +457,23 @@ def mixed_leg(args, dev, stream, barrier, reduce, MAX, SUM):
             "value": reduce(float(conv.sum()), SUM) / dt, "unit": UNIT, "seconds": dt,
             "converged_frac": float(conv.mean()), "iters_mean": float(r["iters"].mean()),
             "per_quad_count": per_nq}
+
+
+def iteration_summary(results, converged_status=1):
+    """Iteration counts (mean, percentiles, max), histogram over fixed bins and
+    the mean objective of the converged problems, from a result-record dict."""
+    it = np.asarray(results["iters"])
+    conv = np.asarray(results["status"]) == converged_status
+    edges = [0, 10, 20, 30, 50, 100, 200, 500, 10 ** 9]
+    hist, _ = np.histogram(it, bins=edges)
+    return {"mean": float(it.mean()) if it.size else 0.0,
+            "p50": float(np.percentile(it, 50)) if it.size else 0.0,
+            "p90": float(np.percentile(it, 90)) if it.size else 0.0,
+            "p99": float(np.percentile(it, 99)) if it.size else 0.0,
+            "max": int(it.max()) if it.size else 0,
+            "histogram": {f"{edges[i]}-{edges[i + 1] - 1}" if i < len(edges) - 2 else f">={edges[i]}": int(h)
+                          for i, h in enumerate(hist)},
+            "objective_mean_converged": float(np.mean(np.asarray(results["obj"])[conv])) if conv.any() else None}
 
 
 def queue_launches(slots):

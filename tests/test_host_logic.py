@@ -74,3 +74,15 @@ def test_bounded_entries_are_exactly_the_inputs_and_slacks(name):
     bounded = set(np.nonzero(np.isfinite(nlp.xl) | np.isfinite(nlp.xu))[0])
     assert set(pos) == bounded
     assert len(_bounded_dense(desc, resto=True)) == len(pos) + 2 * desc.m
+
+
+def test_iteration_summary_of_the_benchmark():
+    import bench
+
+    r = {"iters": np.array([5, 12, 25, 25, 40, 150, 500]), "status": np.array([1, 1, 1, 1, 1, 3, 2]),
+         "obj": np.array([1.0, 2.0, 3.0, 4.0, 5.0, 100.0, 100.0])}
+    s = bench.iteration_summary(r)
+    assert s["max"] == 500 and s["p50"] == 25.0
+    assert sum(s["histogram"].values()) == 7
+    assert s["histogram"]["0-9"] == 1 and s["histogram"]["20-29"] == 2 and s["histogram"][">=500"] == 1
+    assert s["objective_mean_converged"] == 3.0
