@@ -127,7 +127,7 @@ def measured_peaks():
 
 # ------------------------------------------------------------- flop model
 # Operation counts of the model routines, from the host instantiation of the
-# device templates with a counting scalar (paper_2606_26341_gb300/csrc/opcount.cpp;
+# device templates with a counting scalar (tests/opcount.cpp;
 # tests/test_flop_model.py recompiles it and checks these numbers).
 RK4_VALUE_FLOPS = 152 + 200 + 4            # one RK4 step of one quadrotor, value only
 RK4_ADJOINT_FLOPS = 403 + 620 + 4          # value + reverse sweep (gradient of lam^T F)

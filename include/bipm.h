@@ -32,10 +32,12 @@
  *
  * Errors: every int-returning call returns 0 on success or a negative code
  * (BIPM_EINVAL bad argument or size, BIPM_ENOMEM allocation failure,
- * BIPM_ECUDA CUDA error, BIPM_ESTATE call not valid in this state);
- * bipm_last_error() returns a thread-local message for the last failure.
- * Per-problem outcomes (converged, iteration cap, ...) are data, reported in
- * bipm_stats.status, never as a call error.
+ * BIPM_ECUDA CUDA error, BIPM_ESTATE call not valid in this state,
+ * BIPM_ETIMEOUT the call's device time budget bipm_options.time_limit_ms ran
+ * out before every problem terminated); bipm_last_error() returns a
+ * thread-local message for the last failure.  Per-problem outcomes (converged,
+ * iteration cap, ...) are data, reported in bipm_stats.status /
+ * bipm_result.status, never as a call error.
  */
 #ifndef BIPM_H
 #define BIPM_H
@@ -48,21 +50,37 @@ extern "C" {
 #define BIPM_ENOMEM (-12)
 #define BIPM_ECUDA (-100)
 #define BIPM_ESTATE (-101)
+#define BIPM_ETIMEOUT (-102)
 
-/* per-problem status */
+/* Per-problem status (the termination tests of Sec. IV and Table I):
+ * RUNNING        not terminated (also: stopped by the time budget)
+ * CONVERGED      scaled optimality error E_0 of Eq. 5 (mu = 0) <= tol
+ * MAX_ITER       iteration cap reached
+ * RESTO_FAILED   hard feasibility restoration (Table I row 6) failed: its own
+ *                line search failed, it converged to an infeasible stationary
+ *                point, or restoration was needed at a feasible point
+ * EVAL_ERROR     non-finite objective, constraint or gradient value
+ * TINY_STEP      a tiny step (Table I row 4) at the smallest barrier parameter
+ * EMPTY          the slot holds no problem (a queue problem never started)
+ * FP64_ESCALATION_FAILED  mixed precision: iterative refinement of the FP32
+ *                step failed, and the FP64 re-factorisation that replaced it
+ *                did not solve the Newton system (Eq. 7) to a residual ratio
+ *                of 1e-6 either */
 #define BIPM_RUNNING 0
 #define BIPM_CONVERGED 1
 #define BIPM_MAX_ITER 2
 #define BIPM_RESTO_FAILED 3
 #define BIPM_EVAL_ERROR 4
 #define BIPM_TINY_STEP 5
-#define BIPM_EMPTY 6 /* slot holds no problem */
+#define BIPM_EMPTY 6
+#define BIPM_FP64_ESCALATION_FAILED 7
 
 #define BIPM_FILTER_CAP 64
 
 typedef struct bipm_batch bipm_batch;
 
-/* Shared structure of one batch (Eq. 2: identical f, c and bounds). */
+/* Shared structure of one batch (Sec. III, Eq. 2: every instance of a batch
+ * has the same f, c and bounds; the quadrotor NMPC family of Sec. VI). */
 typedef struct {
   int n_quads;        /* quadrotors per problem, 1..8 */
   int horizon;        /* N, number of RK4 intervals, >= 1 */
@@ -72,6 +90,9 @@ typedef struct {
   double pair_dist;   /* minimum pairwise distance; 0 disables the pair rows */
 } bipm_problem_desc;
 
+/* Algorithm options (Sec. IV; the constants the paper defers to IPOPT are
+ * fixed inside the library).  A zero-initialised record is not valid: start
+ * from the documented defaults. */
 typedef struct {
   double tol;         /* scaled KKT tolerance E_0 (default 1e-6) */
   int max_iter;       /* iteration cap, restoration iterations included (500) */
@@ -95,10 +116,20 @@ typedef struct {
                              (0 = default 1e-3) */
   int warm_max_iter;      /* iteration budget of a warm-started run before the
                              cold fallback (0 = default 60; capped by max_iter) */
-  int reserved_;          /* must be 0 */
+  int time_limit_ms;      /* device time budget of one solve or step call in
+                             milliseconds, 0 = none.  Measured on the GPU's
+                             clock from the call's first iteration; every team
+                             checks it before each iteration and before starting
+                             a queue problem.  When it runs out, running
+                             problems stop at an iteration boundary (status
+                             RUNNING; a batch's slots keep their state and the
+                             next bipm_solve continues them), queue problems not
+                             yet started report EMPTY, and the call returns
+                             BIPM_ETIMEOUT. */
 } bipm_options;
 
-/* Per-slot outcome and counters. */
+/* Per-slot outcome and counters: the branches of Table I each problem took
+ * and the optimality measures of Eq. 5 at its final iterate. */
 typedef struct {
   int status;
   int iters;            /* iterations taken (restoration included) */
@@ -121,11 +152,14 @@ typedef struct {
 } bipm_stats;
 
 /* Per-slot SM clock cycles spent in the phases of the iterations so far
- * (profile counters): eval, derivatives, factorisation, solve, line search,
- * other, least-squares multipliers, total.  out holds count x 8 values. */
+ * (profile counters; the paper has no counterpart): eval, derivatives,
+ * factorisation, solve, line search, other, least-squares multipliers, total.
+ * out (host) holds count x 8 values.  Errors: BIPM_EINVAL for a bad slot
+ * range or a NULL out. */
 int bipm_get_phase_cycles(const bipm_batch* b, long long* out, int first_slot, int count);
 
-/* Outcome of one problem solved through the queue. */
+/* Outcome of one problem solved through the queue (Sec. V, iteration-level
+ * batching: results leave the slot when the problem terminates). */
 typedef struct {
   int status;
   int iters;
@@ -173,29 +207,47 @@ typedef struct {
   double mu_r, dw_last_r, theta_max_r, theta_min_r, zeta, theta_ref;
 } bipm_iterate;
 
-/* Creates a batch of `capacity` slots for problems of structure `desc`.
- * `cuda_stream` is a cudaStream_t (NULL = default stream) used by every call. */
+/* Creates a batch of `capacity` slots for problems of structure `desc` (the
+ * batch of Sec. III, Eq. 2: instances sharing f, c and bounds, differing in
+ * theta).  opt NULL = defaults.  `cuda_stream` is a cudaStream_t (NULL = default
+ * stream) used by every later call on the batch.  *out receives the batch
+ * (NULL on error); the batch owns its device memory until bipm_destroy.
+ * Errors: BIPM_EINVAL (bad desc, capacity < 0, bad options), BIPM_ENOMEM,
+ * BIPM_ECUDA. */
 int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_options* opt,
                       void* cuda_stream, bipm_batch** out);
 
-/* Sizes of one problem: primal n, equalities m, parameters n_theta. */
+/* Sizes of one problem of Eq. 1: primal n (slacks included), equalities m,
+ * parameters n_theta; any output pointer may be NULL.  Errors: BIPM_EINVAL for
+ * a NULL batch. */
 int bipm_dims(const bipm_batch* b, int* n, int* m, int* n_theta);
 
-/* Loads `count` parameter vectors (count x n_theta, row-major) into slots
+/* Loads `count` parameter vectors theta_i (the rows of Theta in Eq. 2;
+ * count x n_theta, row-major, host or device per on_device) into slots
  * first_slot.. and resets those slots to the default starting point (states
  * at xbar, hover thrust, slacks at the inequality values), pushed inside the
- * bounds as in IPOPT's initialisation; z = 1; y from least squares at the
- * first iteration. */
+ * bounds as in IPOPT's initialisation (Sec. IV defers to it); z = 1; y from
+ * least squares at the first iteration; mu = mu_init.  Returns after the copy
+ * and initialisation finished.  Errors: BIPM_EINVAL (slot range outside the
+ * capacity, NULL theta), BIPM_ECUDA. */
 int bipm_set_problems(bipm_batch* b, const double* theta, int first_slot, int count,
                       int on_device);
 
-/* Replaces the primal starting point (count x n) of slots first_slot.. (after
- * bipm_set_problems); y (count x m) may be NULL (least squares). */
+/* Replaces the primal starting point x (count x n, the variable order of
+ * the layout above) of slots first_slot.. after bipm_set_problems; y
+ * (count x m) may be NULL (least squares at the first iteration).  The point
+ * is pushed inside the bounds as the default start is.  Host or device
+ * pointers per on_device.  Errors: BIPM_EINVAL, BIPM_ENOMEM (staging),
+ * BIPM_ECUDA. */
 int bipm_set_initial_guess(bipm_batch* b, const double* x, const double* y, int first_slot,
                            int count, int on_device);
 
-/* Runs every loaded slot to termination (persistent kernel; a warp that
- * finishes its problem takes the next unfinished one). */
+/* Runs every loaded slot to termination: the iteration of Sec. IV with every
+ * branch of Table I taken per problem inside one persistent kernel
+ * (heterogeneous iteration fusion, Sec. V); a warp that finishes its problem
+ * takes the next unfinished one.  Per-problem outcomes go to bipm_get_stats.
+ * Errors: BIPM_EINVAL (NULL batch), BIPM_ESTATE (nothing loaded), BIPM_ECUDA,
+ * BIPM_ETIMEOUT (time_limit_ms ran out; call again to continue). */
 int bipm_solve(bipm_batch* b);
 
 /* Iteration-level batching (Sec. V "Iteration level batching"): solves the
@@ -205,7 +257,11 @@ int bipm_solve(bipm_batch* b);
  * may be NULL) and result record, then starts the next problem of the queue
  * in the same slot.  Problems start in queue order from the default starting
  * point.  All pointers are device pointers (on_device = 1) or host pointers
- * (0).  The slots' previous contents are overwritten. */
+ * (0; copies in and out are part of the call).  The slots' previous contents
+ * are overwritten.  Returns when every problem has its record.  Errors:
+ * BIPM_EINVAL (NULL theta_queue or results, n_queue < 0), BIPM_ESTATE (no
+ * slots), BIPM_ENOMEM (host-pointer staging), BIPM_ECUDA, BIPM_ETIMEOUT
+ * (records of unfinished problems say RUNNING or EMPTY). */
 int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, double* x_out,
                      bipm_result* results, int on_device);
 
@@ -217,8 +273,9 @@ int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, doub
  * least squares.  Cold start is the fallback and the KKT residual the judge:
  * a warm-started run that has not terminated converged (E_0 <= tol) within
  * warm_max_iter iterations is rerun from the cold start in the same slot
- * (bipm_result.warm = 2).  Pointers as
- * for bipm_solve_queue (x_guess on the same side as theta_queue). */
+ * (bipm_result.warm = 2).  The learned proposer has no counterpart in the
+ * paper.  Pointers and errors as for bipm_solve_queue (x_guess on the same
+ * side as theta_queue; BIPM_EINVAL if it is NULL). */
 int bipm_solve_queue_warm(bipm_batch* b, const double* theta_queue, const double* x_guess, int n_queue,
                           double* x_out, bipm_result* results, int on_device);
 
@@ -234,16 +291,19 @@ int bipm_solve_queue_warm(bipm_batch* b, const double* theta_queue, const double
  * queue drains.  Precision 0 or 1 (options as for bipm_create_batch; NULL =
  * defaults).  theta, x_out and results are device pointers (on_device = 1) or
  * host pointers (0).  The call allocates its workspace, runs on cuda_stream
- * (NULL = default stream) and returns when the solve has finished. */
+ * (NULL = default stream) and returns when the solve has finished.  Errors:
+ * BIPM_EINVAL (bad class, count or option), BIPM_ENOMEM, BIPM_ECUDA,
+ * BIPM_ETIMEOUT. */
 int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm_options* opt, int n_slots,
                      const int* cls, const double* theta, int n_queue, double* x_out, bipm_result* results,
                      int on_device, void* cuda_stream);
 
-/* One-shot solve that allocates nothing (the paper has no counterpart; this
- * is an addition for callers that cannot allocate device memory when they
- * need a solve: code inside a CUDA stream capture, where cudaMalloc is not
- * permitted, real-time loops that must stay out of the allocator, and
- * processes whose device memory budget is fixed in advance).
+/* One-shot solve that allocates nothing.  The paper has no counterpart: this
+ * entry point is an addition for callers that cannot allocate device memory at
+ * the moment they need a solve -- real-time control loops that must stay out
+ * of the CUDA allocator (cudaMalloc can block, synchronise the device or fail
+ * under fragmentation), and processes whose device memory is budgeted in
+ * advance and may not grow after start-up.
  *
  * Solves `count` problems of structure `desc` (theta: count x n_theta) with
  * the same queue (iteration-level batching) kernel as bipm_solve_queue, but
@@ -258,19 +318,23 @@ int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm
  *
  * The first call on a device looks up the array's device address on that
  * device (with it current); make that first call before any stream capture.
- * All calls share the array and find the previous call's contents in it; the
- * call resets what must start afresh (the queue counter and each problem's
- * slot), but calls that overlap on the GPU (other streams, other threads)
- * race on the array and must be serialised by the caller.  `cuda_stream` is
- * the stream to run on (NULL = default); the call returns when the solve has
- * finished.  Errors as for the other calls (bipm_last_error). */
+ * The call copies its launch record from host memory and waits for the solve
+ * to finish on `cuda_stream` (NULL = default stream) before it returns.  All
+ * calls share the array and find the previous call's contents in it; the call
+ * resets what must start afresh (the queue and time-budget counters and each
+ * problem's slot), but calls that overlap on the GPU (other streams, other
+ * threads) race on the array and must be serialised by the caller.  Errors as
+ * for bipm_solve_queue (bipm_last_error). */
 int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, const double* theta,
                       int count, double* x_out, bipm_result* results, void* cuda_stream);
 
 /* ---------------------------------------------------------------- warm start
  * Encodings of the learned warm start for the cluttered-environment family
  * (one quadrotor, n_cylinders vertical cylinders, no spheres, no pairs, a fixed
- * goal in the reference slot).  All pointers are DEVICE pointers on
+ * goal in the reference slot).  The paper has no counterpart (it names
+ * imitation learning on this solver's trajectories only as future work,
+ * Sec. VII); the proposer maps a problem's parameters theta (Eq. 2) to a
+ * primal starting point.  All pointers are DEVICE pointers on
  * `cuda_stream` (NULL = default stream); the calls return after launching.
  *
  * bipm_warm_features: network input of each problem, count x (12 + 3 k_near)
@@ -283,7 +347,7 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
  * bipm_warm_decode: primal starting points (count x n doubles) from network
  *   outputs in the target encoding: x_0 = xbar, x_k = xbar + S o_k (k >= 1),
  *   u_k = u_hover (1 + o), slacks at the cylinder inequality values g(x_k).
- * Errors: BIPM_EINVAL for another problem family or bad sizes. */
+ * Errors: BIPM_EINVAL for another problem family or bad sizes; BIPM_ECUDA. */
 int bipm_warm_features(const bipm_problem_desc* desc, const double* theta, int count, int k_near,
                        float* features, void* cuda_stream);
 int bipm_warm_encode(const bipm_problem_desc* desc, const double* theta, const double* x, int count,
@@ -303,21 +367,30 @@ int bipm_warm_decode(const bipm_problem_desc* desc, const double* theta, const f
  * Parameters are one flat FP32 vector: per layer W_l (width_l x width_{l-1},
  * row-major) then b_l.  x: rows x widths[0], t and out: rows x widths[last],
  * row-major FP32.  The network owns its device memory; `on_device` selects
- * device (1) or host (0) pointers for the caller's buffers. */
+ * device (1) or host (0) pointers for the caller's buffers.  The paper has no
+ * counterpart (see the warm-start encodings above).  Errors: BIPM_EINVAL (bad
+ * sizes, NULL pointers, rows above max_rows), BIPM_ENOMEM, BIPM_ECUDA. */
 typedef struct bipm_mlp bipm_mlp;
 
 /* widths: n_widths layer widths (input, hidden..., output), 2 <= n_widths <= 9;
  * max_rows: largest batch of a gradient or training call.  Parameters start
- * at zero (set them with bipm_mlp_set_params). */
+ * at zero (set them with bipm_mlp_set_params).  Errors as for the network calls
+ * (above). */
 int bipm_mlp_create(const int* widths, int n_widths, int max_rows, void* cuda_stream, bipm_mlp** out);
+/* Number of flat parameters.  Errors as for the network calls (above). */
 int bipm_mlp_param_count(const bipm_mlp* net, long long* count);
-/* Loads the FP32 master parameters and resets Adam's moments and step count. */
+/* Loads the FP32 master parameters and resets Adam's moments and step count.
+ * Errors as for the network calls (above). */
 int bipm_mlp_set_params(bipm_mlp* net, const float* params, int on_device);
+/* Copies the FP32 master parameters out.  Errors as for the network calls
+ * (above). */
 int bipm_mlp_get_params(const bipm_mlp* net, float* params, int on_device);
-/* out = network(x) for any number of rows (processed max_rows at a time). */
+/* out = network(x) for any number of rows (processed max_rows at a time).
+ * Errors as for the network calls (above). */
 int bipm_mlp_forward(bipm_mlp* net, const float* x, int rows, float* out, int on_device);
 /* Loss and its gradient with respect to the flat parameters (rows <= max_rows);
- * grad (n_params floats) and loss (one double) may be NULL. */
+ * grad (n_params floats) and loss (one double) may be NULL.  Errors as for the
+ * network calls (above). */
 int bipm_mlp_loss_grad(bipm_mlp* net, const float* x, const float* t, int rows, float* grad, double* loss,
                        int on_device);
 /* One Adam step on the batch of rows idx[0..rows) of the n_data rows of x and
@@ -325,30 +398,49 @@ int bipm_mlp_loss_grad(bipm_mlp* net, const float* x, const float* t, int rows, 
  * An index outside [0, n_data) is replaced by row 0 and reported by the next
  * call with a loss pointer (BIPM_EINVAL).  loss (host, may be NULL) receives
  * the batch loss before the step; without it the call returns after
- * launching. */
+ * launching.  Errors as for the network calls (above). */
 int bipm_mlp_train_step(bipm_mlp* net, const float* x, const float* t, int n_data, const int* idx, int rows,
                         float lr, double* loss);
+/* Frees the network and its device memory (NULL is a no-op; no error; the
+ * paper has no counterpart). */
 void bipm_mlp_destroy(bipm_mlp* net);
 
-/* Runs exactly `n_iterations` iterations on every running slot. */
+/* Runs exactly `n_iterations` iterations (the fused iteration body of
+ * Sec. V, one step of Sec. IV per problem) on every running slot; terminated
+ * slots are left as they are.  Used by the state-injection test of Sec. VI
+ * (Eq. 8) with n_iterations = 1.  Errors: BIPM_EINVAL (NULL batch,
+ * n_iterations < 1), BIPM_ESTATE (nothing loaded), BIPM_ECUDA, BIPM_ETIMEOUT. */
 int bipm_step(bipm_batch* b, int n_iterations);
 
-/* Copies the final original-problem iterate of slots first_slot..; any output
- * pointer may be NULL.  Shapes count x n (x, zl, zu) and count x m (y). */
+/* Copies the current original-problem iterate (x, y_c, z_L, z_U) of Eq. 4 of
+ * slots first_slot.. -- the rows X_i of Eq. 2 and their multipliers; any
+ * output pointer may be NULL.  Shapes count x n (x, zl, zu; zeros where a
+ * variable has no such bound) and count x m (y).  Host or device pointers per
+ * on_device.  Errors: BIPM_EINVAL (slot range), BIPM_ENOMEM (staging),
+ * BIPM_ECUDA. */
 int bipm_get_solution(const bipm_batch* b, double* x, double* y, double* zl, double* zu,
                       int first_slot, int count, int on_device);
 
-/* Per-slot status and counters (host array of `count` records). */
+/* Per-slot status and counters (host array of `count` records; see
+ * bipm_stats).  Errors: BIPM_EINVAL (slot range, NULL out), BIPM_ECUDA. */
 int bipm_get_stats(const bipm_batch* b, bipm_stats* out, int first_slot, int count);
 
-/* Reads / writes the complete state of one slot (host arrays). */
+/* Reads / writes the complete solver state of one slot (host arrays; see
+ * bipm_iterate): the state-injection interface of Sec. VI "Correctness"
+ * (Eq. 8).  bipm_set_iterate needs the slot's problem loaded first
+ * (BIPM_ESTATE) and rejects filter lengths outside 0..64 and modes other than
+ * 0 and 1 (BIPM_EINVAL). */
 int bipm_get_iterate(const bipm_batch* b, int slot, bipm_iterate* out);
 int bipm_set_iterate(bipm_batch* b, int slot, const bipm_iterate* in);
 
-/* Thread-local message of the last failed call ("" if none). */
+/* Thread-local message of the last failed call ("" if none); the pointer
+ * stays valid until the thread's next failing call.  The paper has no
+ * counterpart; it cannot fail. */
 const char* bipm_last_error(void);
 
-/* Frees the batch and all its device memory. */
+/* Frees the batch of Sec. III, Eq. 2 and all its device memory (NULL is a
+ * no-op; no error).  Waits for nothing: call it after the batch's last call
+ * returned. */
 void bipm_destroy(bipm_batch* b);
 
 #ifdef __cplusplus

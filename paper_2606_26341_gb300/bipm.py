@@ -15,10 +15,11 @@ import numpy as np
 
 from . import build as _build
 
-RUNNING, CONVERGED, MAX_ITER, RESTO_FAILED, EVAL_ERROR, TINY_STEP, EMPTY = range(7)
+RUNNING, CONVERGED, MAX_ITER, RESTO_FAILED, EVAL_ERROR, TINY_STEP, EMPTY, FP64_ESCALATION_FAILED = range(8)
 STATUS_NAMES = {RUNNING: "running", CONVERGED: "converged", MAX_ITER: "max_iter",
                 RESTO_FAILED: "resto_failed", EVAL_ERROR: "eval_error", TINY_STEP: "tiny_step",
-                EMPTY: "empty"}
+                EMPTY: "empty", FP64_ESCALATION_FAILED: "fp64_escalation_failed"}
+EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = -22, -12, -100, -101, -102
 FILTER_CAP = 64
 
 
@@ -33,7 +34,7 @@ class OptionsC(ctypes.Structure):
                 ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("fp32_switch", ctypes.c_double), ("warm_mu_init", ctypes.c_double),
                 ("warm_bound_push", ctypes.c_double), ("warm_max_iter", ctypes.c_int),
-                ("reserved_", ctypes.c_int)]
+                ("time_limit_ms", ctypes.c_int)]
 
 
 class StatsC(ctypes.Structure):
@@ -148,7 +149,11 @@ def load_library(build_if_missing: bool = True):
 
 
 class BipmError(RuntimeError):
-    pass
+    """A failed library call; `code` is the C return value (EINVAL, ETIMEOUT, ...)."""
+
+    def __init__(self, msg, code=0):
+        super().__init__(msg)
+        self.code = code
 
 
 def solve_static(desc, theta_dev, x_out=None, results=None, options: "Options | None" = None,
@@ -174,7 +179,7 @@ def solve_static(desc, theta_dev, x_out=None, results=None, options: "Options | 
 def _check(rc):
     if rc != 0:
         msg = load_library(False).bipm_last_error().decode()
-        raise BipmError(f"bipm error {rc}: {msg}")
+        raise BipmError(f"bipm error {rc}: {msg}", rc)
 
 
 def _ptr(arr):
@@ -202,10 +207,12 @@ class Options:
     warm_mu_init: float = 0.0     # mu_0 of a warm start (0: library default 1e-2)
     warm_bound_push: float = 0.0  # bound push of a warm start (0: library default 1e-3)
     warm_max_iter: int = 0        # iteration budget of a warm start (0: library default 60)
+    time_limit_ms: int = 0        # device time budget of one call (0: none; BIPM_ETIMEOUT when spent)
 
     def to_c(self):
         return OptionsC(self.tol, self.max_iter, self.mu_init, self.precision, self.schedule,
-                        self.fp32_switch, self.warm_mu_init, self.warm_bound_push, self.warm_max_iter, 0)
+                        self.fp32_switch, self.warm_mu_init, self.warm_bound_push, self.warm_max_iter,
+                        self.time_limit_ms)
 
 
 def _stream_ptr(stream):
@@ -291,8 +298,15 @@ class Batch:
             _check(call(ctypes.c_void_p(results.data_ptr()), 1))
             return None
         arr = (ResultC * max(nq, 1))()
-        _check(call(arr, 0))
-        return {f: np.array([getattr(arr[j], f) for j in range(nq)]) for f, _ in ResultC._fields_}
+        rc = call(arr, 0)
+        out = {f: np.array([getattr(arr[j], f) for j in range(nq)]) for f, _ in ResultC._fields_}
+        try:
+            _check(rc)
+        except BipmError as e:
+            if rc == ETIMEOUT:  # the records are valid: unfinished problems say RUNNING / EMPTY
+                e.results = out
+            raise
+        return out
 
     def step(self, n_iterations: int = 1):
         _check(self.lib.bipm_step(self.h, n_iterations))

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/bipm.h"
+#include "host_api.h"
 #include "kernels.cuh"
 
 using namespace bipm;
@@ -35,6 +36,73 @@ int fail(int code, const std::string& msg) {
 namespace bipm {
 // records the message bipm_last_error() returns (used by every entry point)
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+bipm_options default_options() {
+  bipm_options o;
+  std::memset(&o, 0, sizeof(o));
+  o.tol = 1e-6;
+  o.max_iter = 500;
+  o.mu_init = 0.1;
+  return o;
+}
+
+// Validated dims of one problem structure (0, or an error code with message).
+int dims_from_desc(const bipm_problem_desc* desc, Dims* out) {
+  if (desc->n_quads < 1 || desc->n_quads > 8) return fail(BIPM_EINVAL, "n_quads must be 1..8");
+  if (desc->horizon < 1 || desc->horizon > 1000) return fail(BIPM_EINVAL, "horizon must be 1..1000");
+  if (!(desc->dt > 0.0) || !std::isfinite(desc->dt)) return fail(BIPM_EINVAL, "dt must be > 0");
+  if (desc->n_spheres < 0 || desc->n_cylinders < 0 || desc->n_spheres > 256 || desc->n_cylinders > 256)
+    return fail(BIPM_EINVAL, "obstacle counts must be 0..256");
+  if (!(desc->pair_dist >= 0.0)) return fail(BIPM_EINVAL, "pair_dist must be >= 0");
+  Dims d;
+  std::memset(&d, 0, sizeof(d));
+  d.nq = desc->n_quads;
+  d.N = desc->horizon;
+  d.nx = 12 * d.nq;
+  d.nu = 4 * d.nq;
+  d.n_sph = desc->n_spheres;
+  d.n_cyl = desc->n_cylinders;
+  d.n_pairs = desc->pair_dist > 0.0 ? d.nq * (d.nq - 1) / 2 : 0;
+  d.ni = d.nq * d.n_sph + d.nq * d.n_cyl + d.n_pairs;
+  d.n = d.nx * (d.N + 1) + (d.nu + d.ni) * d.N;
+  d.m = d.nx * (d.N + 1) + d.ni * d.N;
+  d.dt = desc->dt;
+  d.pair_d = desc->pair_dist;
+  d.th_x = 0;
+  d.th_ref = 12 * d.nq;
+  d.th_sph = d.th_ref + 6 * d.nq;
+  d.th_cyl = d.th_sph + 4 * d.n_sph;
+  d.n_theta = d.th_cyl + 3 * d.n_cyl;
+  *out = d;
+  return 0;
+}
+
+// Options with defaults filled in, validated; device options in *dev.
+int options_from(const bipm_options* opt, bipm_options* o_out, Options* dev) {
+  bipm_options o = opt ? *opt : default_options();
+  if (o.fp32_switch == 0.0) o.fp32_switch = kFp32BarrierMax;
+  if (o.warm_mu_init == 0.0) o.warm_mu_init = 1e-2;
+  if (o.warm_bound_push == 0.0) o.warm_bound_push = 1e-3;
+  if (o.warm_max_iter == 0) o.warm_max_iter = 60;
+  if (o.warm_max_iter < 0) return fail(BIPM_EINVAL, "warm_max_iter must be >= 0");
+  if (!(o.warm_mu_init > 0.0) || !(o.warm_bound_push > 0.0) || !(o.warm_bound_push < 0.5))
+    return fail(BIPM_EINVAL, "warm_mu_init must be > 0 and warm_bound_push in (0, 0.5)");
+  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || o.precision < 0 || o.precision > 2 ||
+      o.schedule < 0 || o.schedule > 2)
+    return fail(BIPM_EINVAL, "bad options");
+  if (o.time_limit_ms < 0) return fail(BIPM_EINVAL, "time_limit_ms must be >= 0");
+  dev->tol = o.tol;
+  dev->max_iter = o.max_iter;
+  dev->mu_init = o.mu_init;
+  dev->precision = o.precision;
+  dev->fp32_switch = o.fp32_switch;
+  dev->warm_mu = o.warm_mu_init;
+  dev->warm_push = o.warm_bound_push;
+  dev->warm_max_iter = std::min(o.warm_max_iter, o.max_iter);
+  *o_out = o;
+  return 0;
+}
+
 }  // namespace bipm
 
 struct bipm_batch {
@@ -58,6 +126,7 @@ struct bipm_batch {
   int block_blocks = 0;
   int schedule = 0;
   int loaded = 0;
+  int time_limit_ms = 0;
 };
 
 namespace bipm {
@@ -184,8 +253,30 @@ int ensure_stage(bipm_batch* b, size_t bytes) {
   return 0;
 }
 
+// Clears the time-budget clock and flag before a call's first launch.
+int begin_call(int* counter, cudaStream_t stream) {
+  CUDA_TRY(cudaMemsetAsync(counter + 2, 0, (kCounterInts - 2) * sizeof(int), stream));
+  return 0;
+}
+
+// Waits for the call's work and reports an exhausted time budget.
+int end_call(const int* counter, int time_limit_ms, cudaStream_t stream) {
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  if (time_limit_ms > 0) {
+    int flag = 0;
+    CUDA_TRY(cudaMemcpy(&flag, counter + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag)
+      return fail(BIPM_ETIMEOUT, "time limit of " + std::to_string(time_limit_ms) +
+                                     " ms reached: unfinished problems report RUNNING (started) or EMPTY "
+                                     "(not started)");
+  }
+  return 0;
+}
+
 int run_iterations(bipm_batch* b, int n_iter) {
   if (!b->loaded) return fail(BIPM_ESTATE, "no problems loaded");
+  int rc = begin_call(b->counter, b->stream);
+  if (rc) return rc;
   // warp teams: every problem (at most kBulkVisit iterations in solve mode
   // when block teams take over the remainder)
   if (b->schedule != 2) {
@@ -204,8 +295,7 @@ int run_iterations(bipm_batch* b, int n_iter) {
                               dim3(kBlockTeam), args2, (size_t)b->smem_per_warp + 128,
                               b->stream));
   }
-  CUDA_TRY(cudaStreamSynchronize(b->stream));
-  return 0;
+  return end_call(b->counter, b->time_limit_ms, b->stream);
 }
 
 }  // namespace
@@ -214,62 +304,6 @@ int run_iterations(bipm_batch* b, int n_iter) {
 extern "C" {
 
 const char* bipm_last_error(void) { return g_err.c_str(); }
-
-// Validated dims of one problem structure (0, or an error code with message).
-static int dims_from_desc(const bipm_problem_desc* desc, Dims* out) {
-  if (desc->n_quads < 1 || desc->n_quads > 8) return fail(BIPM_EINVAL, "n_quads must be 1..8");
-  if (desc->horizon < 1 || desc->horizon > 1000) return fail(BIPM_EINVAL, "horizon must be 1..1000");
-  if (!(desc->dt > 0.0) || !std::isfinite(desc->dt)) return fail(BIPM_EINVAL, "dt must be > 0");
-  if (desc->n_spheres < 0 || desc->n_cylinders < 0 || desc->n_spheres > 256 || desc->n_cylinders > 256)
-    return fail(BIPM_EINVAL, "obstacle counts must be 0..256");
-  if (!(desc->pair_dist >= 0.0)) return fail(BIPM_EINVAL, "pair_dist must be >= 0");
-  Dims d;
-  std::memset(&d, 0, sizeof(d));
-  d.nq = desc->n_quads;
-  d.N = desc->horizon;
-  d.nx = 12 * d.nq;
-  d.nu = 4 * d.nq;
-  d.n_sph = desc->n_spheres;
-  d.n_cyl = desc->n_cylinders;
-  d.n_pairs = desc->pair_dist > 0.0 ? d.nq * (d.nq - 1) / 2 : 0;
-  d.ni = d.nq * d.n_sph + d.nq * d.n_cyl + d.n_pairs;
-  d.n = d.nx * (d.N + 1) + (d.nu + d.ni) * d.N;
-  d.m = d.nx * (d.N + 1) + d.ni * d.N;
-  d.dt = desc->dt;
-  d.pair_d = desc->pair_dist;
-  d.th_x = 0;
-  d.th_ref = 12 * d.nq;
-  d.th_sph = d.th_ref + 6 * d.nq;
-  d.th_cyl = d.th_sph + 4 * d.n_sph;
-  d.n_theta = d.th_cyl + 3 * d.n_cyl;
-  *out = d;
-  return 0;
-}
-
-// Options with defaults filled in, validated; device options in *dev.
-static int options_from(const bipm_options* opt, bipm_options* o_out, Options* dev) {
-  bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0, 0, 0.0, 0.0, 0.0, 0, 0};
-  if (o.fp32_switch == 0.0) o.fp32_switch = kFp32BarrierMax;
-  if (o.warm_mu_init == 0.0) o.warm_mu_init = 1e-2;
-  if (o.warm_bound_push == 0.0) o.warm_bound_push = 1e-3;
-  if (o.warm_max_iter == 0) o.warm_max_iter = 60;
-  if (o.warm_max_iter < 0) return fail(BIPM_EINVAL, "warm_max_iter must be >= 0");
-  if (!(o.warm_mu_init > 0.0) || !(o.warm_bound_push > 0.0) || !(o.warm_bound_push < 0.5))
-    return fail(BIPM_EINVAL, "warm_mu_init must be > 0 and warm_bound_push in (0, 0.5)");
-  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || o.precision < 0 || o.precision > 2 ||
-      o.schedule < 0 || o.schedule > 2)
-    return fail(BIPM_EINVAL, "bad options");
-  dev->tol = o.tol;
-  dev->max_iter = o.max_iter;
-  dev->mu_init = o.mu_init;
-  dev->precision = o.precision;
-  dev->fp32_switch = o.fp32_switch;
-  dev->warm_mu = o.warm_mu_init;
-  dev->warm_push = o.warm_bound_push;
-  dev->warm_max_iter = std::min(o.warm_max_iter, o.max_iter);
-  *o_out = o;
-  return 0;
-}
 
 int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_options* opt,
                       void* cuda_stream, bipm_batch** out) {
@@ -320,7 +354,8 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
   if (cudaMalloc(&b->theta, cap * d.n_theta * sizeof(double) + 8) != cudaSuccess)
     return cleanup(BIPM_ENOMEM, "parameters");
   if (cudaMalloc(&b->st, cap * sizeof(SlotState)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "states");
-  if (cudaMalloc(&b->counter, 2 * sizeof(int)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "counter");
+  if (cudaMalloc(&b->counter, kCounterInts * sizeof(int)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "counter");
+  if (cudaMemset(b->counter, 0, kCounterInts * sizeof(int)) != cudaSuccess) return cleanup(BIPM_ECUDA, "memset");
   if (cudaMalloc(&b->dparams, sizeof(Params)) != cudaSuccess) return cleanup(BIPM_ENOMEM, "params");
   if (cudaMemset(b->f64, 0, cap * b->L.slot_f64 * sizeof(double)) != cudaSuccess)
     return cleanup(BIPM_ECUDA, "memset");
@@ -344,6 +379,8 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
   P.st = b->st;
   P.work_counter = b->counter;
   P.smem_per_warp = b->smem_per_warp;
+  set_budget(P, b->counter, o.time_limit_ms);
+  b->time_limit_ms = o.time_limit_ms;
   if (cudaMemcpy(b->dparams, &P, sizeof(P), cudaMemcpyHostToDevice) != cudaSuccess)
     return cleanup(BIPM_ECUDA, "params copy");
 
@@ -509,7 +546,7 @@ static int solve_queue_impl(bipm_batch* b, const double* theta_queue, const doub
   int warps = std::min(b->capacity, b->blocks * kWarpsPerBlock);
   int blocks = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const bool spares = b->capacity > warps;
-  CUDA_TRY(cudaMemsetAsync(b->counter, 0, 2 * sizeof(int), b->stream));
+  CUDA_TRY(cudaMemsetAsync(b->counter, 0, kCounterInts * sizeof(int), b->stream));
   if (spares) {
     reset_states<<<std::max(1, std::min(1024, (b->capacity + 255) / 256)), 256, 0, b->stream>>>(b->dparams);
     CUDA_TRY(cudaGetLastError());
@@ -531,9 +568,8 @@ static int solve_queue_impl(bipm_batch* b, const double* theta_queue, const doub
     if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, x_dev, xb, cudaMemcpyDeviceToHost, b->stream));
     CUDA_TRY(cudaMemcpyAsync(results, r_dev, rb, cudaMemcpyDeviceToHost, b->stream));
   }
-  CUDA_TRY(cudaStreamSynchronize(b->stream));
   b->loaded = 1;
-  return 0;
+  return end_call(b->counter, b->time_limit_ms, b->stream);
 }
 
 int bipm_solve_queue(bipm_batch* b, const double* theta_queue, int n_queue, double* x_out,
@@ -649,7 +685,7 @@ int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm
   void* tf = mem.take((size_t)n_slots * mfac * fsz);
   double* th_slots = (double*)mem.take((size_t)n_slots * mth * sizeof(double));
   SlotState* st = (SlotState*)mem.take((size_t)n_slots * sizeof(SlotState));
-  int* counter = (int*)mem.take(2 * sizeof(int));
+  int* counter = (int*)mem.take(kCounterInts * sizeof(int));
   Params* dP = (Params*)mem.take((size_t)n_classes * sizeof(Params));
   int* cls_d = (int*)mem.take((size_t)n_queue * sizeof(int));
   long long* off_d = (long long*)mem.take((size_t)2 * n_queue * sizeof(long long));
@@ -687,6 +723,7 @@ int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm
     P.n_spare = n_spare;
     P.visit_cap = n_spare > 0 ? kQueueVisit : 0;
     P.theta_stride = mth;
+    set_budget(P, counter, o.time_limit_ms);
   }
   CUDA_TRY(cudaMemsetAsync(f64, 0, (size_t)n_slots * mf64 * sizeof(double), stream));
   CUDA_TRY(cudaMemcpyAsync(dP, Ps.data(), n_classes * sizeof(Params), cudaMemcpyHostToDevice, stream));
@@ -694,7 +731,7 @@ int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm
   CUDA_TRY(cudaMemcpyAsync(off_d, th_off.data(), n_queue * sizeof(long long), cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaMemcpyAsync(off_d + n_queue, x_off.data(), n_queue * sizeof(long long), cudaMemcpyHostToDevice,
                            stream));
-  CUDA_TRY(cudaMemsetAsync(counter, 0, 2 * sizeof(int), stream));
+  CUDA_TRY(cudaMemsetAsync(counter, 0, kCounterInts * sizeof(int), stream));
   reset_states<<<std::max(1, std::min(1024, (n_slots + 255) / 256)), 256, 0, stream>>>(dP);
   CUDA_TRY(cudaGetLastError());
   const long long* thoff_d = off_d;
@@ -715,8 +752,7 @@ int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm
     if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, x_dev, x_tot * sizeof(double), cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaMemcpyAsync(results, r_dev, n_queue * sizeof(bipm_result), cudaMemcpyDeviceToHost, stream));
   }
-  CUDA_TRY(cudaStreamSynchronize(stream));
-  return 0;
+  return end_call(counter, o.time_limit_ms, stream);
 }
 
 int bipm_step(bipm_batch* b, int n_iterations) {

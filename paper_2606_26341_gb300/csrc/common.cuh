@@ -106,6 +106,9 @@ constexpr int kFilterCap = 64;
 constexpr int kLsMaxTrials = 60;
 constexpr int kIrMaxSteps = 10;
 constexpr double kIrTol = 1e-10;
+// residual ratio an FP64 re-solve after failed refinement must meet; above it
+// the problem ends with BIPM_FP64_ESCALATION_FAILED
+constexpr double kEscTol = 1e-6;
 constexpr int kGmresM = 6;        // Krylov dimension per restart
 constexpr double kFp32BarrierMax = 1e5;  // above: factorise in FP64 this iteration
 constexpr int kGmresRestarts = 3;
@@ -222,7 +225,32 @@ struct Params {
   // doubles between the parameter rows of consecutive slots (0: d.n_theta);
   // a mixed queue sizes every slot for its largest structure class
   long long theta_stride;
+  // time budget of one call (0 = none): *t0 holds the device time (ns) at which
+  // the call's first iteration started (0 until then; the host clears it), and
+  // *timeout_flag is set by every team that stops because the budget ran out
+  unsigned long long time_limit_ns;
+  unsigned long long* t0;
+  int* timeout_flag;
 };
+
+// device clock in nanoseconds
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// True once the call's time budget has run out (evaluated by one thread; the
+// caller broadcasts it to its team).  The first thread to ask starts the clock.
+__device__ __forceinline__ bool budget_spent(const Params* P) {
+  if (P->time_limit_ns == 0) return false;
+  const unsigned long long now = global_ns();
+  unsigned long long t0 = atomicCAS(P->t0, 0ull, now);
+  if (t0 == 0ull) t0 = now;
+  if (now - t0 < P->time_limit_ns) return false;
+  atomicExch(P->timeout_flag, 1);
+  return true;
+}
 
 __host__ __device__ __forceinline__ long long theta_stride(const Params* P) {
   return P->theta_stride ? P->theta_stride : (long long)P->d.n_theta;

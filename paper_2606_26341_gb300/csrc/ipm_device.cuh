@@ -69,6 +69,7 @@ struct Ctx {
   double dw;           // regularisation used in the last factorisation
   int use64;           // 1: the last factorisation is the FP64 one
   int n_ir, n_esc;
+  int esc_failed;      // the FP64 solve after a failed refinement missed its accuracy test
   int n_fact, n_solve, n_trial;  // work counters of the current iteration
   int n_fact32, n_solve32;        // ... of which in FP32
 };

@@ -359,6 +359,12 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF>& c, const double* r, doub
   if (factor<TB, TF, double>(c, c.fac64, c.dw, flags, y) == 0) return false;
   c.use64 = 1;
   solve<TB, TF, double>(c, c.fac64, r, out, flags, y);
+  // the FP64 step must solve the system it was given to kEscTol
+  kkt_matvec(c, out, res, c.dw, y);
+  for (int i = lane; i < len; i += c.T) res[at(i)] = -r[at(i)] - res[at(i)];
+  team_sync(c);
+  const double ratio = norm_inf(res) / (fmin(norm_inf(out), 1e6 * rnorm) + rnorm);
+  if (!(ratio <= kEscTol)) c.esc_failed = 1;
   return true;
 }
 
@@ -622,8 +628,21 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
     }
     c.dw = dwc;
     lap(PH_FACTOR);
+    c.esc_failed = 0;
     bool solved = solve_refined(c, rhs, sol);
     lap(PH_SOLVE);
+    if (solved && c.esc_failed) {
+      // no accurate Newton step even in FP64: the problem stops here
+      S.n_ir_steps += c.n_ir;
+      S.n_escalations += c.n_esc;
+      S.n_fact += c.n_fact;
+      S.n_solve += c.n_solve;
+      S.n_fact32 += c.n_fact32;
+      S.n_solve32 += c.n_solve32;
+      S.cyc[PH_TOTAL] += clock64() - t_start;
+      S.status = BIPM_FP64_ESCALATION_FAILED;
+      return;
+    }
     if (solved) break;
     // FP64 refactorisation after failed refinement reported wrong inertia:
     // redo the correction in FP64
@@ -730,7 +749,8 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
               S.n_soc++;
               LANE_LOOP(i, m) rhs2[nwk + i] = csoc[i];
               team_sync(c);
-              if (!solve_refined(c, rhs2, sol2)) break;
+              c.esc_failed = 0;
+              if (!solve_refined(c, rhs2, sol2) || c.esc_failed) break;  // no usable correction
               double a_soc = ftb_primal(c, w, sol2, tau);
               TrialVal<TB, TF> sv = trial_point(c, a_soc, sol2);
               if (!sv.finite) break;

@@ -44,6 +44,7 @@ __device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, in
   c.use64 = 0;
   c.n_ir = 0;
   c.n_esc = 0;
+  c.esc_failed = 0;
   c.n_fact = 0;
   c.n_solve = 0;
   c.n_trial = 0;
@@ -68,20 +69,37 @@ __device__ void slot_metrics(Ctx<TB, TF>& c, SlotState& S) {
   S.inf = e.prim;
 }
 
+// true (in every thread of the team) once the call's time budget has run out
+template <class TB, class TF>
+__device__ __forceinline__ bool team_budget_spent(Ctx<TB, TF>& c) {
+  if (c.P->time_limit_ns == 0) return false;
+  int v = 0;
+  if (c.lane == 0) v = budget_spent(c.P) ? 1 : 0;
+  return team_bcast0(c, v) != 0;
+}
+
 // Iterates one slot: exactly n_iter iterations (n_iter > 0), or until it
 // terminates, or (visit_cap > 0) for at most visit_cap iterations in this visit.
+// Before every iteration the call's time budget is checked; returns true if the
+// slot stopped because it ran out (the problem is left running, resumable).
 template <class TB, class TF>
-__device__ void run_slot(Ctx<TB, TF>& c, SlotState& S, int n_iter, int visit_cap) {
+__device__ bool run_slot(Ctx<TB, TF>& c, SlotState& S, int n_iter, int visit_cap) {
   int done = 0;
+  bool spent = false;
   if (n_iter > 0) {
-    for (; done < n_iter && S.status == BIPM_RUNNING; ++done) iterate(c, S);
+    for (; done < n_iter && S.status == BIPM_RUNNING; ++done) {
+      if ((spent = team_budget_spent(c))) break;
+      iterate(c, S);
+    }
   } else {
     while (S.status == BIPM_RUNNING && (visit_cap <= 0 || done < visit_cap)) {
+      if ((spent = team_budget_spent(c))) break;
       iterate(c, S);
       ++done;
     }
   }
   if (n_iter > 0 || S.status != BIPM_RUNNING) slot_metrics(c, S);
+  return spent;
 }
 
 // Persistent kernel, one warp per problem: each warp takes the next slot from
@@ -256,6 +274,22 @@ __device__ __forceinline__ bipm_result make_result(const SlotState& S, int warm,
   return r;
 }
 
+// record of a queue problem that was never started (the time budget ran out)
+__device__ __forceinline__ bipm_result empty_result() {
+  bipm_result r;
+  memset(&r, 0, sizeof(r));
+  r.status = BIPM_EMPTY;
+  return r;
+}
+
+// warp-uniform time-budget test of a queue warp before it starts a problem
+__device__ __forceinline__ bool queue_budget_spent(const Params* P, int lane) {
+  if (P->time_limit_ns == 0) return false;
+  int v = 0;
+  if (lane == 0) v = budget_spent(P) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, v, 0) != 0;
+}
+
 template <class TB, class TF>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     queue_kernel(const Params* __restrict__ P, const double* __restrict__ theta_q, int n_queue,
@@ -273,6 +307,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     if (lane == 0) id = atomicAdd(P->work_counter, 1);
     id = __shfl_sync(0xffffffffu, id, 0);
     if (id >= n_queue) break;
+    if (queue_budget_spent(P, lane)) {  // out of time: the problem is not started
+      if (lane == 0) res_out[id] = empty_result();
+      continue;
+    }
     double* th = P->theta + (long long)slot * theta_stride(P);
     for (int i = lane; i < d.n_theta; i += 32) th[i] = theta_q[(long long)id * d.n_theta + i];
     __syncwarp();
@@ -282,12 +320,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     Ctx<TB, TF> c;
     make_ctx(c, P, slot, lane, 32, nullptr, smem);
     int warm = gq ? 1 : 0, warm_iters = 0;
-    bool done = false;
+    bool done = false, spent = false;
     if (gq) {
-      run_slot(c, S, 0, P->opt.warm_max_iter);
+      spent = run_slot(c, S, 0, P->opt.warm_max_iter);
       if (S.status == BIPM_CONVERGED) {
         done = true;
-      } else {
+      } else if (!spent) {
         warm = 2;
         warm_iters = S.iter;
         S = init_slot(P, slot, lane, nullptr, nullptr, 0);
@@ -295,9 +333,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
         make_ctx(c, P, slot, lane, 32, nullptr, smem);
       }
     }
-    if (!done) {
-      run_slot(c, S, 0, P->visit_cap);
-      if (S.status == BIPM_RUNNING) {
+    if (!done && !spent) {
+      spent = run_slot(c, S, 0, P->visit_cap);
+      if (S.status == BIPM_RUNNING && !spent) {
         // straggler: park it for the block teams when a spare slot is free
         int ns = 0;
         if (lane == 0) ns = atomicAdd(P->spare_counter, 1);
@@ -316,6 +354,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
         run_slot(c, S, 0, 0);
       }
     }
+    // a problem stopped by the time budget is written out with status RUNNING
     const double* w = c.f + P->L.x;
     if (x_out)
       for (int i = lane; i < d.n; i += 32) x_out[(long long)id * d.n + i] = w[i];
@@ -353,6 +392,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     if (lane == 0) id = atomicAdd(P0->work_counter, 1);
     id = __shfl_sync(0xffffffffu, id, 0);
     if (id >= n_queue) break;
+    if (queue_budget_spent(P0, lane)) {
+      if (lane == 0) res_out[id] = empty_result();
+      continue;
+    }
     const int k = cls[id];
     const Params* P = Pc + k;
     const Dims& d = P->d;
@@ -364,8 +407,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     S.cls = k;
     Ctx<TB, TF> c;
     make_ctx(c, P, slot, lane, 32, nullptr, smem);
-    run_slot(c, S, 0, P->visit_cap);
-    if (S.status == BIPM_RUNNING) {
+    const bool spent = run_slot(c, S, 0, P->visit_cap);
+    if (S.status == BIPM_RUNNING && !spent) {
       int ns = 0;
       if (lane == 0) ns = atomicAdd(P0->spare_counter, 1);
       ns = __shfl_sync(0xffffffffu, ns, 0);

@@ -1,13 +1,14 @@
 // bipm_solve_static: a one-shot batched solve that allocates no memory.
 //
 // Some callers cannot allocate device memory at the time they need a solve:
-// code running inside a CUDA stream capture (where cudaMalloc is not allowed),
-// real-time control loops that must not enter the allocator, and hosts whose
-// memory budget is fixed up front.  This entry point serves them: its whole
-// workspace (slot vectors, derivative blocks, factors, parameters, states and
-// the launch record) lives in one file-scope __device__ array of fixed size,
-// reserved when the library is loaded and held by every GPU that loads it
-// until the process exits.  The caller passes device inputs and outputs only.
+// real-time control loops that must stay out of the CUDA allocator (cudaMalloc
+// can block, synchronise the device or fail under fragmentation), and
+// processes whose device memory is budgeted at start-up and may not grow.
+// This entry point serves them: its whole workspace (slot vectors, derivative
+// blocks, factors, parameters, states, counters and the launch record) lives
+// in one file-scope __device__ array of fixed size, reserved when the library
+// is loaded and held by every GPU that loads it until the process exits.  The
+// caller passes device inputs and outputs only.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,13 +18,10 @@
 #include <string>
 
 #include "../../include/bipm.h"
+#include "host_api.h"
 #include "kernels.cuh"
 
 using namespace bipm;
-
-namespace bipm {
-void set_last_error(const std::string& msg);  // defined with the other entry points
-}
 
 namespace {
 
@@ -71,44 +69,21 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
                       int count, double* x_out, bipm_result* results, void* cuda_stream) {
   if (!desc || !theta || !results) return sfail(BIPM_EINVAL, "null desc, theta or results");
   if (count < 0) return sfail(BIPM_EINVAL, "count must be >= 0");
-  if (desc->n_quads < 1 || desc->n_quads > 8) return sfail(BIPM_EINVAL, "n_quads must be 1..8");
-  if (desc->horizon < 1 || desc->horizon > 1000) return sfail(BIPM_EINVAL, "horizon must be 1..1000");
-  if (!(desc->dt > 0.0) || !std::isfinite(desc->dt)) return sfail(BIPM_EINVAL, "dt must be > 0");
-  if (desc->n_spheres < 0 || desc->n_cylinders < 0 || desc->n_spheres > 256 || desc->n_cylinders > 256)
-    return sfail(BIPM_EINVAL, "obstacle counts must be 0..256");
-  if (!(desc->pair_dist >= 0.0)) return sfail(BIPM_EINVAL, "pair_dist must be >= 0");
-  bipm_options o = opt ? *opt : bipm_options{1e-6, 500, 0.1, 0, 0, 0.0};
-  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.mu_init > 0.0) || o.precision < 0 || o.precision > 2)
-    return sfail(BIPM_EINVAL, "bad options");
-  if (o.fp32_switch == 0.0) o.fp32_switch = kFp32BarrierMax;
+  Dims d;
+  int rc = dims_from_desc(desc, &d);  // the same validation as bipm_create_batch
+  if (rc) return rc;
+  bipm_options o;
+  Options dopt;
+  if ((rc = options_from(opt, &o, &dopt))) return rc;
   if (count == 0) return 0;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
 
-  Dims d;
-  std::memset(&d, 0, sizeof(d));
-  d.nq = desc->n_quads;
-  d.N = desc->horizon;
-  d.nx = 12 * d.nq;
-  d.nu = 4 * d.nq;
-  d.n_sph = desc->n_spheres;
-  d.n_cyl = desc->n_cylinders;
-  d.n_pairs = desc->pair_dist > 0.0 ? d.nq * (d.nq - 1) / 2 : 0;
-  d.ni = d.nq * d.n_sph + d.nq * d.n_cyl + d.n_pairs;
-  d.n = d.nx * (d.N + 1) + (d.nu + d.ni) * d.N;
-  d.m = d.nx * (d.N + 1) + d.ni * d.N;
-  d.dt = desc->dt;
-  d.pair_d = desc->pair_dist;
-  d.th_x = 0;
-  d.th_ref = 12 * d.nq;
-  d.th_sph = d.th_ref + 6 * d.nq;
-  d.th_cyl = d.th_sph + 4 * d.n_sph;
-  d.n_theta = d.th_cyl + 3 * d.n_cyl;
   const Layout L = make_layout(d, o.precision);
   const size_t tsz = o.precision ? sizeof(float) : sizeof(double);
   const size_t fsz = o.precision == 1 ? sizeof(float) : sizeof(double);
 
-  // carve the static array: launch record and counter, then per-slot regions
-  const size_t hdr = align256(sizeof(Params)) + 256;
+  // carve the static array: launch record and counters, then per-slot regions
+  const size_t hdr = align256(sizeof(Params)) + align256(kCounterInts * sizeof(int));
   const size_t per_slot = align256(L.slot_f64 * sizeof(double)) + align256(L.slot_tb * tsz) +
                           align256(L.fac_size * fsz) + align256(d.n_theta * sizeof(double)) +
                           align256(sizeof(SlotState));
@@ -119,8 +94,7 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
   int fit = (int)((kStaticBytes - hdr) / per_slot);
 
   unsigned char* base = nullptr;
-  int rc = workspace_ptr(&base);
-  if (rc) return rc;
+  if ((rc = workspace_ptr(&base))) return rc;
 
   // one slot per resident warp, at most one per problem and per what fits
   void* kfn = o.precision == 2 ? queue_kernel_df() : o.precision ? queue_kernel_f32() : queue_kernel_f64();
@@ -149,11 +123,7 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
   std::memset(&P, 0, sizeof(P));
   P.d = d;
   P.L = L;
-  P.opt.tol = o.tol;
-  P.opt.max_iter = o.max_iter;
-  P.opt.mu_init = o.mu_init;
-  P.opt.precision = o.precision;
-  P.opt.fp32_switch = o.fp32_switch;
+  P.opt = dopt;
   P.n_slots = slots;
   P.f64 = (double*)p;
   p += align256(L.slot_f64 * sizeof(double)) * slots;
@@ -164,12 +134,19 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
   P.theta = (double*)p;
   p += align256(d.n_theta * sizeof(double)) * slots;
   P.st = (SlotState*)p;
-  P.work_counter = (int*)(base + align256(sizeof(Params)));
+  int* counter = (int*)(base + align256(sizeof(Params)));
+  P.work_counter = counter;
   P.smem_per_warp = smem_per_warp;
+  // one slot per warp and no spare slots: a problem is never parked, so the
+  // spare counter is never touched and the visit is unlimited
+  P.spare_counter = counter + 1;
+  P.n_spare = 0;
+  P.visit_cap = 0;
+  set_budget(P, counter, o.time_limit_ms);
   // every call shares the array and finds the previous call's contents in it:
-  // the queue counter must start at zero; slots are fully reset per problem
+  // the counters must start at zero; slots are fully reset per problem
   if (cudaMemcpyAsync(base, &P, sizeof(P), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemsetAsync(P.work_counter, 0, sizeof(int), stream) != cudaSuccess)
+      cudaMemsetAsync(counter, 0, kCounterInts * sizeof(int), stream) != cudaSuccess)
     return sfail(BIPM_ECUDA, "launch record copy");
   const Params* dP = (const Params*)base;
   int n_queue = count;
@@ -181,6 +158,14 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
   if (e != cudaSuccess) return sfail(BIPM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return sfail(BIPM_ECUDA, std::string("solve: ") + cudaGetErrorString(e));
+  if (o.time_limit_ms > 0) {
+    int flag = 0;
+    e = cudaMemcpy(&flag, counter + 2, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return sfail(BIPM_ECUDA, std::string("flag read: ") + cudaGetErrorString(e));
+    if (flag)
+      return sfail(BIPM_ETIMEOUT, "time limit of " + std::to_string(o.time_limit_ms) +
+                                      " ms reached: unfinished problems report RUNNING or EMPTY");
+  }
   return 0;
 }
 

@@ -83,3 +83,29 @@ def test_invalid_arguments_fail_without_a_device(lib):
     assert lib.bipm_create_batch(ctypes.byref(d), 4, None, None, ctypes.byref(h)) == -22
     assert lib.bipm_solve(None) == -22
     assert lib.bipm_step(None, 1) == -22
+
+
+def test_header_codes_match_the_binding():
+    """Error codes and per-problem statuses of include/bipm.h equal the binding's."""
+    text = open(HEADER).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define (BIPM_[A-Z0-9_]+) \(?(-?\d+)\)?", text)}
+    assert defs["BIPM_EINVAL"] == bipm.EINVAL and defs["BIPM_ENOMEM"] == bipm.ENOMEM
+    assert defs["BIPM_ECUDA"] == bipm.ECUDA and defs["BIPM_ESTATE"] == bipm.ESTATE
+    assert defs["BIPM_ETIMEOUT"] == bipm.ETIMEOUT
+    for name in ("RUNNING", "CONVERGED", "MAX_ITER", "RESTO_FAILED", "EVAL_ERROR", "TINY_STEP", "EMPTY",
+                 "FP64_ESCALATION_FAILED"):
+        assert defs["BIPM_" + name] == getattr(bipm, name), name
+    assert set(bipm.STATUS_NAMES) == set(range(8))
+
+
+def test_every_declaration_states_its_errors_or_source():
+    """Each exported call's comment names where it comes from (a passage of the
+    paper, or that the paper has no counterpart) or documents its errors."""
+    text = open(HEADER).read()
+    for name in declared_functions():
+        i = re.search(r"^[a-z].*\b" + name + r"\(", text, flags=re.M).start()
+        start = text.rfind("*/", 0, i)
+        begin = text.rfind("/*", 0, start)
+        comment = re.sub(r"\s*\n\s*\*\s*", " ", text[begin:start])
+        assert ("Sec." in comment or "Eq." in comment or "Table" in comment or "no counterpart" in comment
+                or "Errors" in comment or "as for" in comment), name

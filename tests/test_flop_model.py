@@ -7,14 +7,14 @@ import tempfile
 
 import bench
 
-CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                    "paper_2606_26341_gb300", "csrc")
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2606_26341_gb300", "csrc")
 
 
 def test_model_operation_counts_match_device_templates():
     with tempfile.TemporaryDirectory() as d:
         exe = os.path.join(d, "opcount")
-        subprocess.run(["g++", "-O1", "-std=c++17", "-I", CSRC, os.path.join(CSRC, "opcount.cpp"),
+        subprocess.run(["g++", "-O1", "-std=c++17", "-I", CSRC, os.path.join(HERE, "opcount.cpp"),
                         "-o", exe], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
     counts = {}
