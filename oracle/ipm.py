@@ -77,6 +77,7 @@ class Options:
     filter_cap: int = 64
     ls_max_trials: int = 60
     trace_cond: bool = False  # record the 2-norm condition number of each step's matrix
+    trace_soc: bool = False   # record the linear systems of the second-order corrections
 
 
 @dataclasses.dataclass
@@ -188,6 +189,140 @@ def frac_to_boundary(v, dv, tau):
     return float(min(1.0, np.min(-tau * v[neg] / dv[neg])))
 
 
+def is_tiny_step(x, dx):
+    """Tiny-step test (Table I row 4): max_i |dx_i| / (1 + |x_i|) < 10 eps_mach."""
+    return bool(np.max(np.abs(dx) / (1.0 + np.abs(x))) < 10.0 * EPS_MACH)
+
+
+# ----------------------------------------------------- line-search rules --
+# The acceptance rules of the backtracking filter line search (Table I row 1;
+# IPOPT's Algorithm A with its Eqs. for the switching condition, the Armijo
+# and sufficient-decrease tests and the minimal step size).  theta is the
+# constraint violation and phi the barrier objective at the current iterate,
+# gdx = grad phi^T dx the directional derivative along the primal step.
+
+def alpha_min(theta, gdx, theta_min, opt):
+    """Smallest trial step before the line search gives up (IPOPT's Eq. 23, three cases)."""
+    if gdx < 0 and theta <= theta_min:
+        return opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta / (-gdx),
+                                     opt.delta * theta ** opt.s_theta / (-gdx) ** opt.s_phi)
+    if gdx < 0:
+        return opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta / (-gdx))
+    return opt.gamma_alpha * opt.gamma_theta
+
+
+def switching_condition(alpha, gdx, theta, opt):
+    """gdx < 0 and alpha (-gdx)^s_phi > delta theta^s_theta."""
+    return gdx < 0 and alpha * (-gdx) ** opt.s_phi > opt.delta * theta ** opt.s_theta
+
+
+def armijo_holds(phi_t, phi0, alpha, gdx, opt):
+    """Armijo condition on the barrier objective: phi(x_a) <= phi + eta_phi alpha gdx."""
+    return phi_t <= phi0 + opt.eta_phi * alpha * gdx
+
+
+def sufficient_decrease(theta_t, phi_t, theta, phi0, opt):
+    """Sufficient reduction of theta or phi with respect to the current iterate."""
+    return theta_t <= (1.0 - opt.gamma_theta) * theta or phi_t <= phi0 - opt.gamma_phi * theta
+
+
+def trial_acceptable(ph, theta_t, phi_t, alpha, theta, phi0, gdx, opt):
+    """A trial point is accepted if it is not in the filter and, when the switching
+    condition holds at a nearly feasible iterate (theta <= theta_min), satisfies the
+    Armijo condition, otherwise the sufficient-decrease test."""
+    if not np.isfinite(phi_t) or in_filter(ph, theta_t, phi_t):
+        return False
+    if switching_condition(alpha, gdx, theta, opt) and theta <= ph.theta_min:
+        return armijo_holds(phi_t, phi0, alpha, gdx, opt)
+    return sufficient_decrease(theta_t, phi_t, theta, phi0, opt)
+
+
+def filter_needs_augment(alpha, phi_t, phi0, gdx, theta, opt):
+    """The filter is augmented after an accepted step unless the switching condition
+    and the Armijo condition both hold."""
+    return not (switching_condition(alpha, gdx, theta, opt) and armijo_holds(phi_t, phi0, alpha, gdx, opt))
+
+
+def filter_entry(theta, phi, opt):
+    """The pair stored in the filter for an iterate with (theta, phi)."""
+    return (1.0 - opt.gamma_theta) * theta, phi - opt.gamma_phi * theta
+
+
+def soc_constraint_rhs(alpha_prev, c_soc_prev, c_trial):
+    """Right-hand side of the next second-order correction (Table I row 2):
+    c_soc <- alpha c_soc + c(x_soc); the first one is alpha c(x) + c(x_alpha)."""
+    return alpha_prev * c_soc_prev + c_trial
+
+
+def soc_should_stop(p, theta_soc, theta_old, opt):
+    """Stop correcting after p_max corrections or when theta no longer shrinks by kappa_soc."""
+    return p >= opt.p_max or theta_soc > opt.kappa_soc * theta_old
+
+
+# ------------------------------------------------------ barrier update --
+
+def barrier_update(mu, err_at, tiny, opt):
+    """Monotone barrier update (Table I row 7, monotone schedule).
+
+    While the barrier problem at mu is solved to E_mu <= kappa_eps mu (err_at(mu)
+    is E_mu), or once after a tiny step, mu <- max(tol/10, min(kappa_mu mu,
+    mu^theta_mu)) and the filter is reset.  Returns (mu, decreased, stalled):
+    stalled means a tiny step happened at the floor value of mu."""
+    mu_floor = opt.tol / 10.0
+    first = True
+    decreased = False
+    while True:
+        if (err_at(mu) <= opt.kappa_eps * mu) or (first and tiny):
+            if mu <= mu_floor:
+                return mu, decreased, bool(first and tiny)
+            mu = max(mu_floor, min(opt.kappa_mu * mu, mu ** opt.theta_mu))
+            decreased = True
+            first = False
+            tiny = False
+            continue
+        return mu, decreased, False
+
+
+# ------------------------------------------------- inertia correction --
+
+def inertia_correction(factor_ok, dw_last, opt):
+    """IPOPT's Algorithm IC with delta_w only: the smallest delta_w of its sequence
+    for which factor_ok(delta_w) holds.  Returns (delta_w, n_retries) or
+    (None, n_retries) when delta_w would exceed delta_w_max."""
+    if factor_ok(0.0):
+        return 0.0, 0
+    dw = opt.dw_init if dw_last == 0.0 else max(opt.dw_min, opt.kappa_w_minus * dw_last)
+    n = 0
+    while True:
+        n += 1
+        if factor_ok(dw):
+            return dw, n
+        dw *= opt.kappa_w_plus_bar if dw_last == 0.0 else opt.kappa_w_plus
+        if dw > opt.dw_max:
+            return None, n
+
+
+# ------------------------------------------------ restoration entry --
+
+def resto_elastics(c, mu_r, rho):
+    """Closed-form start of the restoration elastics p, n for c(x) - p + n = 0: the
+    minimiser of rho (p + n) - mu_R (ln p + ln n) on p - n = c (IPOPT Sec. 3.3)."""
+    a = (mu_r - rho * c) / (2.0 * rho)
+    nn = a + np.sqrt(a * a + mu_r * c / (2.0 * rho))
+    return c + nn, nn
+
+
+def resto_scaling(x_ref):
+    """D_R = diag(min(1, 1/|x_R|)) of the restoration objective's proximity term."""
+    return np.minimum(1.0, 1.0 / np.maximum(np.abs(x_ref), 1e-300))
+
+
+def resto_may_return(ph_orig, theta, phi, theta_ref, opt):
+    """Restoration ends when the original constraint violation fell to
+    kappa_resto theta(x_R) and the point is acceptable to the original filter."""
+    return bool(np.isfinite(phi) and theta <= opt.kappa_resto * theta_ref and not in_filter(ph_orig, theta, phi))
+
+
 # ------------------------------------------------------------ linear algebra --
 
 class KKTFactor:
@@ -252,7 +387,7 @@ class RestoNLP:
         self.nx0 = nx
         self.n = nx + 2 * m
         self.m = m
-        self.dr = np.minimum(1.0, 1.0 / np.maximum(np.abs(x_ref), 1e-300))
+        self.dr = resto_scaling(x_ref)
         self.xl = np.concatenate([nlp.xl, np.zeros(2 * m)])
         self.xu = np.concatenate([nlp.xu, np.full(2 * m, np.inf)])
 
@@ -389,21 +524,14 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
         return _Outcome.CONVERGED
 
     # monotone barrier update (Table I row 7), repeated while the subproblem is solved
-    mu_floor = opt.tol / 10.0
-    first = True
-    while True:
-        e_mu = opt_error(nlp, x, y, zl, zu, g, J, c, ph.mu, opt)
-        if (e_mu <= opt.kappa_eps * ph.mu) or (first and ph.tiny):
-            if ph.mu <= mu_floor:
-                if first and ph.tiny:
-                    return _Outcome.TINY_STALL
-                break
-            ph.mu = max(mu_floor, min(opt.kappa_mu * ph.mu, ph.mu ** opt.theta_mu))
-            ph.filt = []
-            first = False
-            ph.tiny = False
-            continue
-        break
+    mu_new, decreased, stalled = barrier_update(
+        ph.mu, lambda mu: opt_error(nlp, x, y, zl, zu, g, J, c, mu, opt), ph.tiny, opt)
+    if stalled:
+        return _Outcome.TINY_STALL
+    if decreased:
+        ph.mu = mu_new
+        ph.filt = []
+        ph.tiny = False
     mu = ph.mu
     tau = max(opt.tau_min, 1.0 - mu)
 
@@ -418,25 +546,22 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
     rhs = -np.concatenate([gphi + J.T @ y, c])
 
     # inertia correction (IPOPT Algorithm IC); delta_c is never used
-    def factor(dw):
-        fac = KKTFactor(augmented_matrix(Wsig, J, dw))
-        ok = (fac.n_pos == nlp.n and fac.n_neg == nlp.m and fac.n_zero == 0)
-        return fac, ok
+    facs = {}
 
-    fac, ok = factor(0.0)
-    dw = 0.0
-    if not ok:
-        dw = opt.dw_init if ph.dw_last == 0.0 else max(opt.dw_min, opt.kappa_w_minus * ph.dw_last)
-        while True:
-            trace["n_inertia_corr"] = trace.get("n_inertia_corr", 0) + 1
-            fac, ok = factor(dw)
-            if ok:
-                break
-            dw *= opt.kappa_w_plus_bar if ph.dw_last == 0.0 else opt.kappa_w_plus
-            if dw > opt.dw_max:
-                trace["ic_failed"] = True
-                return _Outcome.LS_FAILED
+    def factor_ok(dw_try):
+        fac_try = KKTFactor(augmented_matrix(Wsig, J, dw_try))
+        facs[dw_try] = fac_try
+        return fac_try.n_pos == nlp.n and fac_try.n_neg == nlp.m and fac_try.n_zero == 0
+
+    dw, n_retry = inertia_correction(factor_ok, ph.dw_last, opt)
+    if n_retry:
+        trace["n_inertia_corr"] = trace.get("n_inertia_corr", 0) + n_retry
+    if dw is None:
+        trace["ic_failed"] = True
+        return _Outcome.LS_FAILED
+    if n_retry:
         ph.dw_last = dw
+    fac = facs[dw]
     trace["delta_w"] = dw
     if opt.trace_cond:
         trace["cond"] = float(np.linalg.cond(fac.K))
@@ -472,13 +597,13 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
         zu_new = zu + az * dzu_
         zl_new, zu_new = kappa_sigma_reset(nlp, x_new, zl_new, zu_new, mu, opt)
         if augment:
-            filter_add(ph, (1.0 - opt.gamma_theta) * theta0, phi0 - opt.gamma_phi * theta0, opt)
+            filter_add(ph, *filter_entry(theta0, phi0, opt), opt)
         ph.x, ph.y, ph.zl, ph.zu = x_new, y_new, zl_new, zu_new
         trace["alpha"] = alpha
         trace["alpha_z"] = az
 
     # tiny step (Table I row 4)
-    if np.max(np.abs(dx) / (1.0 + np.abs(x))) < 10.0 * EPS_MACH:
+    if is_tiny_step(x, dx):
         trace["tiny"] = True
         accept(a_max, dx, dy, dzl, dzu, False, 0.0, 0.0)
         ph.tiny = True
@@ -488,16 +613,7 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
     # backtracking filter line search (Table I row 1) with SOC (row 2)
     phi0 = barrier_phi(nlp, x, f, mu, opt)
     gdx = float(gphi @ dx)
-    if gdx < 0 and theta <= ph.theta_min:
-        a_min = opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta / (-gdx),
-                                      opt.delta * theta ** opt.s_theta / (-gdx) ** opt.s_phi)
-    elif gdx < 0:
-        a_min = opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta / (-gdx))
-    else:
-        a_min = opt.gamma_alpha * opt.gamma_theta
-
-    def switching(alpha):
-        return gdx < 0 and alpha * (-gdx) ** opt.s_phi > opt.delta * theta ** opt.s_theta
+    a_min = alpha_min(theta, gdx, ph.theta_min, opt)
 
     def trial_values(xt):
         ft = nlp.f(xt)
@@ -507,16 +623,10 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
         return theta_of(ct), barrier_phi(nlp, xt, ft, mu, opt), ct
 
     def acceptable(theta_t, phi_t, alpha):
-        """Filter test (A.5.3) and sufficient decrease (A.5.4); returns (ok, f_type)."""
-        if not np.isfinite(phi_t) or in_filter(ph, theta_t, phi_t):
-            return False, False
-        if switching(alpha) and theta <= ph.theta_min:
-            return phi_t <= phi0 + opt.eta_phi * alpha * gdx, True
-        ok = theta_t <= (1.0 - opt.gamma_theta) * theta or phi_t <= phi0 - opt.gamma_phi * theta
-        return ok, False
+        return trial_acceptable(ph, theta_t, phi_t, alpha, theta, phi0, gdx, opt)
 
     def needs_augment(alpha, phi_t):
-        return not (switching(alpha) and phi_t <= phi0 + opt.eta_phi * alpha * gdx)
+        return filter_needs_augment(alpha, phi_t, phi0, gdx, theta, opt)
 
     alpha = a_max
     n_trial = 0
@@ -526,35 +636,37 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
         tv = trial_values(xt)
         if tv is not None:
             theta_t, phi_t, c_t = tv
-            ok, _ = acceptable(theta_t, phi_t, alpha)
-            if ok:
+            if acceptable(theta_t, phi_t, alpha):
                 accept(alpha, dx, dy, dzl, dzu, needs_augment(alpha, phi_t), theta, phi0)
                 trace["ls_trials"] = n_trial
                 return _Outcome.ACCEPTED
             # second-order correction on the first trial when theta did not decrease
             if n_trial == 1 and not (theta_t < theta):
-                c_soc = alpha * c + c_t
+                c_soc = soc_constraint_rhs(alpha, c, c_t)
                 theta_old = theta
                 for p in range(1, opt.p_max + 1):
                     trace["n_soc"] = trace.get("n_soc", 0) + 1
                     dx_s, dy_s = solve(-np.concatenate([gphi + J.T @ y, c_soc]))
+                    if opt.trace_soc:
+                        trace.setdefault("soc_log", []).append(
+                            {"alpha": alpha, "c": c.copy(), "c_trial": c_t.copy(), "c_soc": c_soc.copy(),
+                             "dx": dx.copy(), "dx_soc": dx_s.copy(), "J": J.copy()})
                     a_soc = alpha_primal_max(dx_s)
                     xs = x + a_soc * dx_s
                     sv = trial_values(xs)
                     if sv is None:
                         break
                     theta_s, phi_s, c_s = sv
-                    ok, _ = acceptable(theta_s, phi_s, alpha)
-                    if ok:
+                    if acceptable(theta_s, phi_s, alpha):
                         dzl_s, dzu_s = z_step(dx_s)
                         accept(a_soc, dx_s, dy_s, dzl_s, dzu_s, needs_augment(alpha, phi_s),
                                theta, phi0)
                         trace["soc_accepted"] = True
                         trace["ls_trials"] = n_trial
                         return _Outcome.ACCEPTED
-                    if p == opt.p_max or theta_s > opt.kappa_soc * theta_old:
+                    if soc_should_stop(p, theta_s, theta_old, opt):
                         break
-                    c_soc = a_soc * c_soc + c_s
+                    c_soc = soc_constraint_rhs(a_soc, c_soc, c_s)
                     theta_old = theta_s
         alpha *= 0.5
         if alpha < a_min or n_trial >= opt.ls_max_trials:
@@ -570,14 +682,12 @@ def resto_start(nlp, st: SolverState, opt: Options):
     f = nlp.f(x)
     theta = theta_of(c)
     phi = barrier_phi(nlp, x, f, ph.mu, opt)
-    filter_add(ph, (1.0 - opt.gamma_theta) * theta, phi - opt.gamma_phi * theta, opt)
+    filter_add(ph, *filter_entry(theta, phi, opt), opt)
     zeta = math.sqrt(ph.mu)
     rnlp = RestoNLP(nlp, x, zeta, opt.rho)
     mu_r = max(ph.mu, float(np.max(np.abs(c))) if c.size else 0.0)
     rho = opt.rho
-    a = (mu_r - rho * c) / (2.0 * rho)
-    nn = a + np.sqrt(a * a + mu_r * c / (2.0 * rho))
-    pp = c + nn
+    pp, nn = resto_elastics(c, mu_r, rho)
     w = np.concatenate([x, pp, nn])
     has_l, has_u = bound_sets(nlp)
     zl = np.concatenate([np.where(has_l, np.minimum(rho, ph.zl), 0.0), mu_r / pp, mu_r / nn])
@@ -666,7 +776,7 @@ def step(nlp, st: SolverState, opt: Options) -> dict:
     ph = st.normal
     phi = barrier_phi(nlp, x, f, ph.mu, opt)
     th_ref = theta_of(nlp.c(st.x_ref))
-    if np.isfinite(phi) and th <= opt.kappa_resto * th_ref and not in_filter(ph, th, phi):
+    if resto_may_return(ph, th, phi, th_ref, opt):
         zl, zu = kappa_sigma_reset(nlp, x, rph.zl[:nlp.n], rph.zu[:nlp.n], ph.mu, opt)
         ph.x, ph.zl, ph.zu = x.copy(), zl, zu
         ph.y = rph.y.copy()
