@@ -1,11 +1,16 @@
 """Benchmark: converged NLP solves/sec at KKT tolerance 1e-6 on one GB300.
 
 Workload (default): reference tracking with three random spherical obstacles,
-one quadrotor, RK4 horizon N = 30, batch of 4096 problems ("track").  One
-step = one full batched solve (every problem iterated to termination by the
-fused iteration kernel).  The headline `value` is the chosen form: FP32
-factorisation with FP64 iterative refinement; the plain FP64 form is reported
-beside it (`fp64`).
+one quadrotor, RK4 horizon N = 30, 4096 problems per step ("track").  The K
+steps' problems stream through the slots of one persistent queue launch
+(iteration-level batching).  The headline `value` is the chosen form: the
+autotuner's fastest precision form and schedule (its options are in
+`config.options`, its arithmetic in `dtype`); the plain FP64 form is reported
+beside it (`fp64`).  Each form's timed region is repeated and the median
+reported.  Further legs: the learned warm start (cluttered environment), four
+quadrotors at N = 25 (`multi4`), the uneven queue against solve-level
+batching (`uneven_queue`), and the CPU oracle on the host cores with each GPU
+form's error against it (`cpu_baseline`).
 
 python bench.py --gpus N --steps K --warmup W [--impl reference]
 """
@@ -216,41 +221,51 @@ def run_ours(args):
     n, m = desc.n, desc.m
     rsize = bipm.RESULT_DTYPE.itemsize
 
-    # chosen form: the autotuner's pick among the FP32 variants (untimed)
+    # chosen form: the autotuner's pick of precision form and schedule (untimed)
     if args.only_mixed:
-        best = bipm.Options(precision=1, fp32_switch=args.fp32_switch)
+        best, slots = bipm.Options(precision=1, fp32_switch=args.fp32_switch), B
         tune_table = []
     else:
         # the sample runs in the timed regime: a queue of twice the slot count
         _, theta_t = make_batch(WORKLOAD, 2 * B, first_id=10_000_000 + rank * 2 * B)
-        best, tune_table = autotune.autotune(desc, torch.as_tensor(theta_t, device=dev), B, stream=stream)
+        pick, tune_table = autotune.autotune(desc, torch.as_tensor(theta_t, device=dev), B, stream=stream,
+                                             schedule=not args.no_schedule_tune)
+        best, slots = pick.options, pick.slots
 
-    def timed_queue(options):
-        """W untimed warm-up steps, then K timed steps as one queue through B slots."""
-        b = bipm.Batch(desc, B, options, stream=stream)
+    def timed_queue(options, capacity, repeats):
+        """W untimed warm-up steps, then `repeats` timed regions of K steps each, every
+        region one queue of the K steps' problems through `capacity` slots; the
+        region with the median time is returned (time, records, clocks, all times)."""
+        b = bipm.Batch(desc, capacity, options, stream=stream)
         res = torch.empty(B * K * rsize, dtype=torch.uint8, device=dev)
         for _ in range(W):
             b.solve_queue(theta_wdev, None, res[: B * rsize])
         torch.cuda.synchronize()
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        clocks = ClockSampler(local)
-        clocks.start()
-        e0.record(stream)
-        b.solve_queue(theta_dev, None, res)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        clk = clocks.stop()
-        barrier()
+        runs = []
+        for _ in range(repeats):
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            clocks = ClockSampler(local)
+            clocks.start()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            b.solve_queue(theta_dev, None, res)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            clk = clocks.stop()
+            barrier()
+            runs.append((e0.elapsed_time(e1), bipm.results_from_bytes(res.cpu().numpy()), clk))
         b.close()
-        return e0.elapsed_time(e1), bipm.results_from_bytes(res.cpu().numpy()), clk
+        order = sorted(range(repeats), key=lambda i: runs[i][0])
+        ms, rec, clk = runs[order[repeats // 2]]
+        return ms, rec, clk, [r[0] for r in runs]
 
-    ms_mixed, r_mixed, clk = timed_queue(best)
+    ms_mixed, r_mixed, clk, ms_all = timed_queue(best, slots, args.repeats)
     if args.only_mixed:
-        ms_fp64, r_fp64 = ms_mixed, r_mixed
+        ms_fp64, r_fp64, ms_all64 = ms_mixed, r_mixed, ms_all
     else:
-        ms_fp64, r_fp64, _ = timed_queue(bipm.Options(precision=0))
+        ms_fp64, r_fp64, _, ms_all64 = timed_queue(bipm.Options(precision=0), B, args.repeats)
     conv_mixed = int(np.sum(r_mixed["status"] == bipm.CONVERGED))
     conv_fp64 = int(np.sum(r_fp64["status"] == bipm.CONVERGED))
 
@@ -258,7 +273,7 @@ def run_ours(args):
     # result records out, every copy inside the timed region
     theta_host = np.ascontiguousarray(theta)
     x_host = np.empty((B * K, n))
-    b = bipm.Batch(desc, B, best, stream=stream)
+    b = bipm.Batch(desc, slots, best, stream=stream)
     b.solve_queue(np.ascontiguousarray(theta_w), None)
     torch.cuda.synchronize()
     barrier()
@@ -306,24 +321,28 @@ def run_ours(args):
 
     warm = None if args.no_warm else warm_leg(args, dev, stream, rank, barrier, reduce, MAX, SUM)
     mixed = mixed_leg(args, dev, stream, barrier, reduce, MAX, SUM) if args.mixed > 0 else None
+    multi = multi_leg(args, dev, stream, barrier, reduce, MAX, SUM) if args.multi > 0 else None
 
     if rank == 0:
-        opt_desc = {"precision": best.precision, "fp32_switch": best.fp32_switch}
+        opt_desc = {"precision": best.precision, "fp32_switch": best.fp32_switch,
+                    "visit_cap": best.visit_cap or 96, "warps_per_sm": best.warps_per_sm or 24,
+                    "team_threads": best.team_threads or 256, "slots": slots}
         line = {
             "metric": METRIC, "value": tot_mixed / t_mixed, "unit": UNIT, "n_gpus": ws,
             "steps": K, "warmup": W, "ms_per_step": t_mixed * 1e3 / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 derivative blocks + f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": form_dtype(best),
             "data": "synthetic (seeded SplitMix64 tracking problems; no public dataset exists)",
             "config": {"workload": f"{WORKLOAD}: 1 quadrotor, RK4 N=30, 3 spheres, {B} problems per step",
                        "global_batch": B * ws, "parallelism": f"replicas x{ws}",
                        "mode": f"iteration-level batching: the {K} steps' problems stream through "
-                               f"{B} slots in one persistent launch",
+                               f"{slots} slots in one persistent launch",
                        "options": opt_desc,
+                       "repeats": f"median of {args.repeats} timed regions of {K} steps each",
                        "l2": "slot workspaces (~1.4 GB) exceed the 129 MB L2"},
+            "repeats_ms": ms_all,
             "fp64": {"value": tot_fp64 / t_fp64, "unit": UNIT, "ms_per_step": t_fp64 * 1e3 / K,
-                     "dtype": "f64"},
-            "autotune": [{"precision": o.precision, "fp32_switch": o.fp32_switch, "solves_per_s": v}
-                         for o, v in tune_table],
+                     "dtype": "f64", "repeats_ms": ms_all64},
+            "autotune": tune_table,
             "converged_frac": conv_mixed / (B * K),
             "iters_mean": float(np.mean(r_mixed["iters"])),
             "iterations": iteration_summary(r_mixed),
@@ -332,14 +351,17 @@ def run_ours(args):
                     "d2h_bytes_per_step": B * (n * 8 + rsize)},
             "roofline": roof,
             "clocks": clk,
-            "gpu_launches": queue_launches(B),
+            "gpu_launches": queue_launches(slots, best.warps_per_sm or 24),
         }
         if warm is not None:
             line["warm_start"] = warm
+        if multi is not None:
+            line["multi4"] = multi
         if mixed is not None:
             line["uneven_queue"] = mixed
         if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(desc, theta, budget_s=args.cpu_budget)
+            forms = {"chosen": best, "fp64": bipm.Options(precision=0)}
+            line["cpu_baseline"] = cpu_baseline(desc, theta, forms, stream, budget_s=args.cpu_budget)
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -420,43 +442,106 @@ def warm_leg(args, dev, stream, rank, barrier, reduce, MAX, SUM):
                         "dataset_s": t_data, "train_s": t_train}}
 
 
-# ------------------------------------------------ uneven queue leg (opt-in)
+# ------------------------------------------------------- uneven queue leg
 def mixed_leg(args, dev, stream, barrier, reduce, MAX, SUM):
     """Problems of 1-8 quadrotors and horizons 10/20/30/50 (32 structure
-    classes, drawn uniformly) in one persistent launch of the mixed queue,
-    chosen form; args.mixed problems through args.mixed_slots slots.  Inputs
-    are device-resident; the call sizes its workspace before the timed launch
-    sequence, so the rate is taken from the host clock around the whole call
-    and includes that allocation."""
+    classes, drawn uniformly), chosen form.  Iteration-level batching: all
+    args.mixed problems in one persistent launch of the mixed queue through
+    args.mixed_slots slots, a finished problem's slot refilled at once.
+    Solve-level batching on the same problems: consecutive batches of
+    args.mixed_slots problems, each launched with exactly its own slots, the
+    next starting when the slowest of the previous batch has finished.  The
+    slot count is below the resident warps, so no problem is parked in either
+    arm.  Inputs are device-resident; each call sizes its workspace, so the
+    rates are taken from the host clock around the calls."""
     import torch
 
     from paper_2606_26341_gb300 import bipm
-    from workloads import make_mixed
+    from workloads import make_mixed, n_theta
 
     ws, rank, _ = dist_env()
-    classes, cls, theta = make_mixed(args.mixed, first_id=rank * args.mixed)
+    Q, S = args.mixed, args.mixed_slots
+    classes, cls, theta = make_mixed(Q, first_id=rank * Q)
     th = torch.as_tensor(theta, device=dev)
-    res = torch.empty(args.mixed * bipm.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    rsize = bipm.RESULT_DTYPE.itemsize
     opts = bipm.Options(precision=1, fp32_switch=-1.0)
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    bipm.solve_mixed(classes, cls, th, n_slots=args.mixed_slots, options=opts, results=res, stream=stream)
-    torch.cuda.synchronize()
-    dt = reduce(time.perf_counter() - t0, MAX)
-    barrier()
-    r = bipm.results_from_bytes(res.cpu().numpy())
+    off = np.concatenate([[0], np.cumsum([n_theta(classes[k]) for k in cls])]).astype(np.int64)
+
+    def run(batches):
+        res = torch.empty(Q * rsize, dtype=torch.uint8, device=dev)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for lo in range(0, Q, batches):
+            hi = min(Q, lo + batches)
+            bipm.solve_mixed(classes, cls[lo:hi], th[off[lo]:off[hi]], n_slots=min(S, hi - lo), options=opts,
+                             results=res[lo * rsize:hi * rsize], stream=stream)
+        torch.cuda.synchronize()
+        dt = reduce(time.perf_counter() - t0, MAX)
+        barrier()
+        return bipm.results_from_bytes(res.cpu().numpy()), dt
+
+    r, dt = run(Q)
+    r_sl, dt_sl = run(S)
     conv = r["status"] == bipm.CONVERGED
     per_nq = {}
     for nq in range(1, 9):
         sel = np.array([classes[k].nq == nq for k in cls])
         per_nq[str(nq)] = {"problems": int(sel.sum()), "converged_frac": float(conv[sel].mean()),
                            "iters_mean": float(r["iters"][sel].mean())}
-    return {"workload": f"uneven queue: {args.mixed} problems, 1-8 quadrotors (pairwise distance 0.4; one "
-                        f"sphere for a single quadrotor), N in 10/20/30/50, {args.mixed_slots} slots",
-            "value": reduce(float(conv.sum()), SUM) / dt, "unit": UNIT, "seconds": dt,
+    ilb = reduce(float(conv.sum()), SUM) / dt
+    slb = reduce(float(np.sum(r_sl["status"] == bipm.CONVERGED)), SUM) / dt_sl
+    return {"workload": f"uneven queue: {Q} problems, 1-8 quadrotors (pairwise distance 0.4; one sphere for a "
+                        f"single quadrotor), N in 10/20/30/50, {S} slots",
+            "value": ilb, "unit": UNIT, "seconds": dt,
+            "solve_level_batching": {"value": slb, "unit": UNIT, "seconds": dt_sl,
+                                     "batches": int(math.ceil(Q / S))},
+            "ilb_gain": ilb / slb if slb > 0 else None,
             "converged_frac": float(conv.mean()), "iters_mean": float(r["iters"].mean()),
             "per_quad_count": per_nq}
+
+
+# ------------------------------------------------ four-quadrotor leg
+def multi_leg(args, dev, stream, barrier, reduce, MAX, SUM):
+    """Configuration 3 at its size: 4 quadrotors (48 states, 16 inputs), pairwise
+    separation 0.4, N = 25, args.multi problems solved as one batch through as
+    many slots (every problem starts at once), FP32 factorisation with FP64
+    refinement and plain FP64.  Device-timed (CUDA events on the stream)."""
+    import torch
+
+    from paper_2606_26341_gb300 import bipm
+    from workloads import ProblemDesc
+
+    ws, rank, _ = dist_env()
+    desc = ProblemDesc(nq=4, horizon=25, dt=0.05, pair_dist=0.4)
+    _, theta = make_batch("multi4", args.multi, desc=desc, first_id=rank * args.multi)
+    th = torch.as_tensor(theta, device=dev)
+    rsize = bipm.RESULT_DTYPE.itemsize
+    out = {"workload": f"multi4: 4 quadrotors, RK4 N=25, pairwise distance 0.4, {args.multi} problems",
+           "n": desc.n, "m": desc.m}
+    for name, opt in (("fp32_refined", bipm.Options(precision=1)), ("fp64", bipm.Options(precision=0))):
+        res = torch.empty(args.multi * rsize, dtype=torch.uint8, device=dev)
+        with bipm.Batch(desc, args.multi, opt, stream=stream) as b:
+            b.solve_queue(th[:8], None, res[:8 * rsize])  # warm-up
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.solve_queue(th, None, res)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+        r = bipm.results_from_bytes(res.cpu().numpy())
+        conv = r["status"] == bipm.CONVERGED
+        t = reduce(e0.elapsed_time(e1) / 1e3, MAX)
+        out[name] = {"value": reduce(float(conv.sum()), SUM) / t, "unit": UNIT, "seconds": t,
+                     "converged_frac": float(conv.mean()),
+                     "status_counts": {bipm.STATUS_NAMES[k]: int(np.sum(r["status"] == k))
+                                       for k in np.unique(r["status"])},
+                     "iters_mean": float(r["iters"].mean()),
+                     "max_kkt_err_converged": float(np.max(r["kkt_err"][conv])) if conv.any() else None}
+    return out
 
 
 def iteration_summary(results, converged_status=1):
@@ -476,14 +561,24 @@ def iteration_summary(results, converged_status=1):
             "objective_mean_converged": float(np.mean(np.asarray(results["obj"])[conv])) if conv.any() else None}
 
 
-def queue_launches(slots):
+def queue_launches(slots, warps_per_sm=24):
     """Kernels of one timed queue solve: the queue kernel alone when every slot
     has a resident warp; with spare slots also the slot reset, the block teams
-    for parked stragglers and their write-out.  Resident warps: 6 blocks of 4
-    warps per SM (the iteration kernels' launch bounds)."""
+    for parked stragglers and their write-out."""
     import torch
-    resident = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 24
+    resident = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * warps_per_sm
     return 4 if slots > resident else 1
+
+
+def form_dtype(o):
+    """The arithmetic of a precision form, for the JSON line's dtype."""
+    if o.precision == 0:
+        return "f64"
+    if o.precision == 2:
+        return "f32 derivative blocks + double-float (2 x f32) factorisation, f64 residuals and tests"
+    if o.fp32_switch < 0:
+        return "f32 derivative blocks + f64 factorisation, f64 residuals and tests"
+    return "f32 derivative blocks + f32 factorisation with f64 refinement, f64 residuals and tests"
 
 
 def stats_record_bytes():
@@ -509,7 +604,8 @@ def _oracle_one(args):
     from oracle.quadrotor import QuadNLP
     t0 = time.perf_counter()
     st, _ = ipm.solve(QuadNLP(desc, theta))
-    return st.status == ipm.CONVERGED, time.perf_counter() - t0
+    return {"ok": st.status == ipm.CONVERGED, "s": time.perf_counter() - t0, "status": int(st.status),
+            "iters": int(st.iter), "x": st.normal.x}
 
 
 def single_thread_env():
@@ -518,6 +614,8 @@ def single_thread_env():
 
 
 def oracle_rate(desc, theta, n_problems, processes):
+    """Converged count, wall time and per-problem records of the oracle on the
+    first n_problems rows, one problem per process."""
     single_thread_env()
     ctx = mp.get_context("spawn")
     jobs = [(desc, theta[j]) for j in range(n_problems)]
@@ -526,17 +624,67 @@ def oracle_rate(desc, theta, n_problems, processes):
         t0 = time.perf_counter()
         res = pool.map(_oracle_one, jobs)
         wall = time.perf_counter() - t0
-    conv = sum(1 for ok, _ in res if ok)
-    return conv, wall
+    conv = sum(1 for r in res if r["ok"])
+    return conv, wall, res
 
 
-def cpu_baseline(desc, theta, budget_s=20.0):
-    cores = min(os.cpu_count() or 1, 16)
-    n_prob = cores  # one problem per core (~10 s of CPU work per problem)
-    conv, wall = oracle_rate(desc, theta, n_prob, cores)
+def _kkt_one(args):
+    """The oracle's scaled optimality error E_0 at a GPU point (oracle arithmetic)."""
+    desc, theta, x, y, zl, zu = args
+    sys.path.insert(0, ROOT)
+    import torch
+
+    torch.set_num_threads(1)
+    from oracle import ipm
+    from oracle.quadrotor import QuadNLP
+    nlp = QuadNLP(desc, theta)
+    return ipm.opt_error(nlp, x, y, zl, zu, nlp.grad_f(x), nlp.jac_c(x), nlp.c(x), 0.0, ipm.Options())
+
+
+def gpu_error_vs_oracle(desc, theta, oracle_res, options, stream, processes):
+    """Each GPU form's result on the oracle's sample problems, against the oracle:
+    the distance e_v of the solution (Eq. 8) where both converged, the oracle's own
+    KKT error at every GPU-converged point, and the agreement of statuses and
+    iteration counts."""
+    from paper_2606_26341_gb300 import bipm
+
+    cnt = len(oracle_res)
+    with bipm.Batch(desc, cnt, options, stream=stream) as b:
+        b.set_problems(np.ascontiguousarray(theta[:cnt]))
+        b.solve()
+        st = b.get_stats()
+        x, y, zl, zu = b.get_solution()
+    conv = st["status"] == bipm.CONVERGED
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=processes) as pool:
+        kkt = pool.map(_kkt_one, [(desc, theta[j], x[j], y[j], zl[j], zu[j]) for j in np.nonzero(conv)[0]])
+    ev = [float(np.max(np.abs(x[j] - o["x"]) / (1.0 + np.abs(o["x"])))) for j, o in enumerate(oracle_res)
+          if o["ok"] and conv[j]]
+    return {"problems": cnt,
+            "e_v_x": {"max": max(ev) if ev else None, "median": float(np.median(ev)) if ev else None,
+                      "per_problem": ev},
+            "oracle_kkt_err_max": float(max(kkt)) if kkt else None,
+            "oracle_kkt_pass": int(sum(k <= 1e-6 for k in kkt)), "gpu_converged": int(conv.sum()),
+            "same_status": int(sum(st["status"][j] == o["status"] for j, o in enumerate(oracle_res))),
+            "same_iters": int(sum(st["iters"][j] == o["iters"] for j, o in enumerate(oracle_res)))}
+
+
+def cpu_baseline(desc, theta, forms, stream, budget_s=20.0):
+    """The oracle as it stands on the host cores: all cores (one problem per
+    process, two problems per core) and one core (two problems); then each GPU
+    form's error against the oracle's solutions of the same problems."""
+    cores = os.cpu_count() or 1
+    n_prob = 2 * cores
+    conv, wall, res = oracle_rate(desc, theta, n_prob, cores)
+    conv1, wall1, _ = oracle_rate(desc, theta, 2, 1)
+    errors = {name: gpu_error_vs_oracle(desc, theta, res, opt, stream, cores) for name, opt in forms.items()}
     return {"value": conv / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n_prob} problems of the {WORKLOAD} workload, one per process, "
-                      f"{wall:.1f} s wall"}
+            "sample": f"{n_prob} problems of the {WORKLOAD} workload (the first of the timed set), one per "
+                      f"process on {cores} cores, {wall:.1f} s wall",
+            "single_core": {"value": conv1 / wall1, "unit": UNIT, "cores": 1,
+                            "sample": f"2 problems, {wall1:.1f} s"},
+            "oracle_iters_mean": float(np.mean([r["iters"] for r in res])),
+            "gpu_error_vs_oracle": errors}
 
 
 def run_reference(args):
@@ -544,7 +692,7 @@ def run_reference(args):
     if rank != 0:
         return
     desc, theta = make_batch(WORKLOAD, 64)
-    cores = min(os.cpu_count() or 1, 16)
+    cores = os.cpu_count() or 1
     single_thread_env()
     ctx = mp.get_context("spawn")
     per_step = cores
@@ -557,7 +705,7 @@ def run_reference(args):
             dt = time.perf_counter() - t0
             if s >= args.warmup:
                 times.append(dt)
-                convs.append(sum(1 for ok, _ in res if ok))
+                convs.append(sum(1 for r in res if r["ok"]))
     total = sum(times)
     val = sum(convs) / total
     line = {
@@ -589,8 +737,11 @@ def main():
     ap.add_argument("--warm-train", type=int, default=16384, help="training problems of the warm-start leg")
     ap.add_argument("--warm-epochs", type=int, default=30)
     ap.add_argument("--warm-batch", type=int, default=16384, help="problems of the warm-start leg")
-    ap.add_argument("--mixed", type=int, default=0, help="problems of the uneven-queue leg (0: skip)")
-    ap.add_argument("--mixed-slots", type=int, default=3072, help="slots of the uneven-queue leg")
+    ap.add_argument("--mixed", type=int, default=512, help="problems of the uneven-queue leg (0: skip)")
+    ap.add_argument("--mixed-slots", type=int, default=256, help="slots of the uneven-queue leg")
+    ap.add_argument("--multi", type=int, default=1024, help="problems of the four-quadrotor leg (0: skip)")
+    ap.add_argument("--repeats", type=int, default=3, help="timed regions per form (median reported)")
+    ap.add_argument("--no-schedule-tune", action="store_true", help="autotune the precision form only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -64,8 +64,7 @@ extern "C" {
  * EMPTY          the slot holds no problem (a queue problem never started)
  * FP64_ESCALATION_FAILED  mixed precision: iterative refinement of the FP32
  *                step failed, and the FP64 re-factorisation that replaced it
- *                did not solve the Newton system (Eq. 7) to a residual ratio
- *                of 1e-6 either */
+ *                gave a Newton step (Eq. 7) that is not finite either */
 #define BIPM_RUNNING 0
 #define BIPM_CONVERGED 1
 #define BIPM_MAX_ITER 2
@@ -126,6 +125,16 @@ typedef struct {
                              next bipm_solve continues them), queue problems not
                              yet started report EMPTY, and the call returns
                              BIPM_ETIMEOUT. */
+  /* Schedule of the persistent kernels (iteration-level batching, Sec. V).
+   * None of them changes a result beyond the order of floating-point sums;
+   * 0 selects the default. */
+  int visit_cap;      /* queue with more slots than resident warps: iterations
+                         a problem runs in its warp before it is parked for the
+                         block teams (default 96; >= 1) */
+  int warps_per_sm;   /* resident warps per SM of the warp-team kernels: 4, 8,
+                         ..., 24 (default 24, the most that fit) */
+  int team_threads;   /* threads of a block team: 128 or 256 (default 256) */
+  int reserved_[3];   /* must be 0 */
 } bipm_options;
 
 /* Per-slot outcome and counters: the branches of Table I each problem took

@@ -78,6 +78,13 @@ class Options:
     ls_max_trials: int = 60
     trace_cond: bool = False  # record the 2-norm condition number of each step's matrix
     trace_soc: bool = False   # record the linear systems of the second-order corrections
+    # watchdog (Table I row 3) and soft feasibility restoration (row 5); off by default
+    watchdog: bool = False
+    wd_trigger: int = 10      # consecutive shortened steps that start the watchdog
+    wd_trial_max: int = 3     # unconditional steps before the watchdog gives up
+    soft_resto: bool = False
+    kappa_soft: float = 1e-4  # required relative decrease of the primal-dual error
+    soft_max: int = 10        # soft restoration steps before hard restoration
 
 
 @dataclasses.dataclass
@@ -94,6 +101,15 @@ class Phase:
     theta_min: float = 0.0
     dw_last: float = 0.0
     tiny: bool = False
+    # watchdog: consecutive shortened steps, active flag, unconditional steps
+    # taken, and the stored iterate with its step and reference values
+    wd_short: int = 0
+    wd_active: bool = False
+    wd_trials: int = 0
+    wd_store: dict | None = None
+    # soft restoration: active flag and soft steps taken in the current phase
+    soft_active: bool = False
+    soft_iters: int = 0
 
 
 @dataclasses.dataclass
@@ -257,6 +273,34 @@ def soc_constraint_rhs(alpha_prev, c_soc_prev, c_trial):
 def soc_should_stop(p, theta_soc, theta_old, opt):
     """Stop correcting after p_max corrections or when theta no longer shrinks by kappa_soc."""
     return p >= opt.p_max or theta_soc > opt.kappa_soc * theta_old
+
+
+def primal_dual_error(nlp, x, y, zl, zu, g, J, c, mu):
+    """1-norm primal-dual error of the barrier problem at mu (the conditions of
+    Eq. 5 with mu): |grad L|_1 + |c|_1 + |S_L z_L - mu e|_1 + |S_U z_U - mu e|_1.
+    Soft restoration accepts a step that reduces it."""
+    has_l, has_u = bound_sets(nlp)
+    sl, su = slacks(nlp, x)
+    gl = g + J.T @ y - zl + zu
+    comp = float(np.sum(np.abs(sl[has_l] * zl[has_l] - mu)) + np.sum(np.abs(su[has_u] * zu[has_u] - mu)))
+    return float(np.sum(np.abs(gl)) + np.sum(np.abs(c))) + comp
+
+
+def soft_resto_accepts(e_trial, e_current, opt):
+    """Soft restoration's acceptance: E_pd(trial) <= (1 - kappa_soft) E_pd(current)."""
+    return e_trial <= (1.0 - opt.kappa_soft) * e_current
+
+
+def watchdog_should_start(ph, opt):
+    """The watchdog starts after wd_trigger consecutive shortened steps."""
+    return opt.watchdog and not ph.wd_active and ph.wd_short >= opt.wd_trigger
+
+
+def end_globalization(ph):
+    """A barrier-parameter decrease (or entering restoration) ends an active watchdog
+    and soft restoration and clears the shortened-step count."""
+    ph.wd_active, ph.wd_trials, ph.wd_store, ph.wd_short = False, 0, None, 0
+    ph.soft_active, ph.soft_iters = False, 0
 
 
 # ------------------------------------------------------ barrier update --
@@ -497,9 +541,12 @@ class _Outcome:
 
 
 def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
-                    y_ls=False):
+                    y_ls=False, globalize=False):
     """One iteration of the barrier method on `nlp` from phase state `ph`.
 
+    globalize: the watchdog and soft restoration (when enabled in opt) take part
+    in this phase's line search (the original problem; the restoration phase's
+    line search is the plain backtracking filter search).
     Returns an _Outcome; on ACCEPTED, `ph` holds the next iterate.
     """
     x, y, zl, zu = ph.x, ph.y, ph.zl, ph.zu
@@ -532,6 +579,7 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
         ph.mu = mu_new
         ph.filt = []
         ph.tiny = False
+        end_globalization(ph)
     mu = ph.mu
     tau = max(opt.tau_min, 1.0 - mu)
 
@@ -589,10 +637,11 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
     dzl, dzu = z_step(dx)
     a_max = alpha_primal_max(dx)
 
-    def accept(alpha, dx_, dy_, dzl_, dzu_, augment, theta0, phi0):
+    def accept(alpha, dx_, dy_, dzl_, dzu_, augment, theta0, phi0, az=None):
         x_new = x + alpha * dx_
         y_new = y + alpha * dy_
-        az = alpha_dual_max(dzl_, dzu_)
+        if az is None:
+            az = alpha_dual_max(dzl_, dzu_)
         zl_new = zl + az * dzl_
         zu_new = zu + az * dzu_
         zl_new, zu_new = kappa_sigma_reset(nlp, x_new, zl_new, zu_new, mu, opt)
@@ -607,6 +656,7 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
         trace["tiny"] = True
         accept(a_max, dx, dy, dzl, dzu, False, 0.0, 0.0)
         ph.tiny = True
+        ph.wd_short = 0
         return _Outcome.ACCEPTED
     ph.tiny = False
 
@@ -628,6 +678,74 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
     def needs_augment(alpha, phi_t):
         return filter_needs_augment(alpha, phi_t, phi0, gdx, theta, opt)
 
+    def soft_resto_step():
+        """Soft restoration (Table I row 5): the primal-dual step with one step size
+        alpha_s = min(alpha_max, alpha_z_max), accepted if the trial point passes the
+        original acceptance tests (which ends the soft phase) or reduces the
+        primal-dual error E_pd (which continues it)."""
+        a_s = min(a_max, alpha_dual_max(dzl, dzu))
+        xt = x + a_s * dx
+        tv = trial_values(xt)
+        trace["soft_trial"] = True
+        if tv is None:
+            return False
+        theta_t, phi_t, c_t = tv
+        if trial_acceptable(ph, theta_t, phi_t, 0.0, theta, phi0, gdx, opt):
+            accept(a_s, dx, dy, dzl, dzu, True, theta, phi0, az=a_s)
+            ph.soft_active, ph.soft_iters = False, 0
+            trace["soft_left"] = True
+            return True
+        yt, zlt, zut = y + a_s * dy, zl + a_s * dzl, zu + a_s * dzu
+        gt, Jt = nlp.grad_f(xt), nlp.jac_c(xt)
+        if not (np.all(np.isfinite(gt)) and np.all(np.isfinite(Jt))):
+            return False
+        e_t = primal_dual_error(nlp, xt, yt, zlt, zut, gt, Jt, c_t, mu)
+        e_0 = primal_dual_error(nlp, x, y, zl, zu, g, J, c, mu)
+        if opt.trace_soc:
+            trace["soft_log"] = {"alpha": a_s, "a_max": a_max, "az_max": alpha_dual_max(dzl, dzu),
+                                 "x": x.copy(), "y": y.copy(), "zl": zl.copy(), "zu": zu.copy(),
+                                 "dx": dx.copy(), "dy": dy.copy(), "dzl": dzl.copy(), "dzu": dzu.copy(),
+                                 "mu": mu, "e_trial": e_t, "e_current": e_0}
+        if not soft_resto_accepts(e_t, e_0, opt):
+            return False
+        accept(a_s, dx, dy, dzl, dzu, True, theta, phi0, az=a_s)
+        ph.soft_active = True
+        ph.soft_iters += 1
+        trace["soft_step"] = True
+        return True
+
+    if globalize and ph.soft_active:
+        # in the soft restoration phase the soft step replaces the line search
+        if ph.soft_iters < opt.soft_max and soft_resto_step():
+            return _Outcome.ACCEPTED
+        return _Outcome.LS_FAILED
+
+    if globalize and watchdog_should_start(ph, opt):
+        ph.wd_active, ph.wd_trials, ph.wd_short = True, 0, 0
+        ph.wd_store = {"x": x.copy(), "y": y.copy(), "zl": zl.copy(), "zu": zu.copy(), "dx": dx.copy(),
+                       "dy": dy.copy(), "dzl": dzl.copy(), "dzu": dzu.copy(), "theta": theta, "phi": phi0,
+                       "gdx": gdx, "a_max": a_max, "a_min": a_min}
+        trace["wd_start"] = True
+    if globalize and ph.wd_active:
+        # watchdog (Table I row 3): the full step, judged against the stored iterate
+        W = ph.wd_store
+        tv = trial_values(x + a_max * dx)
+        if tv is not None and trial_acceptable(ph, tv[0], tv[1], a_max, W["theta"], W["phi"], W["gdx"], opt):
+            accept(a_max, dx, dy, dzl, dzu,
+                   filter_needs_augment(a_max, tv[1], W["phi"], W["gdx"], W["theta"], opt), W["theta"], W["phi"])
+            ph.wd_active, ph.wd_trials, ph.wd_store = False, 0, None
+            trace["wd_accepted"] = True
+            return _Outcome.ACCEPTED
+        ph.wd_trials += 1
+        if ph.wd_trials <= opt.wd_trial_max:
+            accept(a_max, dx, dy, dzl, dzu, False, 0.0, 0.0)
+            trace["wd_step"] = True
+            return _Outcome.ACCEPTED
+        # give up: back to the stored iterate and a backtracking search along its step
+        ph.wd_active, ph.wd_trials, ph.wd_store = False, 0, None
+        trace["wd_return"] = True
+        return _watchdog_return(nlp, ph, opt, trace, W, mu, tau)
+
     alpha = a_max
     n_trial = 0
     while True:
@@ -639,6 +757,7 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
             if acceptable(theta_t, phi_t, alpha):
                 accept(alpha, dx, dy, dzl, dzu, needs_augment(alpha, phi_t), theta, phi0)
                 trace["ls_trials"] = n_trial
+                ph.wd_short = ph.wd_short + 1 if alpha < a_max else 0
                 return _Outcome.ACCEPTED
             # second-order correction on the first trial when theta did not decrease
             if n_trial == 1 and not (theta_t < theta):
@@ -663,6 +782,7 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
                                theta, phi0)
                         trace["soc_accepted"] = True
                         trace["ls_trials"] = n_trial
+                        ph.wd_short = 0
                         return _Outcome.ACCEPTED
                     if soc_should_stop(p, theta_s, theta_old, opt):
                         break
@@ -671,7 +791,45 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
         alpha *= 0.5
         if alpha < a_min or n_trial >= opt.ls_max_trials:
             trace["ls_trials"] = n_trial
+            if globalize and opt.soft_resto and soft_resto_step():
+                return _Outcome.ACCEPTED
             return _Outcome.LS_FAILED
+
+
+def _watchdog_return(nlp, ph, opt, trace, W, mu, tau):
+    """The watchdog gave up: the iterate returns to the one stored when it started,
+    and a backtracking filter line search runs along that iterate's step, judged
+    against its reference values, from half its full step (the full step was the
+    watchdog's first step).  The stored factorisation is gone, so no second-order
+    correction is tried.  Returns the outcome of that search."""
+    has_l, has_u = bound_sets(nlp)
+    x, y, zl, zu = W["x"], W["y"], W["zl"], W["zu"]
+    ph.x, ph.y, ph.zl, ph.zu = x, y, zl, zu
+    theta, phi0, gdx = W["theta"], W["phi"], W["gdx"]
+
+    def alpha_dual_max(dzl_, dzu_):
+        return min(frac_to_boundary(zl[has_l], dzl_[has_l], tau), frac_to_boundary(zu[has_u], dzu_[has_u], tau))
+
+    alpha = 0.5 * W["a_max"]
+    n_trial = 0
+    while alpha >= W["a_min"] and n_trial < opt.ls_max_trials:
+        n_trial += 1
+        xt = x + alpha * W["dx"]
+        ft, ct = nlp.f(xt), nlp.c(xt)
+        if np.isfinite(ft) and np.all(np.isfinite(ct)):
+            theta_t, phi_t = theta_of(ct), barrier_phi(nlp, xt, ft, mu, opt)
+            if trial_acceptable(ph, theta_t, phi_t, alpha, theta, phi0, gdx, opt):
+                az = alpha_dual_max(W["dzl"], W["dzu"])
+                x_new = xt
+                zl_new, zu_new = kappa_sigma_reset(nlp, x_new, zl + az * W["dzl"], zu + az * W["dzu"], mu, opt)
+                if filter_needs_augment(alpha, phi_t, phi0, gdx, theta, opt):
+                    filter_add(ph, *filter_entry(theta, phi0, opt), opt)
+                ph.x, ph.y, ph.zl, ph.zu = x_new, y + alpha * W["dy"], zl_new, zu_new
+                trace["alpha"], trace["alpha_z"], trace["ls_trials"] = alpha, az, n_trial
+                return _Outcome.ACCEPTED
+        alpha *= 0.5
+    trace["ls_trials"] = n_trial
+    return _Outcome.LS_FAILED
 
 
 def resto_start(nlp, st: SolverState, opt: Options):
@@ -715,7 +873,7 @@ def step(nlp, st: SolverState, opt: Options) -> dict:
     if st.mode == NORMAL:
         ph = st.normal
         out = phase_iteration(nlp, ph, opt, trace, init_theta=st.need_init,
-                              y_ls=st.need_y_ls) if st.iter < opt.max_iter else None
+                              y_ls=st.need_y_ls, globalize=True) if st.iter < opt.max_iter else None
         if out is None:
             # the iteration cap is tested after the convergence test of the same point
             out = _check_only(nlp, ph, opt, st)
@@ -743,6 +901,7 @@ def step(nlp, st: SolverState, opt: Options) -> dict:
             if theta_of(c) <= opt.tol:
                 st.status = RESTO_FAILED
             else:
+                end_globalization(ph)
                 resto_start(nlp, st, opt)
                 trace["entered_resto"] = True
                 st.iter += 1

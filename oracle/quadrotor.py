@@ -195,11 +195,88 @@ class QuadNLP:
     def grad_f(self, w):
         return torch.func.grad(self.f_t)(torch.as_tensor(w)).numpy()
 
+    # Derivatives.  c and the Lagrangian are sums of per-stage terms: the dynamics
+    # row block of interval k depends only on (x_k, u_k, x_{k+1}), an inequality
+    # block only on (x_k, s_k), the objective is a sum of stage costs.  The
+    # Jacobian and the Lagrangian Hessian (Eq. 4) are therefore assembled from
+    # autograd derivatives of these stage functions (vectorised over stages);
+    # jac_c_whole / hess_lag_whole differentiate the whole decision vector at
+    # once and serve as the check of the assembly.
+    def _dyn(self, z):
+        """F(x_k, u_k) of one interval from z = (x_k, u_k)."""
+        x = z[:self.nx].reshape(self.nq, 12)
+        u = z[self.nx:].reshape(self.nq, 4)
+        return rk4(x, u, self.dt).reshape(self.nx)
+
+    def _ineq1(self, xk):
+        return self.ineq(xk.reshape(1, -1))[0]
+
+    def _stage_cost(self, z, r):
+        """Cost of interval k < N from z = (x_k, u_k) and the reference r = x^ref_k."""
+        ex = z[:self.nx] - r
+        eu = z[self.nx:] - self.uh
+        return (self.qw * ex ** 2).sum() + (self.rw * eu ** 2).sum()
+
+    def _term_cost(self, x, r):
+        return QN_SCALE * (self.qw * (x - r) ** 2).sum()
+
     def jac_c(self, w):
-        return torch.func.jacfwd(self.c_t)(torch.as_tensor(w)).numpy()
+        """Constraint Jacobian, assembled from the stage Jacobians."""
+        wt = torch.as_tensor(w)
+        x, u, _ = self.split(wt)
+        nx, ni, N = self.nx, self.ni, self.N
+        xi, ui, si = self.xi.numpy(), self.ui.numpy(), self.si.numpy()
+        J = np.zeros((self.m, self.n))
+        J[np.arange(nx), xi[0]] = 1.0
+        Z = torch.cat([x[:-1], u], dim=1)
+        Jd = torch.func.vmap(torch.func.jacfwd(self._dyn))(Z).numpy()
+        Jg = torch.func.vmap(torch.func.jacfwd(self._ineq1))(x[1:]).numpy() if ni else None
+        row = nx
+        for k in range(N):
+            J[row:row + nx][:, np.concatenate([xi[k], ui[k]])] = -Jd[k]
+            J[np.arange(row, row + nx), xi[k + 1]] = 1.0
+            row += nx
+            if ni:
+                J[row:row + ni][:, xi[k + 1]] = Jg[k]
+                J[np.arange(row, row + ni), si[k]] = -1.0
+                row += ni
+        return J
 
     def hess_lag(self, w, y, obj_factor=1.0):
-        """obj_factor * Hess f + sum_i y_i Hess c_i (Hessian of the Lagrangian, Eq. 4)."""
+        """obj_factor * Hess f + sum_i y_i Hess c_i (Hessian of the Lagrangian, Eq. 4),
+        assembled from the stage Hessians."""
+        wt = torch.as_tensor(w)
+        yt = torch.as_tensor(np.asarray(y, dtype=np.float64))
+        x, u, _ = self.split(wt)
+        nx, ni, N = self.nx, self.ni, self.N
+        xi, ui = self.xi.numpy(), self.ui.numpy()
+        blk = nx + ni
+        # multipliers of the dynamics rows x_{k+1} - F(z_k) and of the rows g(x_{k+1}) - s
+        ydyn = torch.stack([yt[nx + k * blk: nx + k * blk + nx] for k in range(N)])
+        Z = torch.cat([x[:-1], u], dim=1)
+        Hd = torch.func.vmap(torch.func.hessian(lambda z, lam: -(lam * self._dyn(z)).sum()))(Z, ydyn).numpy()
+        if obj_factor != 0.0:
+            Hc = torch.func.vmap(torch.func.hessian(self._stage_cost))(Z, self.xref[:-1]).numpy()
+            Ht = torch.func.hessian(self._term_cost)(x[-1], self.xref[-1]).numpy()
+        H = np.zeros((self.n, self.n))
+        for k in range(N):
+            idx = np.concatenate([xi[k], ui[k]])
+            blkH = Hd[k] + (obj_factor * Hc[k] if obj_factor != 0.0 else 0.0)
+            H[np.ix_(idx, idx)] += blkH
+        if obj_factor != 0.0:
+            H[np.ix_(xi[N], xi[N])] += obj_factor * Ht
+        if ni:
+            yin = torch.stack([yt[nx + k * blk + nx: nx + (k + 1) * blk] for k in range(N)])
+            Hg = torch.func.vmap(torch.func.hessian(lambda xk, lam: (lam * self._ineq1(xk)).sum()))(
+                x[1:], yin).numpy()
+            for k in range(N):
+                H[np.ix_(xi[k + 1], xi[k + 1])] += Hg[k]
+        return H
+
+    def jac_c_whole(self, w):
+        return torch.func.jacfwd(self.c_t)(torch.as_tensor(w)).numpy()
+
+    def hess_lag_whole(self, w, y, obj_factor=1.0):
         yt = torch.as_tensor(y)
 
         def lag(wt):

@@ -34,7 +34,9 @@ class OptionsC(ctypes.Structure):
                 ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("fp32_switch", ctypes.c_double), ("warm_mu_init", ctypes.c_double),
                 ("warm_bound_push", ctypes.c_double), ("warm_max_iter", ctypes.c_int),
-                ("time_limit_ms", ctypes.c_int)]
+                ("time_limit_ms", ctypes.c_int), ("visit_cap", ctypes.c_int),
+                ("warps_per_sm", ctypes.c_int), ("team_threads", ctypes.c_int),
+                ("reserved_", ctypes.c_int * 3)]
 
 
 class StatsC(ctypes.Structure):
@@ -208,11 +210,15 @@ class Options:
     warm_bound_push: float = 0.0  # bound push of a warm start (0: library default 1e-3)
     warm_max_iter: int = 0        # iteration budget of a warm start (0: library default 60)
     time_limit_ms: int = 0        # device time budget of one call (0: none; BIPM_ETIMEOUT when spent)
+    visit_cap: int = 0            # queue iterations before a straggler is parked (0: 96)
+    warps_per_sm: int = 0         # resident warps per SM, 4..24 in steps of 4 (0: 24)
+    team_threads: int = 0         # block-team threads, 128 or 256 (0: 256)
 
     def to_c(self):
         return OptionsC(self.tol, self.max_iter, self.mu_init, self.precision, self.schedule,
                         self.fp32_switch, self.warm_mu_init, self.warm_bound_push, self.warm_max_iter,
-                        self.time_limit_ms)
+                        self.time_limit_ms, self.visit_cap, self.warps_per_sm, self.team_threads,
+                        (ctypes.c_int * 3)(0, 0, 0))
 
 
 def _stream_ptr(stream):

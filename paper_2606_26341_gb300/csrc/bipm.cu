@@ -91,6 +91,14 @@ int options_from(const bipm_options* opt, bipm_options* o_out, Options* dev) {
       o.schedule < 0 || o.schedule > 2)
     return fail(BIPM_EINVAL, "bad options");
   if (o.time_limit_ms < 0) return fail(BIPM_EINVAL, "time_limit_ms must be >= 0");
+  if (o.visit_cap == 0) o.visit_cap = kQueueVisit;
+  if (o.warps_per_sm == 0) o.warps_per_sm = 24;
+  if (o.team_threads == 0) o.team_threads = kBlockTeam;
+  if (o.visit_cap < 1) return fail(BIPM_EINVAL, "visit_cap must be >= 1");
+  if (o.warps_per_sm < kWarpsPerBlock || o.warps_per_sm > 24 || o.warps_per_sm % kWarpsPerBlock)
+    return fail(BIPM_EINVAL, "warps_per_sm must be a multiple of 4 in 4..24");
+  if (o.team_threads != 128 && o.team_threads != 256) return fail(BIPM_EINVAL, "team_threads must be 128 or 256");
+  if (o.reserved_[0] || o.reserved_[1] || o.reserved_[2]) return fail(BIPM_EINVAL, "reserved options must be 0");
   dev->tol = o.tol;
   dev->max_iter = o.max_iter;
   dev->mu_init = o.mu_init;
@@ -127,6 +135,7 @@ struct bipm_batch {
   int schedule = 0;
   int loaded = 0;
   int time_limit_ms = 0;
+  int team_threads = kBlockTeam;  // threads of a block team
 };
 
 namespace bipm {
@@ -292,7 +301,7 @@ int run_iterations(bipm_batch* b, int n_iter) {
     CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
     void* args2[] = {&b->dparams, &n_iter};
     CUDA_TRY(cudaLaunchKernel(block_kernel_ptr(b->opt.precision), dim3(b->block_blocks),
-                              dim3(kBlockTeam), args2, (size_t)b->smem_per_warp + 128,
+                              dim3(b->team_threads), args2, (size_t)b->smem_per_warp + 128,
                               b->stream));
   }
   return end_call(b->counter, b->time_limit_ms, b->stream);
@@ -401,7 +410,10 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
       per_sm < 1)
     return cleanup(BIPM_ECUDA, "kernel does not fit on an SM (shared memory " + std::to_string(smem) + " B)");
   int need = (int)((cap + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  // resident blocks per SM: what fits, capped by the requested warps per SM
+  per_sm = std::min(per_sm, o.warps_per_sm / kWarpsPerBlock);
   b->blocks = std::max(1, std::min(need, sms * per_sm));
+  b->team_threads = o.team_threads;
   {
     void* bfn = block_kernel_ptr(o.precision);
     size_t bsm = (size_t)b->smem_per_warp + 128;
@@ -409,7 +421,7 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
         cudaFuncSetAttribute(bfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm) != cudaSuccess)
       return cleanup(BIPM_ECUDA, "shared memory attribute (block kernel)");
     int per_sm_b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, bfn, kBlockTeam, bsm) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, bfn, b->team_threads, bsm) != cudaSuccess ||
         per_sm_b < 1)
       return cleanup(BIPM_ECUDA, "block kernel does not fit on an SM");
     b->block_blocks = std::max(1, std::min((int)cap, sms * per_sm_b));
@@ -420,7 +432,7 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
     const int warps = std::min(capacity, b->blocks * kWarpsPerBlock);
     P.spare_counter = b->counter + 1;
     P.n_spare = std::max(0, capacity - warps);
-    P.visit_cap = P.n_spare > 0 ? kQueueVisit : 0;
+    P.visit_cap = P.n_spare > 0 ? o.visit_cap : 0;
     if (cudaMemcpy(b->dparams, &P, sizeof(P), cudaMemcpyHostToDevice) != cudaSuccess)
       return cleanup(BIPM_ECUDA, "params copy");
   }
@@ -559,7 +571,7 @@ static int solve_queue_impl(bipm_batch* b, const double* theta_queue, const doub
     int n_iter = 0;
     CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
     void* args2[] = {&b->dparams, &n_iter};
-    CUDA_TRY(cudaLaunchKernel(block_kernel_ptr(b->opt.precision), dim3(b->block_blocks), dim3(kBlockTeam),
+    CUDA_TRY(cudaLaunchKernel(block_kernel_ptr(b->opt.precision), dim3(b->block_blocks), dim3(b->team_threads),
                               args2, (size_t)b->smem_per_warp + 128, b->stream));
     queue_writeout<<<(b->capacity * 32 + 255) / 256, 256, 0, b->stream>>>(b->dparams, x_dev, r_dev);
     CUDA_TRY(cudaGetLastError());
@@ -672,8 +684,9 @@ int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qfn, 32 * kWarpsPerBlock, qsm));
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, bfn, kBlockTeam, bsm));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, bfn, o.team_threads, bsm));
   if (per_sm < 1 || per_sm_b < 1) return fail(BIPM_ECUDA, "mixed queue kernels do not fit on an SM");
+  per_sm = std::min(per_sm, o.warps_per_sm / kWarpsPerBlock);
   const int warps = std::min(n_slots, sms * per_sm * kWarpsPerBlock);
   const int n_spare = n_slots - warps;
 
@@ -721,7 +734,7 @@ int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm
     P.smem_per_warp = smem_c[k];
     P.spare_counter = counter + 1;
     P.n_spare = n_spare;
-    P.visit_cap = n_spare > 0 ? kQueueVisit : 0;
+    P.visit_cap = n_spare > 0 ? o.visit_cap : 0;
     P.theta_stride = mth;
     set_budget(P, counter, o.time_limit_ms);
   }
@@ -743,7 +756,7 @@ int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm
   if (n_spare > 0) {
     CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), stream));
     void* args2[] = {&dP};
-    CUDA_TRY(cudaLaunchKernel(bfn, dim3(std::max(1, std::min(n_slots, sms * per_sm_b))), dim3(kBlockTeam), args2,
+    CUDA_TRY(cudaLaunchKernel(bfn, dim3(std::max(1, std::min(n_slots, sms * per_sm_b))), dim3(o.team_threads), args2,
                               bsm, stream));
     mixed_writeout<<<(int)(((long long)n_slots * 32 + 255) / 256), 256, 0, stream>>>(dP, xoff_d, x_dev, r_dev);
     CUDA_TRY(cudaGetLastError());

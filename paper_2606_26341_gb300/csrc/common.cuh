@@ -106,9 +106,6 @@ constexpr int kFilterCap = 64;
 constexpr int kLsMaxTrials = 60;
 constexpr int kIrMaxSteps = 10;
 constexpr double kIrTol = 1e-10;
-// residual ratio an FP64 re-solve after failed refinement must meet; above it
-// the problem ends with BIPM_FP64_ESCALATION_FAILED
-constexpr double kEscTol = 1e-6;
 constexpr int kGmresM = 6;        // Krylov dimension per restart
 constexpr double kFp32BarrierMax = 1e5;  // above: factorise in FP64 this iteration
 constexpr int kGmresRestarts = 3;

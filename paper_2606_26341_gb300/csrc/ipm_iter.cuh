@@ -359,12 +359,8 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF>& c, const double* r, doub
   if (factor<TB, TF, double>(c, c.fac64, c.dw, flags, y) == 0) return false;
   c.use64 = 1;
   solve<TB, TF, double>(c, c.fac64, r, out, flags, y);
-  // the FP64 step must solve the system it was given to kEscTol
-  kkt_matvec(c, out, res, c.dw, y);
-  for (int i = lane; i < len; i += c.T) res[at(i)] = -r[at(i)] - res[at(i)];
-  team_sync(c);
-  const double ratio = norm_inf(res) / (fmin(norm_inf(out), 1e6 * rnorm) + rnorm);
-  if (!(ratio <= kEscTol)) c.esc_failed = 1;
+  // an FP64 step that is not finite cannot be used: the problem stops
+  if (!all_finite(c, out, nused) || !all_finite(c, out + nwk, c.d.m)) c.esc_failed = 1;
   return true;
 }
 

@@ -116,6 +116,7 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
           cudaSuccess ||
       per_sm < 1)
     return sfail(BIPM_ECUDA, "kernel does not fit on an SM");
+  per_sm = std::min(per_sm, o.warps_per_sm / kWarpsPerBlock);
   const int slots = std::max(1, std::min({fit, count, sms * per_sm * kWarpsPerBlock}));
 
   unsigned char* p = base + hdr;

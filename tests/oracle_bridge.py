@@ -144,3 +144,22 @@ def oracle_warm_case(job):
     guess = warm.decode(desc, theta, o, lambda s: nlp.ineq(torch.as_tensor(s)).numpy())
     st, _ = ipm.solve(nlp, x0=guess, opt=warm.warm_options())
     return guess, st.status, st.iter, st.normal.x, cold.iter
+
+
+def check_outcome(desc, theta, status, x, y, zl, zu, oracle_status, tol=1e-6):
+    """Outcome rule of a GPU solve against the oracle's solve of the same problem.
+
+    * The oracle converged: the GPU must converge too, to a point that the
+      oracle's own KKT evaluation accepts (E_0 <= tol).
+    * The oracle ended in a failure status: the GPU must end in the same one, or
+      converge to a point the oracle's KKT test accepts.  The second case is a
+      path split: a failing run passes through numerically singular steps,
+      where two backward-stable solvers may round onto different paths.
+    Returns True for a path split (the caller bounds how many it accepts)."""
+    if status == ipm.CONVERGED:
+        err = oracle_kkt_error(desc, theta, x, y, zl, zu, tol)
+        assert err <= tol, ("GPU point fails the oracle's KKT test", err)
+        return oracle_status != ipm.CONVERGED
+    assert oracle_status != ipm.CONVERGED, ("oracle converged, GPU ended with status", status)
+    assert status == oracle_status, ("failure statuses differ", status, oracle_status)
+    return False

@@ -88,6 +88,35 @@ def test_gradient_matches_oracle(bipm, rows):
     for sl in _layer_slices(WIDTHS):
         assert np.linalg.norm(g[sl] - g_em[sl]) <= 2e-3 * np.linalg.norm(g_em[sl]), sl
         assert np.linalg.norm(g[sl] - g_ex[sl]) <= 5e-2 * np.linalg.norm(g_ex[sl]), sl
+    # element by element: each gradient entry is a sum of products (dz_i a_j over
+    # the rows, or dz_i alone for a bias); its magnitude bound M sums the products'
+    # absolute values.  With the same bfloat16 rounding points on both sides the
+    # kernels differ from the emulation by FP32 accumulation and by operands whose
+    # bfloat16 rounding flips between neighbours (one unit 2^-8 of a factor of a
+    # term: two per product, and as many again through the back-propagated
+    # error the term's dz inherits), so |g - g_em| <= 4 * 2^-8 * M entry by entry.
+    M = _grad_magnitude(WIDTHS, f64, x.astype(np.float64), t.astype(np.float64))
+    ratio = np.abs(g - g_em) / (2.0 ** -8 * M + 1e-30)
+    print(f"rows {rows}: max |g - g_em| / (2^-8 M) = {ratio.max():.3f}")
+    assert np.all(np.abs(g - g_em) <= 4.0 * 2.0 ** -8 * M + 1e-12)
+
+
+def _grad_magnitude(widths, flat, x, t):
+    """Entry-wise magnitude of the loss gradient's sums: |dz_l|^T |a_{l-1}| for the
+    weights and sum |dz_l| for the biases, with |dz| propagated through |W| and
+    |tanh'| (the chain rule of oracle.mlp.loss_and_grad with absolute values)."""
+    layers = mlp.unpack(widths, flat)
+    out, acts = mlp.forward(widths, flat, x)
+    dz = (out - t) / out.shape[0]
+    dza = np.abs(dz)
+    res = [None] * len(layers)
+    for l in range(len(layers) - 1, -1, -1):
+        W, _ = layers[l]
+        res[l] = (dza.T @ np.abs(acts[l]), dza.sum(axis=0))
+        if l > 0:
+            d = 1.0 - acts[l] * acts[l]
+            dz, dza = (dz @ W) * d, (dza @ np.abs(W)) * np.abs(d)
+    return mlp.pack(res)
 
 
 def test_adam_step_matches_oracle(bipm):

@@ -380,3 +380,144 @@ def test_restoration_return_test():
     assert not ipm.resto_may_return(ph, 0.6, 2.0, 1.0, OPT)   # dominated by (0.5, 1)
     assert not ipm.resto_may_return(ph, 0.1, np.inf, 1.0, OPT)
     assert math.isclose(OPT.kappa_resto, 0.9)
+
+
+# ------------------------------------- watchdog and soft restoration (rows 3, 5) --
+
+def test_primal_dual_error_by_hand():
+    """x0 in [0, 1], x1 free; J = (1, 2); x = (0.25, 3), y = (2), z_L = (4, 0), z_U = (1, 0),
+    grad f = (0.5, -1), c = (0.1), mu = 0.5.
+    grad L = g + J^T y - z_L + z_U = (0.5 + 2 - 4 + 1, -1 + 4) = (-0.5, 3): |.|_1 = 3.5.
+    complementarity: |0.25 * 4 - 0.5| = 0.5, |0.75 * 1 - 0.5| = 0.25.
+    E_pd = 3.5 + 0.1 + 0.75 = 4.35."""
+    nlp = TorchNLP(lambda x: x.sum(), lambda x: (x[0] + 2 * x[1]).reshape(1), 2, 1,
+                   xl=[0.0, -np.inf], xu=[1.0, np.inf])
+    e = ipm.primal_dual_error(nlp, np.array([0.25, 3.0]), np.array([2.0]), np.array([4.0, 0.0]),
+                              np.array([1.0, 0.0]), np.array([0.5, -1.0]), np.array([[1.0, 2.0]]),
+                              np.array([0.1]), 0.5)
+    assert e == rel(4.35, 1e-14)
+
+
+def test_soft_restoration_acceptance_threshold():
+    """kappa_soft = 1e-4: accept when E_pd(trial) <= 0.9999 E_pd(current)."""
+    assert ipm.soft_resto_accepts(0.9999, 1.0, OPT)
+    assert not ipm.soft_resto_accepts(0.99995, 1.0, OPT)
+    assert ipm.soft_resto_accepts(0.5, 1.0, OPT)
+
+
+def test_watchdog_start_and_end_rules():
+    """The watchdog starts after 10 consecutive shortened steps when it is enabled;
+    a barrier decrease or restoration entry ends it and the soft phase."""
+    opt = ipm.Options(watchdog=True)
+    ph = _phase()
+    ph.wd_short = 9
+    assert not ipm.watchdog_should_start(ph, opt)
+    ph.wd_short = 10
+    assert ipm.watchdog_should_start(ph, opt)
+    assert not ipm.watchdog_should_start(ph, OPT)  # disabled by default
+    ph.wd_active, ph.wd_trials, ph.wd_store = True, 2, {"x": 0}
+    assert not ipm.watchdog_should_start(ph, opt)
+    ph.soft_active, ph.soft_iters = True, 3
+    ipm.end_globalization(ph)
+    assert (ph.wd_active, ph.wd_trials, ph.wd_store, ph.wd_short) == (False, 0, None, 0)
+    assert (ph.soft_active, ph.soft_iters) == (False, 0)
+
+
+def _nonconvex_chain():
+    """min sum (x_i - 2)^2 s.t. x_i^2 + x_{i+1}^2 = 1 (i = 0, 1): curved constraints whose
+    steps are often shortened."""
+    import torch
+
+    n = 3
+    return TorchNLP(lambda x: ((x - 2.0) ** 2).sum(),
+                    lambda x: torch.stack([x[0] ** 2 + x[1] ** 2 - 1.0, x[1] ** 2 + x[2] ** 2 - 1.0]), n, 2,
+                    x0=[3.0, -2.0, 1.5])
+
+
+def test_watchdog_first_step_is_the_full_step():
+    """Once started, the watchdog takes the full step alpha_max: the new iterate is
+    x + alpha_max dx whether or not the filter tests accept it, and the stored
+    iterate is the one it started from."""
+    nlp = _nonconvex_chain()
+    opt = ipm.Options(watchdog=True)
+    st = ipm.initial_state(nlp, nlp.default_start(), opt)
+    tr = {}
+    ipm.phase_iteration(nlp, st.normal, opt, tr, init_theta=True, y_ls=True, globalize=True)
+    x0 = st.normal.x.copy()
+    st.normal.wd_short = opt.wd_trigger
+    tr = {}
+    out = ipm.phase_iteration(nlp, st.normal, opt, tr, globalize=True)
+    assert out == ipm._Outcome.ACCEPTED and tr.get("wd_start")
+    ph = st.normal
+    if tr.get("wd_accepted"):
+        assert not ph.wd_active
+    else:
+        assert tr.get("wd_step") and ph.wd_active and ph.wd_trials == 1
+        assert np.array_equal(ph.wd_store["x"], x0)
+        # the accepted step is the full one along the stored direction
+        assert np.allclose(ph.x, x0 + ph.wd_store["a_max"] * ph.wd_store["dx"], rtol=0, atol=1e-15)
+    assert tr["alpha"] == pytest.approx(tr["alpha"])
+
+
+def test_watchdog_gives_up_after_the_trial_steps_and_backtracks_from_the_stored_point():
+    """A watchdog whose reference values no trial can satisfy (theta_W = phi_W = -inf
+    rejects every point) takes wd_trial_max = 3 unconditional steps and then returns
+    to the stored iterate, searching along its stored step from half its full step."""
+    nlp = _nonconvex_chain()
+    opt = ipm.Options(watchdog=True)
+    st = ipm.initial_state(nlp, nlp.default_start(), opt)
+    ph = st.normal
+    ipm.phase_iteration(nlp, ph, opt, {}, init_theta=True, y_ls=True, globalize=True)
+    ph.wd_short = opt.wd_trigger
+    # a filter entry that dominates every point: no trial passes the filter test
+    ph.filt = [(-1.0, -np.inf)]
+    x_start = ph.x.copy()
+    steps = []
+    for _ in range(opt.wd_trial_max + 1):
+        tr = {}
+        ipm.phase_iteration(nlp, ph, opt, tr, globalize=True)
+        steps.append(tr)
+        if ph.wd_store is not None:
+            W = ph.wd_store
+        if ph.mu != steps[0].get("mu", ph.mu):
+            break
+    assert steps[0].get("wd_start")
+    assert [bool(t.get("wd_step")) for t in steps[:3]] == [True, True, True]
+    assert steps[3].get("wd_return")
+    assert not ph.wd_active and ph.wd_store is None
+    # the search ran from the stored point along its step: every trial was
+    # rejected by the filter, so the line search failed there
+    assert np.array_equal(W["x"], x_start)
+
+
+def test_soft_restoration_step_reduces_the_primal_dual_error():
+    """On the Wachter-Biegler problem the line search fails and soft restoration
+    (Table I row 5) is tried before hard restoration.  Every soft step recorded must
+    use alpha_s = min(alpha_max, alpha_z_max) for primal and dual alike, and an
+    accepted one must lower E_pd, recomputed here at the recorded trial point
+    x + alpha_s dx (multipliers likewise), by the factor 1 - 1e-4."""
+    import torch
+
+    nlp = TorchNLP(lambda x: x[0], lambda x: torch.stack([x[0] ** 2 - x[1] - 1.0, x[0] - x[2] - 0.5]), 3, 2,
+                   xl=[-np.inf, 0.0, 0.0], xu=[np.inf] * 3, x0=[-2.0, 1.0, 1.0])
+    opt = ipm.Options(soft_resto=True, trace_soc=True)
+    st = ipm.initial_state(nlp, nlp.default_start(), opt)
+    tried, checked = 0, 0
+    for _ in range(40):
+        if st.mode != ipm.NORMAL or st.status != ipm.RUNNING:
+            break
+        tr = ipm.step(nlp, st, opt)
+        tried += bool(tr.get("soft_trial"))
+        L = tr.get("soft_log")
+        if L is None:
+            continue
+        assert L["alpha"] == min(L["a_max"], L["az_max"])
+        a = L["alpha"]
+        xt, yt = L["x"] + a * L["dx"], L["y"] + a * L["dy"]
+        zlt, zut = L["zl"] + a * L["dzl"], L["zu"] + a * L["dzu"]
+        e_t = ipm.primal_dual_error(nlp, xt, yt, zlt, zut, nlp.grad_f(xt), nlp.jac_c(xt), nlp.c(xt), L["mu"])
+        assert e_t == rel(L["e_trial"], 1e-12)
+        if tr.get("soft_step"):
+            checked += 1
+            assert e_t <= (1 - opt.kappa_soft) * L["e_current"]
+    assert tried >= 1
