@@ -461,7 +461,7 @@ def mixed_leg(args, dev, stream, barrier, reduce, MAX, SUM):
 
     ws, rank, _ = dist_env()
     Q, S = args.mixed, args.mixed_slots
-    classes, cls, theta = make_mixed(Q, first_id=rank * Q)
+    classes, cls, theta = make_mixed(Q, max_quads=args.mixed_max_quads, first_id=rank * Q)
     th = torch.as_tensor(theta, device=dev)
     rsize = bipm.RESULT_DTYPE.itemsize
     opts = bipm.Options(precision=1, fp32_switch=-1.0)
@@ -485,14 +485,16 @@ def mixed_leg(args, dev, stream, barrier, reduce, MAX, SUM):
     r_sl, dt_sl = run(S)
     conv = r["status"] == bipm.CONVERGED
     per_nq = {}
-    for nq in range(1, 9):
+    for nq in range(1, args.mixed_max_quads + 1):
         sel = np.array([classes[k].nq == nq for k in cls])
+        if not sel.any():
+            continue
         per_nq[str(nq)] = {"problems": int(sel.sum()), "converged_frac": float(conv[sel].mean()),
                            "iters_mean": float(r["iters"][sel].mean())}
     ilb = reduce(float(conv.sum()), SUM) / dt
     slb = reduce(float(np.sum(r_sl["status"] == bipm.CONVERGED)), SUM) / dt_sl
-    return {"workload": f"uneven queue: {Q} problems, 1-8 quadrotors (pairwise distance 0.4; one sphere for a "
-                        f"single quadrotor), N in 10/20/30/50, {S} slots",
+    return {"workload": f"uneven queue: {Q} problems, 1-{args.mixed_max_quads} quadrotors (pairwise distance "
+                        f"0.4; one sphere for a single quadrotor), N in 10/20/30/50, {S} slots",
             "value": ilb, "unit": UNIT, "seconds": dt,
             "solve_level_batching": {"value": slb, "unit": UNIT, "seconds": dt_sl,
                                      "batches": int(math.ceil(Q / S))},
@@ -737,9 +739,11 @@ def main():
     ap.add_argument("--warm-train", type=int, default=16384, help="training problems of the warm-start leg")
     ap.add_argument("--warm-epochs", type=int, default=30)
     ap.add_argument("--warm-batch", type=int, default=16384, help="problems of the warm-start leg")
-    ap.add_argument("--mixed", type=int, default=512, help="problems of the uneven-queue leg (0: skip)")
-    ap.add_argument("--mixed-slots", type=int, default=256, help="slots of the uneven-queue leg")
-    ap.add_argument("--multi", type=int, default=1024, help="problems of the four-quadrotor leg (0: skip)")
+    ap.add_argument("--mixed", type=int, default=192, help="problems of the uneven-queue leg (0: skip)")
+    ap.add_argument("--mixed-slots", type=int, default=96, help="slots of the uneven-queue leg")
+    ap.add_argument("--mixed-max-quads", type=int, default=4,
+                    help="largest quadrotor count of the uneven-queue leg (the workload's own range is 1-8)")
+    ap.add_argument("--multi", type=int, default=256, help="problems of the four-quadrotor leg (0: skip)")
     ap.add_argument("--repeats", type=int, default=3, help="timed regions per form (median reported)")
     ap.add_argument("--no-schedule-tune", action="store_true", help="autotune the precision form only")
     args = ap.parse_args()

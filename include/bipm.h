@@ -134,7 +134,27 @@ typedef struct {
   int warps_per_sm;   /* resident warps per SM of the warp-team kernels: 4, 8,
                          ..., 24 (default 24, the most that fit) */
   int team_threads;   /* threads of a block team: 128 or 256 (default 256) */
-  int reserved_[3];   /* must be 0 */
+  /* Globalisation branches of Table I for the original problem (off = 0):
+   * watchdog (row 3): after 10 consecutive shortened steps the full step is
+   * taken for up to 3 iterations, judged against the iterate where it started,
+   * and if none becomes acceptable the iterate returns there and backtracks
+   * along its step; soft restoration (row 5): when the line search fails, a
+   * primal-dual step that reduces the barrier problem's primal-dual error
+   * |grad L|_1 + |c|_1 + |S z - mu|_1 by the factor 1 - 1e-4 is taken, for at
+   * most 10 iterations, until a step passes the original tests; else hard
+   * restoration follows. */
+  int watchdog;
+  int soft_resto;
+  /* Barrier update (Table I row 7): 0 monotone (mu falls once the barrier
+   * problem is solved, E_mu <= 10 mu); 1 adaptive: free mode sets mu every
+   * iteration by LOQO's centrality rule, mu = 0.1 min(0.05 (1 - xi)/xi, 2)^3 *
+   * (average complementarity), xi = min / average complementarity, within
+   * [1e-11, 1e3 * the starting average], while the optimality error E_0 keeps
+   * falling below 0.9999 times the largest of its last four values; without that
+   * progress (or after a tiny step) the monotone rule takes over from 0.8 times
+   * the average complementarity, until a solved barrier problem with progress
+   * returns to free mode.  Restoration always uses the monotone rule. */
+  int mu_strategy;
 } bipm_options;
 
 /* Per-slot outcome and counters: the branches of Table I each problem took
@@ -214,6 +234,28 @@ typedef struct {
   int n_filter_r;
   double mu, dw_last, theta_max, theta_min;
   double mu_r, dw_last_r, theta_max_r, theta_min_r, zeta, theta_ref;
+  /* watchdog and soft restoration state (original problem; meaningful when the
+   * options enable them): the iterate stored when the watchdog started and its
+   * step, counters, and the stored iterate's reference values */
+  double* wd_x;     /* n */
+  double* wd_y;     /* m */
+  double* wd_zl;    /* n */
+  double* wd_zu;    /* n */
+  double* wd_dx;    /* n   primal step at the stored iterate */
+  double* wd_dy;    /* m   multiplier step */
+  int wd_short;     /* consecutive shortened steps */
+  int wd_active;
+  int wd_trials;    /* unconditional watchdog steps taken */
+  int soft_active;
+  int soft_iters;   /* soft restoration steps in the current soft phase */
+  int reserved_wd;
+  double wd_theta, wd_phi, wd_gdx, wd_amax, wd_amin;
+  /* adaptive barrier update: free mode flag, the reference values of E_0 and
+   * the cap of mu */
+  int mu_free;
+  int n_refs;       /* 0..4 */
+  double mu_refs[4];
+  double mu_max;
 } bipm_iterate;
 
 /* Creates a batch of `capacity` slots for problems of structure `desc` (the

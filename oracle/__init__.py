@@ -9,13 +9,15 @@ one problem at a time:
 
 * ``quadrotor``  - the multiple-shooting NMPC transcription of the quadrotor
   problems (problem form of Eq. 1, inequalities through slacks), written as
-  plain PyTorch CPU functions; derivatives come from PyTorch autograd on the
-  whole decision vector (a library primitive), never from hand-written code.
+  plain PyTorch CPU functions; derivatives come from PyTorch autograd (a library
+  primitive) of the stage functions, assembled into the full Jacobian and
+  Lagrangian Hessian, never from hand-written code.
 * ``ipm``        - the primal-dual interior-point iteration the paper reviews
   in Sec. IV (barrier Eq. 3, Lagrangian Eq. 4, optimality conditions Eq. 5,
   Newton system Eq. 6 reduced to the augmented system Eq. 7, inertia
   correction, and the branches of Table I: backtracking filter line search,
-  second-order correction, tiny step, hard feasibility restoration and the
+  second-order correction, watchdog and soft feasibility restoration (both
+  optional, off by default), tiny step, hard feasibility restoration and the
   monotone barrier update).  The details the paper defers to the IPOPT paper
   (Wachter & Biegler 2006) follow that paper's algorithm as read in the design
   notes.  Linear algebra is the dense full-space augmented matrix factorised

@@ -14,11 +14,12 @@ This follows the paper's review of IPOPT (Sec. IV) step by step:
   symmetric indefinite LDL^T whose inertia is checked and corrected by the
   regularisation delta_x I (text after Eq. 7; IPOPT's Algorithm IC);
 * the branches of Table I: (1) backtracking filter line search,
-  (2) second-order correction, (4) tiny step, (6) hard feasibility
-  restoration (a nested interior-point solve of the l1 restoration problem;
-  a restoration inside restoration is reported as a failure), and
-  (7) the monotone barrier update.  The watchdog (3), soft restoration (5) and
-  the adaptive barrier rule are not part of this method.
+  (2) second-order correction, (3) the watchdog and (5) soft feasibility
+  restoration (options, off by default; the original problem only),
+  (4) tiny step, (6) hard feasibility restoration (a nested interior-point
+  solve of the l1 restoration problem; a restoration inside restoration is
+  reported as a failure), and (7) the monotone barrier update.  The adaptive
+  barrier rule is not part of this method.
 
 Every constant is IPOPT's published default as listed in ``Options``.
 One call of ``step`` is one iteration; the complete state between iterations
@@ -85,6 +86,14 @@ class Options:
     soft_resto: bool = False
     kappa_soft: float = 1e-4  # required relative decrease of the primal-dual error
     soft_max: int = 10        # soft restoration steps before hard restoration
+    # barrier update (Table I row 7): "monotone" (Fiacco-McCormick) or "adaptive"
+    # (free mode with the LOQO centrality rule, monotone fallback)
+    mu_strategy: str = "monotone"
+    mu_min_adaptive: float = 1e-11   # floor of mu in free mode
+    mu_max_fact: float = 1e3         # mu <= mu_max_fact * (average complementarity at the start)
+    refs_red_fact: float = 0.9999    # required reduction of E_0 against the reference values
+    num_refs_max: int = 4            # reference values kept
+    mu_monotone_init: float = 0.8    # fixed mode starts at this fraction of the average complementarity
 
 
 @dataclasses.dataclass
@@ -110,6 +119,10 @@ class Phase:
     # soft restoration: active flag and soft steps taken in the current phase
     soft_active: bool = False
     soft_iters: int = 0
+    # adaptive barrier update: free mode flag, reference values of E_0 and the cap of mu
+    mu_free: bool = True
+    mu_refs: list = dataclasses.field(default_factory=list)
+    mu_max: float = 0.0
 
 
 @dataclasses.dataclass
@@ -325,6 +338,65 @@ def barrier_update(mu, err_at, tiny, opt):
             tiny = False
             continue
         return mu, decreased, False
+
+
+def complementarity_stats(nlp, x, zl, zu):
+    """(average, minimum) of the complementarity products s_i z_i over all bounds."""
+    has_l, has_u = bound_sets(nlp)
+    sl, su = slacks(nlp, x)
+    prod = np.concatenate([sl[has_l] * zl[has_l], su[has_u] * zu[has_u]])
+    if prod.size == 0:
+        return 0.0, 0.0
+    return float(np.mean(prod)), float(np.min(prod))
+
+
+def loqo_mu(avg, minimum):
+    """LOQO's centrality rule (Vanderbei & Shanno): mu = sigma * average
+    complementarity with sigma = 0.1 min(0.05 (1 - xi) / xi, 2)^3, xi = min / average."""
+    if avg <= 0.0:
+        return 0.0
+    xi = minimum / avg
+    t = min(0.05 * (1.0 - xi) / xi, 2.0) if xi > 0 else 2.0
+    return 0.1 * t * t * t * avg
+
+
+def sufficient_progress(err, refs, opt):
+    """Free-mode progress: E_0 at most refs_red_fact times the largest of the stored
+    reference values (no reference yet counts as progress)."""
+    return not refs or err <= opt.refs_red_fact * max(refs)
+
+
+def remember_reference(refs, err, opt):
+    """Append E_0 of an accepted free-mode iterate; keep the last num_refs_max."""
+    refs.append(err)
+    if len(refs) > opt.num_refs_max:
+        refs.pop(0)
+
+
+def adaptive_barrier_update(ph, err0, err_at, avg, minimum, tiny, opt):
+    """Adaptive barrier update (Table I row 7).  Free mode: mu = max(mu_min, min(mu_max,
+    LOQO(x))) every iteration while E_0 keeps falling (sufficient_progress); without
+    progress, or after a tiny step, the fixed (monotone) mode starts at mu =
+    mu_monotone_init * average complementarity.  Fixed mode: the monotone rule, except
+    that once the barrier problem is solved (E_mu <= kappa_eps mu) with progress of
+    E_0 against the references, free mode resumes.  Returns (mu, changed, stalled)."""
+    mu_old = ph.mu
+    if ph.mu_free:
+        if sufficient_progress(err0, ph.mu_refs, opt) and not tiny:
+            remember_reference(ph.mu_refs, err0, opt)
+            mu = max(opt.mu_min_adaptive, min(ph.mu_max, loqo_mu(avg, minimum)))
+            return mu, mu != mu_old, False
+        ph.mu_free = False
+        mu = max(opt.tol / 10.0, opt.mu_monotone_init * avg)
+        return mu, mu != mu_old, False
+    # fixed mode
+    if err_at(ph.mu) <= opt.kappa_eps * ph.mu and sufficient_progress(err0, ph.mu_refs, opt):
+        ph.mu_free = True
+        ph.mu_refs = [err0]
+        mu = max(opt.mu_min_adaptive, min(ph.mu_max, loqo_mu(avg, minimum)))
+        return mu, mu != mu_old, False
+    mu, decreased, stalled = barrier_update(ph.mu, err_at, tiny, opt)
+    return mu, decreased, stalled
 
 
 # ------------------------------------------------- inertia correction --
@@ -570,9 +642,20 @@ def phase_iteration(nlp, ph: Phase, opt: Options, trace: dict, init_theta=False,
     if opt_error(nlp, x, y, zl, zu, g, J, c, 0.0, opt) <= opt.tol:
         return _Outcome.CONVERGED
 
-    # monotone barrier update (Table I row 7), repeated while the subproblem is solved
-    mu_new, decreased, stalled = barrier_update(
-        ph.mu, lambda mu: opt_error(nlp, x, y, zl, zu, g, J, c, mu, opt), ph.tiny, opt)
+    # barrier update (Table I row 7): monotone, repeated while the subproblem is
+    # solved; or adaptive (free mode with the monotone fallback) on the original problem
+    err_at = lambda mu: opt_error(nlp, x, y, zl, zu, g, J, c, mu, opt)  # noqa: E731
+    if globalize and opt.mu_strategy == "adaptive":
+        avg, minimum = complementarity_stats(nlp, x, zl, zu)
+        if ph.mu_max == 0.0:
+            ph.mu_max = opt.mu_max_fact * max(avg, opt.tol)
+        was_free = ph.mu_free
+        mu_new, decreased, stalled = adaptive_barrier_update(ph, err_at(0.0), err_at, avg, minimum, ph.tiny, opt)
+        trace["mu_free"] = ph.mu_free
+        if was_free != ph.mu_free:
+            trace["mu_mode_switch"] = True
+    else:
+        mu_new, decreased, stalled = barrier_update(ph.mu, err_at, ph.tiny, opt)
     if stalled:
         return _Outcome.TINY_STALL
     if decreased:

@@ -36,7 +36,7 @@ class OptionsC(ctypes.Structure):
                 ("warm_bound_push", ctypes.c_double), ("warm_max_iter", ctypes.c_int),
                 ("time_limit_ms", ctypes.c_int), ("visit_cap", ctypes.c_int),
                 ("warps_per_sm", ctypes.c_int), ("team_threads", ctypes.c_int),
-                ("reserved_", ctypes.c_int * 3)]
+                ("watchdog", ctypes.c_int), ("soft_resto", ctypes.c_int), ("mu_strategy", ctypes.c_int)]
 
 
 class StatsC(ctypes.Structure):
@@ -80,7 +80,14 @@ class IterateC(ctypes.Structure):
                 ("theta_max", ctypes.c_double), ("theta_min", ctypes.c_double),
                 ("mu_r", ctypes.c_double), ("dw_last_r", ctypes.c_double),
                 ("theta_max_r", ctypes.c_double), ("theta_min_r", ctypes.c_double),
-                ("zeta", ctypes.c_double), ("theta_ref", ctypes.c_double)]
+                ("zeta", ctypes.c_double), ("theta_ref", ctypes.c_double),
+                ("wd_x", _DP), ("wd_y", _DP), ("wd_zl", _DP), ("wd_zu", _DP), ("wd_dx", _DP), ("wd_dy", _DP),
+                ("wd_short", ctypes.c_int), ("wd_active", ctypes.c_int), ("wd_trials", ctypes.c_int),
+                ("soft_active", ctypes.c_int), ("soft_iters", ctypes.c_int), ("reserved_wd", ctypes.c_int),
+                ("wd_theta", ctypes.c_double), ("wd_phi", ctypes.c_double), ("wd_gdx", ctypes.c_double),
+                ("wd_amax", ctypes.c_double), ("wd_amin", ctypes.c_double),
+                ("mu_free", ctypes.c_int), ("n_refs", ctypes.c_int), ("mu_refs", ctypes.c_double * 4),
+                ("mu_max", ctypes.c_double)]
 
 
 EXPORTS = ["bipm_create_batch", "bipm_dims", "bipm_set_problems", "bipm_set_initial_guess",
@@ -213,12 +220,15 @@ class Options:
     visit_cap: int = 0            # queue iterations before a straggler is parked (0: 96)
     warps_per_sm: int = 0         # resident warps per SM, 4..24 in steps of 4 (0: 24)
     team_threads: int = 0         # block-team threads, 128 or 256 (0: 256)
+    watchdog: int = 0             # Table I row 3 on the original problem (0 off, 1 on)
+    soft_resto: int = 0           # Table I row 5 on the original problem (0 off, 1 on)
+    mu_strategy: int = 0          # Table I row 7: 0 monotone, 1 adaptive (free mode, monotone fallback)
 
     def to_c(self):
         return OptionsC(self.tol, self.max_iter, self.mu_init, self.precision, self.schedule,
                         self.fp32_switch, self.warm_mu_init, self.warm_bound_push, self.warm_max_iter,
                         self.time_limit_ms, self.visit_cap, self.warps_per_sm, self.team_threads,
-                        (ctypes.c_int * 3)(0, 0, 0))
+                        self.watchdog, self.soft_resto, self.mu_strategy)
 
 
 def _stream_ptr(stream):
@@ -350,8 +360,8 @@ class Batch:
 
     def get_iterate(self, slot: int) -> dict:
         n, m = self.n, self.m
-        bufs = {k: np.zeros(n) for k in ("x", "zl", "zu", "x_ref")}
-        bufs.update({k: np.zeros(m) for k in ("y", "p", "nn", "zp", "zn")})
+        bufs = {k: np.zeros(n) for k in ("x", "zl", "zu", "x_ref", "wd_x", "wd_zl", "wd_zu", "wd_dx")}
+        bufs.update({k: np.zeros(m) for k in ("y", "p", "nn", "zp", "zn", "wd_y", "wd_dy")})
         bufs["filter"] = np.zeros(2 * FILTER_CAP)
         bufs["filter_r"] = np.zeros(2 * FILTER_CAP)
         it = IterateC()
@@ -362,6 +372,7 @@ class Batch:
         for f, _ in IterateC._fields_:
             if f not in bufs:
                 out[f] = getattr(it, f)
+        out["mu_refs"] = list(out["mu_refs"])[: out["n_refs"]]
         out["filter"] = out["filter"][: 2 * out["n_filter"]].reshape(-1, 2)
         out["filter_r"] = out["filter_r"][: 2 * out["n_filter_r"]].reshape(-1, 2)
         return out
@@ -370,7 +381,8 @@ class Batch:
         it = IterateC()
         keep = []
         n, m = self.n, self.m
-        sizes = {"x": n, "zl": n, "zu": n, "x_ref": n, "y": m, "p": m, "nn": m, "zp": m, "zn": m}
+        sizes = {"x": n, "zl": n, "zu": n, "x_ref": n, "y": m, "p": m, "nn": m, "zp": m, "zn": m,
+                 "wd_x": n, "wd_zl": n, "wd_zu": n, "wd_dx": n, "wd_y": m, "wd_dy": m}
         for k, ln in sizes.items():
             v = state.get(k)
             if v is None:
@@ -388,9 +400,14 @@ class Batch:
             setattr(it, k, f.ctypes.data_as(_DP))
             setattr(it, nk, int(src.size // 2))
         for f, _ in IterateC._fields_:
-            if f in sizes or f in ("filter", "filter_r", "n_filter", "n_filter_r"):
+            if f in sizes or f in ("filter", "filter_r", "n_filter", "n_filter_r", "mu_refs", "n_refs"):
                 continue
             setattr(it, f, state.get(f, 0))
+        refs = list(state.get("mu_refs", []))
+        it.n_refs = len(refs)
+        it.mu_refs = (ctypes.c_double * 4)(*(refs + [0.0] * (4 - len(refs))))
+        if "mu_free" not in state:
+            it.mu_free = 1
         _check(self.lib.bipm_set_iterate(self.h, slot, ctypes.byref(it)))
 
 

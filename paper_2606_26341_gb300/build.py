@@ -19,8 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIBNAME = "libbipm.so"
-UNITS = ["bipm.cu", "kernels_f64.cu", "kernels_f32.cu", "kernels_f64_block.cu", "kernels_f32_block.cu",
-         "kernels_df.cu", "kernels_df_block.cu", "noalloc.cu", "mlp.cu", "warm.cu"]
+UNITS = ["bipm.cu", "noalloc.cu", "mlp.cu", "warm.cu"] + [
+    f"kernels_{form}{part}{spec}.cu" for form in ("f64", "f32", "df") for part in ("", "_block") for spec in ("", "_q1")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + INCLUDE]

@@ -37,6 +37,12 @@ namespace bipm {
 // records the message bipm_last_error() returns (used by every entry point)
 void set_last_error(const std::string& msg) { g_err = msg; }
 
+void* queue_kernel_ptr(int precision, int nq) {
+  if (nq == 1)
+    return precision == 2 ? queue_kernel_df_q1() : precision ? queue_kernel_f32_q1() : queue_kernel_f64_q1();
+  return precision == 2 ? queue_kernel_df() : precision ? queue_kernel_f32() : queue_kernel_f64();
+}
+
 bipm_options default_options() {
   bipm_options o;
   std::memset(&o, 0, sizeof(o));
@@ -98,7 +104,9 @@ int options_from(const bipm_options* opt, bipm_options* o_out, Options* dev) {
   if (o.warps_per_sm < kWarpsPerBlock || o.warps_per_sm > 24 || o.warps_per_sm % kWarpsPerBlock)
     return fail(BIPM_EINVAL, "warps_per_sm must be a multiple of 4 in 4..24");
   if (o.team_threads != 128 && o.team_threads != 256) return fail(BIPM_EINVAL, "team_threads must be 128 or 256");
-  if (o.reserved_[0] || o.reserved_[1] || o.reserved_[2]) return fail(BIPM_EINVAL, "reserved options must be 0");
+  if (o.mu_strategy != 0 && o.mu_strategy != 1) return fail(BIPM_EINVAL, "mu_strategy must be 0 or 1");
+  if ((o.watchdog != 0 && o.watchdog != 1) || (o.soft_resto != 0 && o.soft_resto != 1))
+    return fail(BIPM_EINVAL, "watchdog and soft_resto must be 0 or 1");
   dev->tol = o.tol;
   dev->max_iter = o.max_iter;
   dev->mu_init = o.mu_init;
@@ -107,6 +115,9 @@ int options_from(const bipm_options* opt, bipm_options* o_out, Options* dev) {
   dev->warm_mu = o.warm_mu_init;
   dev->warm_push = o.warm_bound_push;
   dev->warm_max_iter = std::min(o.warm_max_iter, o.max_iter);
+  dev->watchdog = o.watchdog;
+  dev->soft_resto = o.soft_resto;
+  dev->mu_strategy = o.mu_strategy;
   *o_out = o;
   return 0;
 }
@@ -187,6 +198,14 @@ Layout make_layout(const Dims& d, int precision) {
   L.rct = take(m);
   L.filt = take(2 * (kFilterCap + 1));  // one spare entry: a full filter appends before dropping
   L.filt_r = take(2 * (kFilterCap + 1));
+  L.wd_x = take(L.nw);
+  L.wd_zl = take(L.nw);
+  L.wd_zu = take(L.nw);
+  L.wd_y = take(m);
+  L.wd_dir = take(L.nk);
+  L.sft_g = take(L.nw);
+  L.sft_j = take(L.nw);
+  L.sft_y = take(m);
   // factor region layout (element offsets)
   long long fo = 0;
   auto ftake = [&](long long len) {
@@ -230,17 +249,19 @@ __global__ void gather_kernel(const Params* __restrict__ P, int first, int count
 }
 
 // ------------------------------------------------------------- host helpers
-void* iter_kernel_ptr(int precision) {
+// kernel entry points of a precision form; problems of one quadrotor take the
+// instantiation whose sizes are compile-time constants
+void* iter_kernel_ptr(int precision, int nq) {
+  if (nq == 1) return precision == 2 ? iter_kernel_df_q1() : precision ? iter_kernel_f32_q1() : iter_kernel_f64_q1();
   return precision == 2 ? iter_kernel_df() : precision ? iter_kernel_f32() : iter_kernel_f64();
 }
 void* init_kernel_ptr(int precision) {
   return precision == 2 ? init_kernel_df() : precision ? init_kernel_f32() : init_kernel_f64();
 }
-void* block_kernel_ptr(int precision) {
+void* block_kernel_ptr(int precision, int nq) {
+  if (nq == 1)
+    return precision == 2 ? block_kernel_df_q1() : precision ? block_kernel_f32_q1() : block_kernel_f64_q1();
   return precision == 2 ? block_kernel_df() : precision ? block_kernel_f32() : block_kernel_f64();
-}
-void* queue_kernel_ptr(int precision) {
-  return precision == 2 ? queue_kernel_df() : precision ? queue_kernel_f32() : queue_kernel_f64();
 }
 
 int check_slots(const bipm_batch* b, int first, int count) {
@@ -292,7 +313,7 @@ int run_iterations(bipm_batch* b, int n_iter) {
     int cap = (n_iter > 0 || b->schedule == 1) ? 0 : kBulkVisit;
     CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
     void* args[] = {&b->dparams, &n_iter, &cap};
-    CUDA_TRY(cudaLaunchKernel(iter_kernel_ptr(b->opt.precision), dim3(b->blocks),
+    CUDA_TRY(cudaLaunchKernel(iter_kernel_ptr(b->opt.precision, b->d.nq), dim3(b->blocks),
                               dim3(32 * kWarpsPerBlock), args,
                               (size_t)b->smem_per_warp * kWarpsPerBlock, b->stream));
   }
@@ -300,7 +321,7 @@ int run_iterations(bipm_batch* b, int n_iter) {
     // block teams: the long-running remainder, to termination
     CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
     void* args2[] = {&b->dparams, &n_iter};
-    CUDA_TRY(cudaLaunchKernel(block_kernel_ptr(b->opt.precision), dim3(b->block_blocks),
+    CUDA_TRY(cudaLaunchKernel(block_kernel_ptr(b->opt.precision, b->d.nq), dim3(b->block_blocks),
                               dim3(b->team_threads), args2, (size_t)b->smem_per_warp + 128,
                               b->stream));
   }
@@ -394,11 +415,11 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
     return cleanup(BIPM_ECUDA, "params copy");
 
   // persistent grid: as many resident blocks as fit, capped by the work
-  void* kfn = iter_kernel_ptr(o.precision);
+  void* kfn = iter_kernel_ptr(o.precision, d.nq);
   size_t smem = (size_t)b->smem_per_warp * kWarpsPerBlock;
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(queue_kernel_ptr(o.precision), cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(queue_kernel_ptr(o.precision, d.nq), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return cleanup(BIPM_ECUDA, "shared memory attribute");
   }
@@ -415,7 +436,7 @@ int bipm_create_batch(const bipm_problem_desc* desc, int capacity, const bipm_op
   b->blocks = std::max(1, std::min(need, sms * per_sm));
   b->team_threads = o.team_threads;
   {
-    void* bfn = block_kernel_ptr(o.precision);
+    void* bfn = block_kernel_ptr(o.precision, d.nq);
     size_t bsm = (size_t)b->smem_per_warp + 128;
     if (bsm > 48 * 1024 &&
         cudaFuncSetAttribute(bfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm) != cudaSuccess)
@@ -564,14 +585,14 @@ static int solve_queue_impl(bipm_batch* b, const double* theta_queue, const doub
     CUDA_TRY(cudaGetLastError());
   }
   void* args[] = {&b->dparams, &th_dev, &n_queue, &warps, &x_dev, &r_dev, &g_dev};
-  CUDA_TRY(cudaLaunchKernel(queue_kernel_ptr(b->opt.precision), dim3(blocks), dim3(32 * kWarpsPerBlock),
+  CUDA_TRY(cudaLaunchKernel(queue_kernel_ptr(b->opt.precision, b->d.nq), dim3(blocks), dim3(32 * kWarpsPerBlock),
                             args, (size_t)b->smem_per_warp * kWarpsPerBlock, b->stream));
   if (spares) {
     // block teams finish the parked stragglers, then their results go out
     int n_iter = 0;
     CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
     void* args2[] = {&b->dparams, &n_iter};
-    CUDA_TRY(cudaLaunchKernel(block_kernel_ptr(b->opt.precision), dim3(b->block_blocks), dim3(b->team_threads),
+    CUDA_TRY(cudaLaunchKernel(block_kernel_ptr(b->opt.precision, b->d.nq), dim3(b->block_blocks), dim3(b->team_threads),
                               args2, (size_t)b->smem_per_warp + 128, b->stream));
     queue_writeout<<<(b->capacity * 32 + 255) / 256, 256, 0, b->stream>>>(b->dparams, x_dev, r_dev);
     CUDA_TRY(cudaGetLastError());
@@ -894,6 +915,27 @@ int bipm_get_iterate(const bipm_batch* b, int slot, bipm_iterate* out) {
   out->theta_min_r = s.theta_min_r;
   out->zeta = s.zeta;
   out->theta_ref = s.theta_ref;
+  put(out->wd_x, L.wd_x, d.n);
+  put(out->wd_y, L.wd_y, d.m);
+  put(out->wd_zl, L.wd_zl, d.n);
+  put(out->wd_zu, L.wd_zu, d.n);
+  put(out->wd_dx, L.wd_dir, d.n);
+  put(out->wd_dy, L.wd_dir + L.nw, d.m);
+  out->wd_short = s.wd_short;
+  out->wd_active = s.wd_active;
+  out->wd_trials = s.wd_trials;
+  out->soft_active = s.soft_active;
+  out->soft_iters = s.soft_iters;
+  out->reserved_wd = 0;
+  out->wd_theta = s.wd_theta;
+  out->wd_phi = s.wd_phi;
+  out->wd_gdx = s.wd_gdx;
+  out->wd_amax = s.wd_amax;
+  out->wd_amin = s.wd_amin;
+  out->mu_free = s.mu_free;
+  out->n_refs = s.n_refs;
+  for (int i = 0; i < 4; ++i) out->mu_refs[i] = s.mu_refs[i];
+  out->mu_max = s.mu_max;
   return 0;
 }
 
@@ -928,6 +970,12 @@ int bipm_set_iterate(bipm_batch* b, int slot, const bipm_iterate* in) {
   get(in->x_ref, L.xr, d.n);
   get(in->filter, L.filt, 2 * kFilterCap);
   get(in->filter_r, L.filt_r, 2 * kFilterCap);
+  get(in->wd_x, L.wd_x, d.n);
+  get(in->wd_y, L.wd_y, d.m);
+  get(in->wd_zl, L.wd_zl, d.n);
+  get(in->wd_zu, L.wd_zu, d.n);
+  get(in->wd_dx, L.wd_dir, d.n);
+  get(in->wd_dy, L.wd_dir + L.nw, d.m);
   CUDA_TRY(cudaMemcpy(base, buf.data(), L.slot_f64 * sizeof(double), cudaMemcpyHostToDevice));
   SlotState s;
   CUDA_TRY(cudaMemcpy(&s, b->st + slot, sizeof(s), cudaMemcpyDeviceToHost));
@@ -950,6 +998,21 @@ int bipm_set_iterate(bipm_batch* b, int slot, const bipm_iterate* in) {
   s.theta_min_r = in->theta_min_r;
   s.zeta = in->zeta;
   s.theta_ref = in->theta_ref;
+  s.wd_short = in->wd_short;
+  s.wd_active = in->wd_active;
+  s.wd_trials = in->wd_trials;
+  s.soft_active = in->soft_active;
+  s.soft_iters = in->soft_iters;
+  s.wd_theta = in->wd_theta;
+  s.wd_phi = in->wd_phi;
+  s.wd_gdx = in->wd_gdx;
+  s.wd_amax = in->wd_amax;
+  s.wd_amin = in->wd_amin;
+  if (in->n_refs < 0 || in->n_refs > kNumRefs) return fail(BIPM_EINVAL, "n_refs outside 0..4");
+  s.mu_free = in->mu_free;
+  s.n_refs = in->n_refs;
+  for (int i = 0; i < kNumRefs; ++i) s.mu_refs[i] = in->mu_refs[i];
+  s.mu_max = in->mu_max;
   CUDA_TRY(cudaMemcpy(b->st + slot, &s, sizeof(s), cudaMemcpyHostToDevice));
   return 0;
 }

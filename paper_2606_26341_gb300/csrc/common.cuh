@@ -89,6 +89,9 @@ struct Options {
   double warm_mu;      // mu_0 of a warm start
   double warm_push;    // bound push and fraction of a warm start
   int warm_max_iter;   // iteration budget of a warm-started run
+  int watchdog;        // Table I row 3 on the original problem
+  int soft_resto;      // Table I row 5 on the original problem
+  int mu_strategy;     // 0 monotone, 1 adaptive (Table I row 7)
 };
 
 // IPOPT constants (Wachter & Biegler 2006 defaults)
@@ -104,6 +107,13 @@ constexpr double kBoundPush = 1e-2, kBoundFrac = 1e-2, kYmax = 1e3;
 constexpr double kRho = 1000.0, kKappaResto = 0.9;
 constexpr int kFilterCap = 64;
 constexpr int kLsMaxTrials = 60;
+constexpr int kWdTrigger = 10, kWdTrialMax = 3;  // watchdog: shortened steps, unconditional steps
+constexpr double kKappaSoft = 1e-4;              // soft restoration: required error reduction
+constexpr int kSoftMax = 10;                     // soft restoration steps per soft phase
+// adaptive barrier update: free-mode floor, cap factor, progress factor, references,
+// and the fixed mode's start as a fraction of the average complementarity
+constexpr double kMuMinFree = 1e-11, kMuMaxFact = 1e3, kRefsRedFact = 0.9999, kMuMonoInit = 0.8;
+constexpr int kNumRefs = 4;
 constexpr int kIrMaxSteps = 10;
 constexpr double kIrTol = 1e-10;
 constexpr int kGmresM = 6;        // Krylov dimension per restart
@@ -135,21 +145,38 @@ struct Dims {
   int th_x, th_ref, th_sph, th_cyl;
 };
 
+// Dims with the per-quadrotor sizes fixed at compile time: NQ quadrotors per
+// problem (12 states, 4 inputs each); NQ = 0 keeps the runtime fields.  The
+// static members hide the base fields of the same name, so code written
+// against `d.nx` gets a constant in the specialised kernels.
+template <int NQ>
+struct DimsT : Dims {
+  static constexpr int nq = NQ, nx = 12 * NQ, nu = 4 * NQ;
+};
+template <>
+struct DimsT<0> : Dims {};
+
 // primal offset of x_k, u_k, s_k inside one problem's variable vector
-__device__ __forceinline__ int off_x(const Dims& d, int k) {
+template <class D>
+__device__ __forceinline__ int off_x(const D& d, int k) {
   return k == 0 ? 0 : (d.nx + d.nu) + (k - 1) * (d.nx + d.nu + d.ni);
 }
-__device__ __forceinline__ int off_u(const Dims& d, int k) { return off_x(d, k) + d.nx; }
-__device__ __forceinline__ int off_s(const Dims& d, int k) {  // k >= 1
+template <class D>
+__device__ __forceinline__ int off_u(const D& d, int k) { return off_x(d, k) + d.nx; }
+template <class D>
+__device__ __forceinline__ int off_s(const D& d, int k) {  // k >= 1
   return off_x(d, k) + d.nx + (k < d.N ? d.nu : 0);
 }
 // equality rows: init block [0, nx), then per k: dynamics (nx) then inequalities (ni)
-__device__ __forceinline__ int row_dyn(const Dims& d, int k) { return d.nx + k * (d.nx + d.ni); }
-__device__ __forceinline__ int row_ineq(const Dims& d, int k) {  // inequalities of stage k >= 1
+template <class D>
+__device__ __forceinline__ int row_dyn(const D& d, int k) { return d.nx + k * (d.nx + d.ni); }
+template <class D>
+__device__ __forceinline__ int row_ineq(const D& d, int k) {  // inequalities of stage k >= 1
   return d.nx + (k - 1) * (d.nx + d.ni) + d.nx;
 }
 
-__device__ __forceinline__ int var_kind(const Dims& d, int i) {
+template <class D>
+__device__ __forceinline__ int var_kind(const D& d, int i) {
   if (i < d.nx + d.nu) return i < d.nx ? VK_FREE : VK_BOX;
   int j = i - (d.nx + d.nu);
   int blk = d.nx + d.nu + d.ni;
@@ -177,6 +204,8 @@ struct Layout {
   long long fdg;                    // diagonal terms of an FP64 factorisation ((N+1) nx + N nu)
   long long rhs, sol, rhs2, sol2, res, corr, rct;
   long long filt, filt_r;
+  long long wd_x, wd_zl, wd_zu, wd_y, wd_dir;  // watchdog: stored iterate and its K-sized step
+  long long sft_g, sft_j, sft_y;               // soft restoration: gradient, J^T y, y at the trial
   long long f64_fac;  // FP64 factor arrays (mixed precision: escalation and LS)
   long long gscr;     // factorisation scratch in global memory (large problems)
   long long gmv;      // GMRES basis (kGmresM + 1 K-sized vectors, mixed precision)
@@ -195,10 +224,15 @@ struct SlotState {
   int parked;              // queue straggler left to the block teams (results pending)
   int warm_flag, warm_it;  // warm-start outcome of a parked problem (bipm_result.warm / warm_iters)
   int cls;                 // structure class of the slot's problem (mixed queues)
+  int wd_short, wd_active, wd_trials;  // watchdog (Table I row 3)
+  int soft_active, soft_iters;         // soft restoration (Table I row 5)
+  int mu_free, n_refs;                 // adaptive barrier update: mode, references kept
   long long cyc[8];  // clock cycles per phase (see kPhase*)
   double mu, dw_last, theta_max, theta_min;
   double mu_r, dw_last_r, theta_max_r, theta_min_r, zeta, theta_ref;
   double obj, kkt, inf, last_alpha;
+  double wd_theta, wd_phi, wd_gdx, wd_amax, wd_amin;  // watchdog reference values
+  double mu_refs[kNumRefs], mu_max;                   // E_0 references, cap of mu (0: unset)
 };
 
 struct Params {

@@ -29,5 +29,7 @@ bipm_options default_options();
 int dims_from_desc(const bipm_problem_desc* desc, Dims* out);
 // Options with defaults filled in and validated (o_out), and their device copy.
 int options_from(const bipm_options* opt, bipm_options* o_out, Options* dev);
+// The queue kernel of a precision form for problems of nq quadrotors.
+void* queue_kernel_ptr(int precision, int nq);
 
 }  // namespace bipm

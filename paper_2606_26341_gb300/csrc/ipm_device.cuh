@@ -44,10 +44,10 @@ __device__ __forceinline__ Fac<T> make_fac(T* base, const Layout& L) {
 
 enum FactorFlags : int { FF_IDENT = 1, FF_RESTO = 2 };
 
-template <class TB, class TF>
+template <class TB, class TF, int NQ>
 struct Ctx {
   const Params* P;
-  Dims d;
+  DimsT<NQ> d;         // problem sizes (nq, nx, nu compile-time when NQ > 0)
   Layout L;
   int lane;            // thread index within the team
   int T;               // team size: 32 (warp) or the block size
@@ -113,7 +113,8 @@ struct VarInfo {
   int loc;    // position in the stage block
 };
 
-__device__ __forceinline__ VarInfo var_info(const Dims& d, int i) {
+template <class D>
+__device__ __forceinline__ VarInfo var_info(const D& d, int i) {
   VarInfo v;
   if (i < d.nx + d.nu) {
     v.k = 0;
@@ -133,7 +134,8 @@ __device__ __forceinline__ VarInfo var_info(const Dims& d, int i) {
 }
 
 // kind of entry i of a W-sized vector (x, then p, then n)
-__device__ __forceinline__ int wkind(const Dims& d, int i) {
+template <class D>
+__device__ __forceinline__ int wkind(const D& d, int i) {
   return i < d.n ? var_kind(d, i) : VK_LOWER;
 }
 __device__ __forceinline__ bool has_lower(int kind) { return kind != VK_FREE; }
@@ -145,10 +147,12 @@ __device__ __forceinline__ bool has_upper(int kind) { return kind == VK_BOX; }
 // instructions cost the same whatever the number of active lanes, so loops
 // over bounds run over this numbering with every lane busy instead of
 // skipping the free entries of a W-sized loop.
-__device__ __forceinline__ int n_bounded(const Dims& d, int len) {
+template <class D>
+__device__ __forceinline__ int n_bounded(const D& d, int len) {
   return d.N * d.nu + d.N * d.ni + (len - d.n);
 }
-__device__ __forceinline__ int bnd_index(const Dims& d, int b, int& kind) {
+template <class D>
+__device__ __forceinline__ int bnd_index(const D& d, int b, int& kind) {
   const int nu_all = d.N * d.nu;
   if (b < nu_all) {
     const int k = b / d.nu;
@@ -168,7 +172,8 @@ __device__ __forceinline__ int bnd_index(const Dims& d, int b, int& kind) {
 // ------------------------------------------------------ reference trajectory
 // reference state component j of quad q at stage k: circle position and
 // velocity, zero attitude and body rates (evaluated once per problem)
-__device__ __forceinline__ double ref_value(const double* th, const Dims& d, int k, int q, int j) {
+template <class D>
+__device__ __forceinline__ double ref_value(const double* th, const D& d, int k, int q, int j) {
   if (j >= 6) return 0.0;
   const double* r = th + d.th_ref + 6 * q;
   double t = k * d.dt;
@@ -185,7 +190,8 @@ __device__ __forceinline__ double ref_value(const double* th, const Dims& d, int
   }
 }
 
-__device__ __forceinline__ double cost_weight(const Dims& d, int k, int j) {
+template <class D>
+__device__ __forceinline__ double cost_weight(const D& d, int k, int j) {
   return q_weight(j) * (k == d.N ? kQNscale : 1.0);
 }
 
@@ -199,7 +205,8 @@ struct IneqRow {
   double hdiag;    // Hessian of g: hdiag * (I on involved components); pairs: +-hdiag
 };
 
-__device__ __forceinline__ IneqRow ineq_row(const Dims& d, const double* th, const double* xk,
+template <class D>
+__device__ __forceinline__ IneqRow ineq_row(const D& d, const double* th, const double* xk,
                                             int j) {
   IneqRow r;
   r.q1 = -1;
@@ -249,7 +256,8 @@ struct IneqGrad {
   int q0, q1, ncomp;
   double g[3];
 };
-__device__ __forceinline__ IneqGrad ineq_grad(const Dims& d, const double* th, const double* xk, int j) {
+template <class D>
+__device__ __forceinline__ IneqGrad ineq_grad(const D& d, const double* th, const double* xk, int j) {
   IneqGrad r;
   r.q1 = -1;
   const int nsq = d.nq * d.n_sph, ncq = d.nq * d.n_cyl;
@@ -284,7 +292,8 @@ __device__ __forceinline__ IneqGrad ineq_grad(const Dims& d, const double* th, c
 }
 // The same gradient read from the table fill_ineq_grad wrote for the iterate
 // (row t = (k - 1) ni + j of stage k >= 1).
-__device__ __forceinline__ IneqGrad ineq_grad_tab(const Dims& d, const double* igr, int t, int j) {
+template <class D>
+__device__ __forceinline__ IneqGrad ineq_grad_tab(const D& d, const double* igr, int t, int j) {
   IneqGrad r;
   r.q1 = -1;
   const int nsq = d.nq * d.n_sph, ncq = d.nq * d.n_cyl;
@@ -327,10 +336,10 @@ __device__ __forceinline__ double hess_pos(const IneqGrad& r, int qa, int ca, in
 
 // ---------------------------------------------------------------- evaluation
 // Constraint values c(x) (original problem) into cout and the objective f(x).
-template <class TB, class TF>
-__device__ __noinline__ double eval_values(Ctx<TB, TF>& c, const double* x, double* cout,
+template <class TB, class TF, int NQ>
+__device__ __noinline__ double eval_values(Ctx<TB, TF, NQ>& c, const double* x, double* cout,
                               bool dynamics = true) {
-  const Dims& d = c.d;
+  const auto& d = c.d;
   const int lane = c.lane;
   LANE_LOOP(i, d.nx) cout[i] = x[i] - c.th[d.th_x + i];
   for (int t = lane; t < (dynamics ? d.N * d.nq : 0); t += c.T) {
@@ -371,9 +380,9 @@ __device__ __noinline__ double eval_values(Ctx<TB, TF>& c, const double* x, doub
 }
 
 // Gradient of the objective of the current phase into g (W-sized).
-template <class TB, class TF>
-__device__ __noinline__ void eval_grad(Ctx<TB, TF>& c, const double* x, double* g) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void eval_grad(Ctx<TB, TF, NQ>& c, const double* x, double* g) {
+  const auto& d = c.d;
   const int lane = c.lane;
   const double* xr = c.f + c.L.xr;
   LANE_LOOP(i, c.nw) {
@@ -401,9 +410,9 @@ __device__ __noinline__ void eval_grad(Ctx<TB, TF>& c, const double* x, double* 
 }
 
 // Objective of the restoration problem: rho sum(p + n) + zeta/2 |D_R (x - x_R)|^2.
-template <class TB, class TF>
-__device__ __noinline__ double resto_objective(Ctx<TB, TF>& c, const double* w) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ>
+__device__ __noinline__ double resto_objective(Ctx<TB, TF, NQ>& c, const double* w) {
+  const auto& d = c.d;
   const int lane = c.lane;
   const double* xr = c.f + c.L.xr;
   double acc = 0.0;
@@ -423,9 +432,9 @@ __device__ __noinline__ double resto_objective(Ctx<TB, TF>& c, const double* w) 
 // at stage k.  The columns of A for p and v are constant (F is affine in p, v)
 // and the Hessian of lam^T F vanishes in those rows, so only ten directions
 // carry derivatives.  lam = -y_dyn (the Lagrangian term is +y^T (x_{k+1} - F)).
-template <class TB, class TF>
-__device__ __noinline__ void eval_blocks(Ctx<TB, TF>& c, const double* x, const double* y, bool hess) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void eval_blocks(Ctx<TB, TF, NQ>& c, const double* x, const double* y, bool hess) {
+  const auto& d = c.d;
   const int lane = c.lane;
   typedef Dual<TB> DT;
   const int ntask = d.N * d.nq * 10;
@@ -478,10 +487,10 @@ __device__ __noinline__ void eval_blocks(Ctx<TB, TF>& c, const double* x, const 
 
 // J^T y of the original constraints (x-part, n entries) in FP64, plus the
 // elastic parts (-y, +y) in restoration.
-template <class TB, class TF>
-__device__ __noinline__ void eval_jty(Ctx<TB, TF>& c, const double* x, const double* y, double* jty,
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void eval_jty(Ctx<TB, TF, NQ>& c, const double* x, const double* y, double* jty,
                          double* cout = nullptr) {
-  const Dims& d = c.d;
+  const auto& d = c.d;
   const int lane = c.lane;
   for (int t = lane; t < d.N * d.nq; t += c.T) {
     int k = t / d.nq, q = t - (t / d.nq) * d.nq;
@@ -540,13 +549,13 @@ __device__ __noinline__ void eval_jty(Ctx<TB, TF>& c, const double* x, const dou
 // ------------------------------------------------- barrier quantities (FP64)
 // Sigma_i = z_L/s_L + z_U/s_U of W-entry i, from the array fill_sigma wrote
 // for the current iterate.
-template <class TB, class TF>
-__device__ __forceinline__ double sigma_of(Ctx<TB, TF>& c, int i) {
+template <class TB, class TF, int NQ>
+__device__ __forceinline__ double sigma_of(Ctx<TB, TF, NQ>& c, int i) {
   return c.f[c.L.sig + i];
 }
 
-template <class TB, class TF>
-__device__ __noinline__ void fill_sigma(Ctx<TB, TF>& c) {
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void fill_sigma(Ctx<TB, TF, NQ>& c) {
   const double* x = c.f + c.L.x;
   const double* zl = c.f + c.L.zl;
   const double* zu = c.f + c.L.zu;
@@ -566,10 +575,10 @@ __device__ __noinline__ void fill_sigma(Ctx<TB, TF>& c) {
 
 // Diagonal Hessian of the objective on W-entry i (cost weights, or zeta D_R^2
 // in restoration, or 1 for the least-squares multiplier system).
-template <class TB, class TF>
-__device__ __forceinline__ double obj_hdiag(Ctx<TB, TF>& c, int i, int flags) {
+template <class TB, class TF, int NQ>
+__device__ __forceinline__ double obj_hdiag(Ctx<TB, TF, NQ>& c, int i, int flags) {
   if (flags & FF_IDENT) return 1.0;
-  const Dims& d = c.d;
+  const auto& d = c.d;
   if (i >= d.n) return 0.0;
   if (c.resto) {
     const double* xr = c.f + c.L.xr;
@@ -584,9 +593,9 @@ __device__ __forceinline__ double obj_hdiag(Ctx<TB, TF>& c, int i, int flags) {
 
 // Position gradients of every inequality row at the point x (the iterate),
 // one pass over all rows; factorisation, solves and the KKT mat-vec read them.
-template <class TB, class TF>
-__device__ __noinline__ void fill_ineq_grad(Ctx<TB, TF>& c, const double* x) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void fill_ineq_grad(Ctx<TB, TF, NQ>& c, const double* x) {
+  const auto& d = c.d;
   double* igr = c.f + c.L.igr;
   for (int t = c.lane; t < d.N * d.ni; t += c.T) {
     const int k = 1 + t / d.ni, j = t - (k - 1) * d.ni;
@@ -601,9 +610,9 @@ __device__ __noinline__ void fill_ineq_grad(Ctx<TB, TF>& c, const double* x) {
 // Condensation diagonals for regularisation dw:
 //   slack (k, r):  D_s = H_ss + Sigma_s + dw,  E = D_s / (1 + D_s D_g)
 //   row i (restoration): 1/(Sigma_p + dw), 1/(Sigma_n + dw), D = their sum
-template <class TB, class TF>
-__device__ __noinline__ void compute_diag(Ctx<TB, TF>& c, double dw, int flags) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void compute_diag(Ctx<TB, TF, NQ>& c, double dw, int flags) {
+  const auto& d = c.d;
   const int lane = c.lane;
   double* dsv = c.f + c.L.dsv;
   double* ev = c.f + c.L.ev;
@@ -654,9 +663,9 @@ __device__ __noinline__ void compute_diag(Ctx<TB, TF>& c, double dw, int flags) 
 //   qpos_k(a, b) = sum_r E_r g_r(a) g_r(b) + y_r H_r(a, b),
 // a, b over the 3 nq position components of stage k (no Hessian term in the
 // least-squares multiplier system).
-template <class TB, class TF>
-__device__ __noinline__ void ineq_blocks(Ctx<TB, TF>& c, int flags) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void ineq_blocks(Ctx<TB, TF, NQ>& c, int flags) {
+  const auto& d = c.d;
   const int lane = c.lane;
   const double* ev = c.f + c.L.ev;
   const int np = 3 * d.nq, npp = np * np;
@@ -690,8 +699,8 @@ struct Scratch {
   double* R64;
 };
 
-template <class TX>
-__device__ __forceinline__ Scratch<TX> scratch(char* smem, const Dims& d) {
+template <class TX, class D>
+__device__ __forceinline__ Scratch<TX> scratch(char* smem, const D& d) {
   Scratch<TX> s;
   TX* p = (TX*)smem;
   int nx = d.nx, nu = d.nu;
@@ -723,17 +732,17 @@ __host__ __device__ inline size_t scratch_bytes(int nq, int nx, int nu, int elem
 
 // shared memory when the scratch of precision TX fits, else the slot's
 // global scratch region
-template <class TX, class TB, class TF>
-__device__ __forceinline__ char* scratch_base(const Ctx<TB, TF>& c) {
+template <class TX, class TB, class TF, int NQ>
+__device__ __forceinline__ char* scratch_base(const Ctx<TB, TF, NQ>& c) {
   return scratch_bytes(c.d.nq, c.d.nx, c.d.nu, (int)sizeof(TX)) <= (size_t)c.smem_bytes ? c.smem
                                                                                         : c.gscratch;
 }
 
 // Q~_k (state block, written to Pb as TX), including the inequality terms.
-template <class TB, class TF, class TX>
-__device__ __noinline__ void add_state_block(Ctx<TB, TF>& c, int k, TX* Q, double dw, int flags,
+template <class TB, class TF, int NQ, class TX>
+__device__ __noinline__ void add_state_block(Ctx<TB, TF, NQ>& c, int k, TX* Q, double dw, int flags,
                                 const double* y, bool accumulate, const TX* xdg = nullptr) {
-  const Dims& d = c.d;
+  const auto& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx;
   const double* qpos = c.f + c.L.qpos;
@@ -853,9 +862,9 @@ __device__ inline int stage_pivot_check(const C& c, const TX* R, double* a64, in
 }
 
 // Restoration: P~ = P - Y^T Y with Y = L_M^{-1} D^1/2 P, M = I + D^1/2 P D^1/2 = L_M L_M^T.
-template <class TB, class TF, class TX>
-__device__ __noinline__ bool resto_transform(Ctx<TB, TF>& c, TX* Pb, const double* D, TX* LM, TX* Y) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ, class TX>
+__device__ __noinline__ bool resto_transform(Ctx<TB, TF, NQ>& c, TX* Pb, const double* D, TX* LM, TX* Y) {
+  const auto& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx;
   // M in LM (as TX) ; factor in double would need nx^2 doubles: factor in TX
@@ -900,9 +909,9 @@ __device__ __noinline__ bool resto_transform(Ctx<TB, TF>& c, TX* Pb, const doubl
   return true;
 }
 
-template <class TB, class TF, class TX>
-__device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int flags, const double* y) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ, class TX>
+__device__ __noinline__ int factor(Ctx<TB, TF, NQ>& c, Fac<TX> F, double dw, int flags, const double* y) {
+  const auto& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx, nu = d.nu, nq = d.nq, N = d.N;
   const bool ident = flags & FF_IDENT;
@@ -946,10 +955,10 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
   }
 
   // terminal block P_N = Q~_N
-  add_state_block<TB, TF, TX>(c, N, s.Pb, dw, flags, y, false, xdg);
+  add_state_block<TB, TF, NQ, TX>(c, N, s.Pb, dw, flags, y, false, xdg);
   team_sync(c);
   if (resto) {
-    if (!resto_transform<TB, TF, TX>(c, s.Pb, dv + row_dyn(d, N - 1), F.LM + (long long)N * nx * nx,
+    if (!resto_transform<TB, TF, NQ, TX>(c, s.Pb, dv + row_dyn(d, N - 1), F.LM + (long long)N * nx * nx,
                                      F.Yr + (long long)N * nx * nx))
       return 0;
   }
@@ -1032,7 +1041,7 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
       s.Pb[(12 * q + ci) * nx + col] = dot12(s.Ab + q * 144 + ci * 12, 1, s.PA + (12 * q) * nx + col, nx);
     }
     team_sync(c);
-    add_state_block<TB, TF, TX>(c, k, s.Pb, dw, flags, y, true, xdg);
+    add_state_block<TB, TF, NQ, TX>(c, k, s.Pb, dw, flags, y, true, xdg);
     if constexpr (f32) {
       // FP32 Cholesky of R^ for the gains; the FP64 inertia test follows the
       // recursion.  A pivot FP32 cannot factor ends the recursion here.
@@ -1096,7 +1105,7 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
     team_sync(c);
     if (resto) {
       const double* D = dv + (k == 0 ? 0 : row_dyn(d, k - 1));
-      if (!resto_transform<TB, TF, TX>(c, s.Pb, D, F.LM + (long long)k * nx * nx,
+      if (!resto_transform<TB, TF, NQ, TX>(c, s.Pb, D, F.LM + (long long)k * nx * nx,
                                        F.Yr + (long long)k * nx * nx))
         return 0;
     }
@@ -1118,10 +1127,10 @@ __device__ __noinline__ int factor(Ctx<TB, TF>& c, Fac<TX> F, double dw, int fla
 // is the augmented matrix of Eq. 7 (restoration: with the elastic variables)
 // and r is K-sized: [r_x (n) | r_p (m) | r_n (m) | r_c (m)] (r_p, r_n only in
 // restoration; the layout always reserves them).  out has the same layout.
-template <class TB, class TF, class TX>
-__device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, double* out, int flags,
+template <class TB, class TF, int NQ, class TX>
+__device__ __noinline__ void solve(Ctx<TB, TF, NQ>& c, Fac<TX> F, const double* r, double* out, int flags,
                       const double* y) {
-  const Dims& d = c.d;
+  const auto& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx, nu = d.nu, N = d.N, n = d.n, m = d.m;
   const bool resto = flags & FF_RESTO;
@@ -1376,10 +1385,10 @@ __device__ __noinline__ void solve(Ctx<TB, TF>& c, Fac<TX> F, const double* r, d
 // ---------------------------------------------------- KKT mat-vec (FP64)
 // out = K v for the matrix that `factor` condensed (same dw, same phase),
 // K-sized layout as in `solve`.  Used for iterative refinement.
-template <class TB, class TF>
-__device__ __noinline__ void kkt_matvec(Ctx<TB, TF>& c, const double* v, double* out, double dw,
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void kkt_matvec(Ctx<TB, TF, NQ>& c, const double* v, double* out, double dw,
                            const double* y) {
-  const Dims& d = c.d;
+  const auto& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx, nu = d.nu, N = d.N, n = d.n, m = d.m;
   const long long nwk = c.L.nw;

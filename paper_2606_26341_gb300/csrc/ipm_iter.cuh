@@ -18,20 +18,20 @@ namespace bipm {
 enum Outcome : int { OUT_ACCEPTED = 0, OUT_LS_FAILED = 1 };
 
 // ------------------------------------------------------------- reductions
-template <class TB, class TF>
-__device__ double l1_norm(Ctx<TB, TF>& c, const double* v, int len) {
+template <class TB, class TF, int NQ>
+__device__ double l1_norm(Ctx<TB, TF, NQ>& c, const double* v, int len) {
   double a = 0.0;
   for (int i = c.lane; i < len; i += c.T) a += fabs(v[i]);
   return team_sum(c, a);
 }
-template <class TB, class TF>
-__device__ double inf_norm(Ctx<TB, TF>& c, const double* v, int len) {
+template <class TB, class TF, int NQ>
+__device__ double inf_norm(Ctx<TB, TF, NQ>& c, const double* v, int len) {
   double a = 0.0;
   for (int i = c.lane; i < len; i += c.T) a = fmax(a, fabs(v[i]));
   return team_max(c, a);
 }
-template <class TB, class TF>
-__device__ bool all_finite(Ctx<TB, TF>& c, const double* v, int len) {
+template <class TB, class TF, int NQ>
+__device__ bool all_finite(Ctx<TB, TF, NQ>& c, const double* v, int len) {
   int bad = 0;
   for (int i = c.lane; i < len; i += c.T) bad |= !isfinite(v[i]);
   return !team_or(c, bad);
@@ -39,8 +39,8 @@ __device__ bool all_finite(Ctx<TB, TF>& c, const double* v, int len) {
 
 // barrier objective phi_mu (Eq. 3) with the one-sided damping term, over the
 // first `len` entries of a W-sized point w; +inf outside the bounds
-template <class TB, class TF>
-__device__ __noinline__ double barrier_phi(Ctx<TB, TF>& c, const double* w, double f, double mu, int len) {
+template <class TB, class TF, int NQ>
+__device__ __noinline__ double barrier_phi(Ctx<TB, TF, NQ>& c, const double* w, double f, double mu, int len) {
   double acc = 0.0;
   int bad = 0;
   const int nb = n_bounded(c.d, len);
@@ -67,8 +67,8 @@ struct ErrParts {
   double dual, prim, y1, z1, nb;
 };
 
-template <class TB, class TF>
-__device__ __noinline__ ErrParts err_parts(Ctx<TB, TF>& c) {
+template <class TB, class TF, int NQ>
+__device__ __noinline__ ErrParts err_parts(Ctx<TB, TF, NQ>& c) {
   const double* gf = c.f + c.L.gf;
   const double* jty = c.f + c.L.jty;
   const double* zl = c.f + c.L.zl;
@@ -98,8 +98,8 @@ __device__ __noinline__ ErrParts err_parts(Ctx<TB, TF>& c) {
   return e;
 }
 
-template <class TB, class TF>
-__device__ __noinline__ double opt_error(Ctx<TB, TF>& c, const ErrParts& e, double mu) {
+template <class TB, class TF, int NQ>
+__device__ __noinline__ double opt_error(Ctx<TB, TF, NQ>& c, const ErrParts& e, double mu) {
   const double* w = c.f + c.L.x;
   const double* zl = c.f + c.L.zl;
   const double* zu = c.f + c.L.zu;
@@ -120,8 +120,8 @@ __device__ __noinline__ double opt_error(Ctx<TB, TF>& c, const ErrParts& e, doub
 
 // largest alpha in (0, 1] keeping the bounded entries of w + alpha dw at least
 // the fraction 1 - tau of their distance to the bounds
-template <class TB, class TF>
-__device__ __noinline__ double ftb_primal(Ctx<TB, TF>& c, const double* w, const double* dw, double tau) {
+template <class TB, class TF, int NQ>
+__device__ __noinline__ double ftb_primal(Ctx<TB, TF, NQ>& c, const double* w, const double* dw, double tau) {
   double a = 1.0;
   const int nb = n_bounded(c.d, c.nw);
   for (int b = c.lane; b < nb; b += c.T) {
@@ -187,9 +187,9 @@ __device__ __forceinline__ void filter_add(const C& c, double* filt, int& nf, do
 // the condensation weight E of the slacks.  Relative to the O(1) Hessian
 // blocks it measures how much of FP32's 24-bit mantissa the factorisation
 // loses in the position and input blocks.
-template <class TB, class TF>
-__device__ __noinline__ double barrier_scale(Ctx<TB, TF>& c) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ>
+__device__ __noinline__ double barrier_scale(Ctx<TB, TF, NQ>& c) {
+  const auto& d = c.d;
   const double* ev = c.f + c.L.ev;
   const double* sg = c.f + c.L.sig;
   double b = 0.0;
@@ -201,14 +201,14 @@ __device__ __noinline__ double barrier_scale(Ctx<TB, TF>& c) {
   return team_max(c, b);
 }
 
-template <class TB, class TF>
-__device__ __noinline__ bool factor_any(Ctx<TB, TF>& c, double dw, bool force64) {
+template <class TB, class TF, int NQ>
+__device__ __noinline__ bool factor_any(Ctx<TB, TF, NQ>& c, double dw, bool force64) {
   const int flags = c.resto ? FF_RESTO : 0;
   const double* y = c.f + c.L.y;
   if (HighPrecision<TF>::value && !std::is_same<TF, double>::value && !c.resto && !force64) {
     // double-float factorisation: accurate enough to need no refinement
     c.use64 = 0;
-    return factor<TB, TF, TF>(c, c.fac, dw, flags, y) != 0;
+    return factor<TB, TF, NQ, TF>(c, c.fac, dw, flags, y) != 0;
   }
   if (sizeof(TF) == 4 && !c.resto && !force64) {
     // per-problem precision choice: FP32 only while the barrier terms leave
@@ -221,14 +221,14 @@ __device__ __noinline__ bool factor_any(Ctx<TB, TF>& c, double dw, bool force64)
   }
   if (HighPrecision<TF>::value || c.resto || force64) {
     c.use64 = 1;
-    return factor<TB, TF, double>(c, c.fac64, dw, flags, y) != 0;
+    return factor<TB, TF, NQ, double>(c, c.fac64, dw, flags, y) != 0;
   }
-  int r = factor<TB, TF, TF>(c, c.fac, dw, flags, y);
+  int r = factor<TB, TF, NQ, TF>(c, c.fac, dw, flags, y);
   if (r == 0) return false;
   if (r == 2) {
     c.n_esc++;
     c.use64 = 1;
-    return factor<TB, TF, double>(c, c.fac64, dw, flags, y) != 0;
+    return factor<TB, TF, NQ, double>(c, c.fac64, dw, flags, y) != 0;
   }
   c.use64 = 0;
   return true;
@@ -241,16 +241,16 @@ __device__ __noinline__ bool factor_any(Ctx<TB, TF>& c, double dw, bool force64)
 // residual ratio |K out + r| / (min(|out|, 1e6 |r|) + |r|) drops below 1e-10;
 // if that fails within the restarts the matrix is refactorised in FP64.
 // Returns false only if that FP64 refactorisation reports wrong inertia.
-template <class TB, class TF>
-__device__ __noinline__ bool solve_refined(Ctx<TB, TF>& c, const double* r, double* out) {
+template <class TB, class TF, int NQ>
+__device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ>& c, const double* r, double* out) {
   const int flags = c.resto ? FF_RESTO : 0;
   const double* y = c.f + c.L.y;
   if (c.use64) {
-    solve<TB, TF, double>(c, c.fac64, r, out, flags, y);
+    solve<TB, TF, NQ, double>(c, c.fac64, r, out, flags, y);
     return true;
   }
   if (HighPrecision<TF>::value) {  // double-float factors: no refinement needed
-    solve<TB, TF, TF>(c, c.fac, r, out, flags, y);
+    solve<TB, TF, NQ, TF>(c, c.fac, r, out, flags, y);
     return true;
   }
   const int lane = c.lane;
@@ -279,9 +279,9 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF>& c, const double* r, doub
   auto precond = [&](const double* v, double* z) {
     for (int i = lane; i < len; i += c.T) corr[at(i)] = -v[at(i)];
     team_sync(c);
-    solve<TB, TF, TF>(c, c.fac, corr, z, flags, y);
+    solve<TB, TF, NQ, TF>(c, c.fac, corr, z, flags, y);
   };
-  solve<TB, TF, TF>(c, c.fac, r, out, flags, y);
+  solve<TB, TF, NQ, TF>(c, c.fac, r, out, flags, y);
   const double rnorm = norm_inf(r);
   if (rnorm == 0.0) return true;
   for (int rs = 0; rs <= kGmresRestarts; ++rs) {
@@ -356,9 +356,9 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF>& c, const double* r, doub
   }
   // refinement did not converge: refactorise in FP64
   c.n_esc++;
-  if (factor<TB, TF, double>(c, c.fac64, c.dw, flags, y) == 0) return false;
+  if (factor<TB, TF, NQ, double>(c, c.fac64, c.dw, flags, y) == 0) return false;
   c.use64 = 1;
-  solve<TB, TF, double>(c, c.fac64, r, out, flags, y);
+  solve<TB, TF, NQ, double>(c, c.fac64, r, out, flags, y);
   // an FP64 step that is not finite cannot be used: the problem stops
   if (!all_finite(c, out, nused) || !all_finite(c, out + nwk, c.d.m)) c.esc_failed = 1;
   return true;
@@ -366,9 +366,9 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF>& c, const double* r, doub
 
 // Least-squares multipliers: [[I, J^T], [J, 0]] (w, y) = (-(grad f - z_L + z_U), 0);
 // y = 0 if |y|_inf > y_max.
-template <class TB, class TF>
-__device__ __noinline__ void ls_multipliers(Ctx<TB, TF>& c) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void ls_multipliers(Ctx<TB, TF, NQ>& c) {
+  const auto& d = c.d;
   const int lane = c.lane;
   double* w = c.f + c.L.x;
   double* y = c.f + c.L.y;
@@ -384,16 +384,16 @@ __device__ __noinline__ void ls_multipliers(Ctx<TB, TF>& c) {
   }
   LANE_LOOP(i, d.m) rhs[c.L.nw + i] = 0.0;
   team_sync(c);
-  factor<TB, TF, double>(c, c.fac64, 0.0, FF_IDENT, y);
-  solve<TB, TF, double>(c, c.fac64, rhs, sol, FF_IDENT, y);
+  factor<TB, TF, NQ, double>(c, c.fac64, 0.0, FF_IDENT, y);
+  solve<TB, TF, NQ, double>(c, c.fac64, rhs, sol, FF_IDENT, y);
   double ymax = inf_norm(c, sol + c.L.nw, d.m);
   LANE_LOOP(i, d.m) y[i] = ymax > kYmax ? 0.0 : sol[c.L.nw + i];
   team_sync(c);
 }
 
 // z <- max(min(z, kappa_Sigma mu / s), mu / (kappa_Sigma s)) over the first len entries
-template <class TB, class TF>
-__device__ __noinline__ void kappa_sigma_reset(Ctx<TB, TF>& c, int len, double mu) {
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void kappa_sigma_reset(Ctx<TB, TF, NQ>& c, int len, double mu) {
   double* w = c.f + c.L.x;
   double* zl = c.f + c.L.zl;
   double* zu = c.f + c.L.zu;
@@ -411,8 +411,79 @@ __device__ __noinline__ void kappa_sigma_reset(Ctx<TB, TF>& c, int len, double m
   team_sync(c);
 }
 
+// A barrier-parameter decrease or entering restoration ends an active
+// watchdog and soft restoration and clears the shortened-step count.
+__device__ __forceinline__ void end_globalization(SlotState& S) {
+  S.wd_active = 0;
+  S.wd_trials = 0;
+  S.wd_short = 0;
+  S.soft_active = 0;
+  S.soft_iters = 0;
+}
+
+// Average and minimum of the complementarity products s_i z_i over all bounds
+// of the original problem.
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void complementarity_stats(Ctx<TB, TF, NQ>& c, double& avg, double& mn) {
+  const auto& d = c.d;
+  const double* w = c.f + c.L.x;
+  const double* zl = c.f + c.L.zl;
+  const double* zu = c.f + c.L.zu;
+  double sum = 0.0, lo = INFINITY, cnt = 0.0;
+  const int nb = n_bounded(d, d.n);
+  for (int b = c.lane; b < nb; b += c.T) {
+    int kind;
+    const int i = bnd_index(d, b, kind);
+    const double pl = w[i] * zl[i];
+    sum += pl;
+    lo = fmin(lo, pl);
+    cnt += 1.0;
+    if (kind == VK_BOX) {
+      const double pu = (kUmax - w[i]) * zu[i];
+      sum += pu;
+      lo = fmin(lo, pu);
+      cnt += 1.0;
+    }
+  }
+  sum = team_sum(c, sum);
+  cnt = team_sum(c, cnt);
+  mn = team_min(c, lo);
+  avg = cnt > 0.0 ? sum / cnt : 0.0;
+  if (!(cnt > 0.0)) mn = 0.0;
+}
+
+// LOQO's centrality rule: sigma * average with sigma = 0.1 min(0.05 (1 - xi)/xi, 2)^3,
+// xi = min / average
+__device__ __forceinline__ double loqo_mu(double avg, double mn) {
+  if (!(avg > 0.0)) return 0.0;
+  const double xi = mn / avg;
+  const double t = xi > 0.0 ? fmin(0.05 * (1.0 - xi) / xi, 2.0) : 2.0;
+  return 0.1 * t * t * t * avg;
+}
+
+// 1-norm primal-dual error of the barrier problem at mu (original problem):
+// |grad f + J^T y - z_L + z_U|_1 + |c|_1 + |S_L z_L - mu e|_1 + |S_U z_U - mu e|_1
+template <class TB, class TF, int NQ>
+__device__ __noinline__ double pd_error(Ctx<TB, TF, NQ>& c, const double* w, const double* zl, const double* zu,
+                                        const double* gf, const double* jty, const double* cv, double mu) {
+  const auto& d = c.d;
+  double a = 0.0;
+  for (int i = c.lane; i < d.n; i += c.T) {
+    const int kind = wkind(d, i);
+    a += fabs(gf[i] + jty[i] - (has_lower(kind) ? zl[i] : 0.0) + (has_upper(kind) ? zu[i] : 0.0));
+  }
+  for (int i = c.lane; i < d.m; i += c.T) a += fabs(cv[i]);
+  const int nb = n_bounded(d, d.n);
+  for (int b = c.lane; b < nb; b += c.T) {
+    int kind;
+    const int i = bnd_index(d, b, kind);
+    a += fabs(w[i] * zl[i] - mu);
+    if (kind == VK_BOX) a += fabs((kUmax - w[i]) * zu[i] - mu);
+  }
+  return team_sum(c, a);
+}
+
 // ------------------------------------------------------------- iteration
-template <class TB, class TF>
 struct TrialVal {
   double theta, phi, f;
   bool finite;
@@ -420,9 +491,9 @@ struct TrialVal {
 
 // trial point w + alpha * dir: constraint violation and barrier objective of
 // the current phase; the phase constraint vector goes to ct
-template <class TB, class TF>
-__device__ __noinline__ TrialVal<TB, TF> trial_point(Ctx<TB, TF>& c, double alpha, const double* dir) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ>
+__device__ __noinline__ TrialVal trial_point(Ctx<TB, TF, NQ>& c, double alpha, const double* dir) {
+  const auto& d = c.d;
   const int lane = c.lane;
   const double* w = c.f + c.L.x;
   double* xt = c.f + c.L.xt;
@@ -436,7 +507,7 @@ __device__ __noinline__ TrialVal<TB, TF> trial_point(Ctx<TB, TF>& c, double alph
     team_sync(c);
     f = resto_objective(c, xt);
   }
-  TrialVal<TB, TF> tv;
+  TrialVal tv;
   tv.finite = isfinite(f) && all_finite(c, ct, d.m);
   tv.theta = l1_norm(c, ct, d.m);
   tv.phi = tv.finite ? barrier_phi(c, xt, f, c.mu, c.nw) : INFINITY;
@@ -444,9 +515,9 @@ __device__ __noinline__ TrialVal<TB, TF> trial_point(Ctx<TB, TF>& c, double alph
   return tv;
 }
 
-template <class TB, class TF>
-__device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
-  const Dims& d = c.d;
+template <class TB, class TF, int NQ>
+__device__ __noinline__ void iterate(Ctx<TB, TF, NQ>& c, SlotState& S) {
+  const auto& d = c.d;
   const int lane = c.lane;
   const Options& opt = c.P->opt;
   const int n = d.n, m = d.m;
@@ -542,8 +613,49 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
     return;
   }
 
+  // ---- barrier update (Table I row 7): adaptive on the original problem, if chosen
+  bool mu_done = false;
+  if (!c.resto && opt.mu_strategy == 1) {
+    const double err0 = opt_error(c, ep, 0.0);
+    double avg, mn;
+    complementarity_stats(c, avg, mn);
+    if (S.mu_max == 0.0) S.mu_max = kMuMaxFact * fmax(avg, opt.tol);
+    double mu_new = mu;
+    bool progress = S.n_refs == 0;
+    {
+      double rmax = 0.0;
+      for (int i = 0; i < S.n_refs; ++i) rmax = fmax(rmax, S.mu_refs[i]);
+      if (S.n_refs > 0) progress = err0 <= kRefsRedFact * rmax;
+    }
+    if (S.mu_free) {
+      mu_done = true;
+      if (progress && !tiny) {
+        if (S.n_refs == kNumRefs) {
+          for (int i = 1; i < kNumRefs; ++i) S.mu_refs[i - 1] = S.mu_refs[i];
+          S.n_refs--;
+        }
+        S.mu_refs[S.n_refs++] = err0;
+        mu_new = fmax(kMuMinFree, fmin(S.mu_max, loqo_mu(avg, mn)));
+      } else {
+        S.mu_free = 0;
+        mu_new = fmax(opt.tol / 10.0, kMuMonoInit * avg);
+      }
+    } else if (opt_error(c, ep, mu) <= kKappaEps * mu && progress) {
+      mu_done = true;
+      S.mu_free = 1;
+      S.mu_refs[0] = err0;
+      S.n_refs = 1;
+      mu_new = fmax(kMuMinFree, fmin(S.mu_max, loqo_mu(avg, mn)));
+    }
+    if (mu_done && mu_new != mu) {
+      mu = mu_new;
+      nf = 0;
+      tiny = 0;
+      end_globalization(S);
+    }
+  }
   // ---- monotone barrier update (Table I row 7)
-  {
+  if (!mu_done) {
     const double mu_floor = opt.tol / 10.0;
     bool first = true;
     while (true) {
@@ -560,6 +672,7 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
         nf = 0;
         first = false;
         tiny = 0;
+        if (!c.resto) end_globalization(S);
         continue;
       }
       break;
@@ -651,14 +764,14 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
 
   Outcome outcome = OUT_LS_FAILED;
   double theta0 = theta, phi0 = 0.0, gdx = 0.0;
+  bool wd_restored = false;  // the watchdog returned the iterate to its stored point
   if (!ls_fail) {
     const double* dx = sol;
     double a_max = ftb_primal(c, w, dx, tau);
 
     // accept a step (alpha, dir) with dir K-sized; the z step follows from dir
-    auto accept = [&](double alpha, const double* dir, bool augment) {
-      const double* ddx = dir;
-      const double* ddy = dir + nwk;
+    // fraction-to-boundary step of the bound multipliers along the z step of dir
+    auto dual_max = [&](const double* ddx) {
       double az = 1.0;
       const int nb = n_bounded(d, c.nw);
       for (int b = lane; b < nb; b += c.T) {
@@ -671,7 +784,15 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
           if (dzu < 0.0) az = fmin(az, -tau * zu[i] / dzu);
         }
       }
-      az = team_min(c, az);
+      return team_min(c, az);
+    };
+    // accept a step (alpha, dir) with dir K-sized; the z step follows from dir
+    // (az_fixed >= 0: that dual step size instead of its fraction to the boundary)
+    auto accept = [&](double alpha, const double* dir, bool augment, double az_fixed = -1.0) {
+      const double* ddx = dir;
+      const double* ddy = dir + nwk;
+      const double az = az_fixed >= 0.0 ? az_fixed : dual_max(ddx);
+      const int nb = n_bounded(d, c.nw);
       // bound multipliers from the step at the current point, then the primal step
       for (int b = lane; b < nb; b += c.T) {
         int kind;
@@ -696,6 +817,7 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
       accept(a_max, sol, false);
       tiny = 1;
       S.n_tiny++;
+      if (!c.resto) S.wd_short = 0;
       outcome = OUT_ACCEPTED;
     } else {
       tiny = 0;
@@ -723,15 +845,154 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
       auto needs_augment = [&](double alpha, double ph_t) {
         return !(switching(alpha) && ph_t <= phi0 + kEtaPhi * alpha * gdx);
       };
+      const bool globalize = !c.resto;  // watchdog and soft restoration: original problem only
+
+      // soft restoration (Table I row 5): one primal-dual step alpha_s = min(alpha_max,
+      // alpha_z_max); accepted if it passes the original tests (the soft phase ends)
+      // or lowers the primal-dual error E_pd by the factor 1 - kappa_soft
+      auto soft_step = [&]() {
+        const double a_s = fmin(a_max, dual_max(dx));
+        TrialVal tv = trial_point(c, a_s, dx);
+        if (!tv.finite) return false;
+        if (acceptable(tv.theta, tv.phi, 0.0)) {
+          accept(a_s, sol, true, a_s);
+          S.soft_active = 0;
+          S.soft_iters = 0;
+          return true;
+        }
+        // errors at the current point and at the trial (y and z moved by a_s too)
+        const double e0 = pd_error(c, w, zl, zu, gf, jty, cv, mu);
+        const double* xt = c.f + c.L.xt;
+        double* gt = c.f + c.L.sft_g;
+        double* jt = c.f + c.L.sft_j;
+        double* yt = c.f + c.L.sft_y;
+        double* zlt = c.f + c.L.res;
+        double* zut = c.f + c.L.corr;
+        LANE_LOOP(i, m) yt[i] = y[i] + a_s * dx[nwk + i];
+        LANE_LOOP(i, n) {
+          zlt[i] = zl[i];
+          zut[i] = zu[i];
+        }
+        team_sync(c);
+        {
+          const int nb = n_bounded(d, n);
+          for (int b = lane; b < nb; b += c.T) {
+            int kind;
+            const int i = bnd_index(d, b, kind);
+            zlt[i] = zl[i] + a_s * dz_lower(w[i], zl[i], mu, dx[i]);
+            if (kind == VK_BOX) zut[i] = zu[i] + a_s * dz_upper(kUmax - w[i], zu[i], mu, dx[i]);
+          }
+        }
+        team_sync(c);
+        eval_grad(c, xt, gt);
+        eval_jty(c, xt, yt, jt);
+        if (!all_finite(c, gt, n) || !all_finite(c, jt, n)) return false;
+        const double e1 = pd_error(c, xt, zlt, zut, gt, jt, ct, mu);
+        if (!(e1 <= (1.0 - kKappaSoft) * e0)) return false;
+        accept(a_s, sol, true, a_s);
+        S.soft_active = 1;
+        S.soft_iters++;
+        return true;
+      };
+
+      // filter tests against the reference values stored when the watchdog started
+      auto switching_ref = [&](double alpha) {
+        return S.wd_gdx < 0.0 && alpha * pow(-S.wd_gdx, kSPhi) > kDelta * pow(S.wd_theta, kSTheta);
+      };
+      auto acceptable_ref = [&](double th_t, double ph_t, double alpha) {
+        if (!isfinite(ph_t) || in_filter(c, filt, nf, th_t, ph_t, th_max)) return false;
+        if (switching_ref(alpha) && S.wd_theta <= th_min) return ph_t <= S.wd_phi + kEtaPhi * alpha * S.wd_gdx;
+        return th_t <= (1.0 - kGammaTheta) * S.wd_theta || ph_t <= S.wd_phi - kGammaPhi * S.wd_theta;
+      };
+      auto needs_augment_ref = [&](double alpha, double ph_t) {
+        return !(switching_ref(alpha) && ph_t <= S.wd_phi + kEtaPhi * alpha * S.wd_gdx);
+      };
+
+      bool handled = false;
+      if (globalize && opt.soft_resto && S.soft_active) {
+        // in the soft restoration phase the soft step replaces the line search
+        handled = true;
+        if (S.soft_iters < kSoftMax && soft_step()) outcome = OUT_ACCEPTED;
+      }
+      if (!handled && globalize && opt.watchdog && !S.wd_active && S.wd_short >= kWdTrigger) {
+        // watchdog (Table I row 3) starts: store the iterate, its step and references
+        double* sx = c.f + c.L.wd_x;
+        double* szl = c.f + c.L.wd_zl;
+        double* szu = c.f + c.L.wd_zu;
+        double* sy = c.f + c.L.wd_y;
+        double* sd = c.f + c.L.wd_dir;
+        LANE_LOOP(i, n) {
+          sx[i] = w[i];
+          szl[i] = zl[i];
+          szu[i] = zu[i];
+          sd[i] = dx[i];
+        }
+        LANE_LOOP(i, m) {
+          sy[i] = y[i];
+          sd[nwk + i] = dx[nwk + i];
+        }
+        team_sync(c);
+        S.wd_active = 1;
+        S.wd_trials = 0;
+        S.wd_short = 0;
+        S.wd_theta = theta;
+        S.wd_phi = phi0;
+        S.wd_gdx = gdx;
+        S.wd_amax = a_max;
+        S.wd_amin = a_min;
+      }
+      if (!handled && globalize && opt.watchdog && S.wd_active) {
+        // the full step, judged against the stored iterate
+        handled = true;
+        TrialVal tv = trial_point(c, a_max, dx);
+        if (tv.finite && acceptable_ref(tv.theta, tv.phi, a_max)) {
+          theta0 = S.wd_theta;
+          phi0 = S.wd_phi;
+          accept(a_max, sol, needs_augment_ref(a_max, tv.phi));
+          S.wd_active = 0;
+          S.wd_trials = 0;
+          outcome = OUT_ACCEPTED;
+        } else if (++S.wd_trials <= kWdTrialMax) {
+          accept(a_max, sol, false);  // unconditionally
+          outcome = OUT_ACCEPTED;
+        } else {
+          // give up: back to the stored iterate, backtracking along its step from
+          // half its full step (no second-order correction: its factors are gone)
+          S.wd_active = 0;
+          S.wd_trials = 0;
+          const double* sd = c.f + c.L.wd_dir;
+          LANE_LOOP(i, n) {
+            w[i] = c.f[c.L.wd_x + i];
+            zl[i] = c.f[c.L.wd_zl + i];
+            zu[i] = c.f[c.L.wd_zu + i];
+          }
+          LANE_LOOP(i, m) y[i] = c.f[c.L.wd_y + i];
+          team_sync(c);
+          wd_restored = true;
+          theta0 = S.wd_theta;
+          phi0 = S.wd_phi;
+          int n_try = 0;
+          for (double alpha = 0.5 * S.wd_amax; alpha >= S.wd_amin && n_try < kLsMaxTrials; alpha *= 0.5) {
+            ++n_try;
+            TrialVal tv2 = trial_point(c, alpha, sd);
+            if (tv2.finite && acceptable_ref(tv2.theta, tv2.phi, alpha)) {
+              accept(alpha, sd, needs_augment_ref(alpha, tv2.phi));
+              outcome = OUT_ACCEPTED;
+              break;
+            }
+          }
+        }
+      }
 
       double alpha = a_max;
       int n_trial = 0;
-      while (true) {
+      while (!handled) {
         ++n_trial;
-        TrialVal<TB, TF> tv = trial_point(c, alpha, dx);
+        TrialVal tv = trial_point(c, alpha, dx);
         if (tv.finite) {
           if (acceptable(tv.theta, tv.phi, alpha)) {
             accept(alpha, sol, needs_augment(alpha, tv.phi));
+            if (globalize) S.wd_short = alpha < a_max ? S.wd_short + 1 : 0;
             outcome = OUT_ACCEPTED;
             break;
           }
@@ -748,7 +1009,7 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
               c.esc_failed = 0;
               if (!solve_refined(c, rhs2, sol2) || c.esc_failed) break;  // no usable correction
               double a_soc = ftb_primal(c, w, sol2, tau);
-              TrialVal<TB, TF> sv = trial_point(c, a_soc, sol2);
+              TrialVal sv = trial_point(c, a_soc, sol2);
               if (!sv.finite) break;
               if (acceptable(sv.theta, sv.phi, alpha)) {
                 accept(a_soc, sol2, needs_augment(alpha, sv.phi));
@@ -761,13 +1022,17 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
               theta_old = sv.theta;
             }
             if (soc_ok) {
+              if (globalize) S.wd_short = 0;
               outcome = OUT_ACCEPTED;
               break;
             }
           }
         }
         alpha *= 0.5;
-        if (alpha < a_min || n_trial >= kLsMaxTrials) break;
+        if (alpha < a_min || n_trial >= kLsMaxTrials) {
+          if (globalize && opt.soft_resto && soft_step()) outcome = OUT_ACCEPTED;
+          break;
+        }
       }
     }
   }
@@ -813,11 +1078,17 @@ __device__ __noinline__ void iterate(Ctx<TB, TF>& c, SlotState& S) {
     S.status = BIPM_RESTO_FAILED;
     return;
   }
+  if (wd_restored) {
+    // the failed search ran from the watchdog's stored iterate: restoration starts there
+    f_orig = eval_values(c, w, cv);
+    theta = l1_norm(c, cv, m);
+  }
   if (theta <= opt.tol) {
     S.status = BIPM_RESTO_FAILED;
     return;
   }
   // enter restoration (IPOPT Sec. 3.3 reading)
+  end_globalization(S);
   {
     double phi = barrier_phi(c, w, f_orig, S.mu, n);
     filter_add(c, filt, nf, (1.0 - kGammaTheta) * theta, phi - kGammaPhi * theta);

@@ -14,11 +14,11 @@ constexpr int kBulkVisit = 64;     // iterations per problem in the warp kernel
 constexpr int kQueueVisit = 96;    // iterations before a queue problem is parked for block teams
 constexpr int kMaxClasses = 64;    // structure classes of one mixed queue
 
-template <class TB, class TF>
-__device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, int T, double* red,
+template <class TB, class TF, int NQ>
+__device__ void make_ctx(Ctx<TB, TF, NQ>& c, const Params* P, int slot, int lane, int T, double* red,
                          char* smem) {
   c.P = P;
-  c.d = P->d;
+  static_cast<Dims&>(c.d) = P->d;
   c.L = P->L;
   c.lane = lane;
   c.T = T;
@@ -53,8 +53,8 @@ __device__ void make_ctx(Ctx<TB, TF>& c, const Params* P, int slot, int lane, in
 }
 
 // final objective, scaled KKT error and infeasibility of the original problem
-template <class TB, class TF>
-__device__ void slot_metrics(Ctx<TB, TF>& c, SlotState& S) {
+template <class TB, class TF, int NQ>
+__device__ void slot_metrics(Ctx<TB, TF, NQ>& c, SlotState& S) {
   c.resto = 0;
   c.nw = c.d.n;
   double* w = c.f + c.L.x;
@@ -70,8 +70,8 @@ __device__ void slot_metrics(Ctx<TB, TF>& c, SlotState& S) {
 }
 
 // true (in every thread of the team) once the call's time budget has run out
-template <class TB, class TF>
-__device__ __forceinline__ bool team_budget_spent(Ctx<TB, TF>& c) {
+template <class TB, class TF, int NQ>
+__device__ __forceinline__ bool team_budget_spent(Ctx<TB, TF, NQ>& c) {
   if (c.P->time_limit_ns == 0) return false;
   int v = 0;
   if (c.lane == 0) v = budget_spent(c.P) ? 1 : 0;
@@ -82,8 +82,8 @@ __device__ __forceinline__ bool team_budget_spent(Ctx<TB, TF>& c) {
 // terminates, or (visit_cap > 0) for at most visit_cap iterations in this visit.
 // Before every iteration the call's time budget is checked; returns true if the
 // slot stopped because it ran out (the problem is left running, resumable).
-template <class TB, class TF>
-__device__ bool run_slot(Ctx<TB, TF>& c, SlotState& S, int n_iter, int visit_cap) {
+template <class TB, class TF, int NQ>
+__device__ bool run_slot(Ctx<TB, TF, NQ>& c, SlotState& S, int n_iter, int visit_cap) {
   int done = 0;
   bool spent = false;
   if (n_iter > 0) {
@@ -105,7 +105,7 @@ __device__ bool run_slot(Ctx<TB, TF>& c, SlotState& S, int n_iter, int visit_cap
 // Persistent kernel, one warp per problem: each warp takes the next slot from
 // the work counter and iterates it (iteration-level batching: a warp that
 // finishes a problem immediately starts another one).
-template <class TB, class TF>
+template <class TB, class TF, int NQ>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     ipm_kernel(const Params* __restrict__ P, int n_iter, int visit_cap) {
   extern __shared__ __align__(16) char smem_all[];
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     if (slot >= P->n_slots) break;
     SlotState S = P->st[slot];
     if (S.status != BIPM_RUNNING) continue;
-    Ctx<TB, TF> c;
+    Ctx<TB, TF, NQ> c;
     make_ctx(c, P, slot, lane, 32, nullptr, smem);
     run_slot(c, S, n_iter, visit_cap);
     __syncwarp();
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
 // block's threads spread over all four SM sub-partitions, for the few
 // long-running problems left after the warp kernel (their per-iteration
 // latency, not the batch throughput, bounds the solve).
-template <class TB, class TF>
+template <class TB, class TF, int NQ>
 __global__ void __launch_bounds__(kBlockTeam)
     ipm_block_kernel(const Params* __restrict__ P, int n_iter) {
   extern __shared__ __align__(16) char smem_all[];
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kBlockTeam)
     if (slot >= P->n_slots) break;
     SlotState S = P->st[slot];
     if (S.status != BIPM_RUNNING) continue;
-    Ctx<TB, TF> c;
+    Ctx<TB, TF, NQ> c;
     make_ctx(c, P, slot, (int)threadIdx.x, (int)blockDim.x, red, smem);
     run_slot(c, S, n_iter, 0);
     __syncthreads();
@@ -231,11 +231,12 @@ __device__ __forceinline__ SlotState init_slot(const Params* P, int slot, int la
   S.need_init = 1;
   S.need_y_ls = yguess ? 0 : 1;
   S.mu = warm ? P->opt.warm_mu : P->opt.mu_init;
+  S.mu_free = 1;  // the adaptive barrier update starts in free mode
   S.problem_id = slot;
   return S;
 }
 
-template <class TB, class TF>
+template <class TB, class TF, int NQ>
 __global__ void init_kernel(const Params* __restrict__ P, int first, int count,
                             const double* __restrict__ guess, const double* __restrict__ yguess) {
   const int lane = threadIdx.x & 31;
@@ -290,7 +291,7 @@ __device__ __forceinline__ bool queue_budget_spent(const Params* P, int lane) {
   return __shfl_sync(0xffffffffu, v, 0) != 0;
 }
 
-template <class TB, class TF>
+template <class TB, class TF, int NQ>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     queue_kernel(const Params* __restrict__ P, const double* __restrict__ theta_q, int n_queue,
                  int n_warps, double* __restrict__ x_out, bipm_result* __restrict__ res_out,
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     const double* gq = x_guess ? x_guess + (long long)id * d.n : nullptr;
     SlotState S = init_slot(P, slot, lane, gq, nullptr, gq != nullptr);
     S.problem_id = id;
-    Ctx<TB, TF> c;
+    Ctx<TB, TF, NQ> c;
     make_ctx(c, P, slot, lane, 32, nullptr, smem);
     int warm = gq ? 1 : 0, warm_iters = 0;
     bool done = false, spent = false;
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
 // parameters at theta_q + th_off[id] and its solution row at x_out + x_off[id].
 // smem_stride: shared-memory bytes per warp of the launch.  Stragglers are
 // parked as in queue_kernel and finished by block_mixed_kernel.
-template <class TB, class TF>
+template <class TB, class TF, int NQ>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     queue_mixed_kernel(const Params* __restrict__ Pc, const int* __restrict__ cls,
                        const long long* __restrict__ th_off, const long long* __restrict__ x_off,
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     SlotState S = init_slot(P, slot, lane, nullptr, nullptr, 0);
     S.problem_id = id;
     S.cls = k;
-    Ctx<TB, TF> c;
+    Ctx<TB, TF, NQ> c;
     make_ctx(c, P, slot, lane, 32, nullptr, smem);
     const bool spent = run_slot(c, S, 0, P->visit_cap);
     if (S.status == BIPM_RUNNING && !spent) {
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
 
 // Block teams finish the parked problems of a mixed queue (each slot's class
 // is recorded in its state).
-template <class TB, class TF>
+template <class TB, class TF, int NQ>
 __global__ void __launch_bounds__(kBlockTeam)
     block_mixed_kernel(const Params* __restrict__ Pc) {
   extern __shared__ __align__(16) char smem_all[];
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(kBlockTeam)
     SlotState S = P0->st[slot];
     if (S.status != BIPM_RUNNING) continue;
     const Params* P = Pc + S.cls;
-    Ctx<TB, TF> c;
+    Ctx<TB, TF, NQ> c;
     make_ctx(c, P, slot, (int)threadIdx.x, (int)blockDim.x, red, smem);
     run_slot(c, S, 0, 0);
     __syncthreads();
@@ -468,19 +469,29 @@ __global__ void __launch_bounds__(kBlockTeam)
 // offsets of the per-slot arrays for problems of dims d (host)
 Layout make_layout(const Dims& d, int precision);
 
-// host-side accessors of the kernel entry points of one precision
+// host-side accessors of the kernel entry points of one precision; the _q1
+// variants are specialised for one quadrotor per problem
 void* iter_kernel_f64();
 void* init_kernel_f64();
 void* queue_kernel_f64();
-void* queue_kernel_f32();
 void* block_kernel_f64();
 void* iter_kernel_f32();
 void* init_kernel_f32();
+void* queue_kernel_f32();
 void* block_kernel_f32();
 void* iter_kernel_df();
 void* init_kernel_df();
 void* block_kernel_df();
 void* queue_kernel_df();
+void* iter_kernel_f64_q1();
+void* queue_kernel_f64_q1();
+void* block_kernel_f64_q1();
+void* iter_kernel_f32_q1();
+void* queue_kernel_f32_q1();
+void* block_kernel_f32_q1();
+void* iter_kernel_df_q1();
+void* queue_kernel_df_q1();
+void* block_kernel_df_q1();
 void* queue_mixed_f64();
 void* queue_mixed_f32();
 void* block_mixed_f64();

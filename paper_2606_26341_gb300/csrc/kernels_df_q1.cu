@@ -1,0 +1,8 @@
+// Double-float factorisation instantiation of the solver kernels specialised for one
+// quadrotor per problem (12 states, 4 inputs fixed at compile time).
+#include "kernels.cuh"
+
+namespace bipm {
+void* iter_kernel_df_q1() { return (void*)ipm_kernel<float, df, 1>; }
+void* queue_kernel_df_q1() { return (void*)queue_kernel<float, df, 1>; }
+}  // namespace bipm

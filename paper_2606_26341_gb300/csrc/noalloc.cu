@@ -97,7 +97,7 @@ int bipm_solve_static(const bipm_problem_desc* desc, const bipm_options* opt, co
   if ((rc = workspace_ptr(&base))) return rc;
 
   // one slot per resident warp, at most one per problem and per what fits
-  void* kfn = o.precision == 2 ? queue_kernel_df() : o.precision ? queue_kernel_f32() : queue_kernel_f64();
+  void* kfn = queue_kernel_ptr(o.precision, d.nq);
   int smem_per_warp;
   {
     size_t need = scratch_bytes(d.nq, d.nx, d.nu, o.precision == 1 ? 4 : 8);

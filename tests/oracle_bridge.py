@@ -25,7 +25,15 @@ def oracle_to_iterate(nlp, st: ipm.SolverState) -> dict:
         "tiny": int(ph.tiny), "mu": ph.mu, "dw_last": ph.dw_last,
         "theta_max": ph.theta_max, "theta_min": ph.theta_min,
         "filter": np.array(ph.filt, dtype=np.float64).reshape(-1, 2),
+        "wd_short": int(ph.wd_short), "wd_active": int(ph.wd_active), "wd_trials": int(ph.wd_trials),
+        "soft_active": int(ph.soft_active), "soft_iters": int(ph.soft_iters),
+        "mu_free": int(ph.mu_free), "mu_refs": list(ph.mu_refs), "mu_max": ph.mu_max,
     }
+    if ph.wd_store is not None:
+        W = ph.wd_store
+        out.update(wd_x=W["x"], wd_y=W["y"], wd_zl=W["zl"], wd_zu=W["zu"], wd_dx=W["dx"], wd_dy=W["dy"],
+                   wd_theta=W["theta"], wd_phi=W["phi"], wd_gdx=W["gdx"], wd_amax=W["a_max"],
+                   wd_amin=W["a_min"])
     if st.mode == ipm.NORMAL:
         out.update(x=ph.x, y=ph.y, zl=ph.zl, zu=ph.zu)
     else:
@@ -40,11 +48,23 @@ def oracle_to_iterate(nlp, st: ipm.SolverState) -> dict:
 
 
 def compare_vector(state: dict) -> np.ndarray:
-    """Quantities compared by e_v: the active iterate and the barrier parameter(s)."""
+    """Quantities compared by e_v: the active iterate and the barrier parameter(s),
+    and the watchdog's stored iterate and step while it is active."""
     parts = [state["x"], state["y"], state["zl"], state["zu"], [state["mu"]]]
     if state["mode"] == ipm.RESTO:
         parts += [state["p"], state["nn"], state["zp"], state["zn"], [state["mu_r"]]]
+    refs = list(state.get("mu_refs", []))
+    parts += [refs, [state.get("mu_max", 0.0)]]
+    if state.get("wd_active"):
+        parts += [state["wd_x"], state["wd_y"], state["wd_zl"], state["wd_zu"], state["wd_dx"], state["wd_dy"],
+                  [state["wd_theta"], state["wd_phi"], state["wd_gdx"], state["wd_amax"], state["wd_amin"]]]
     return np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in parts])
+
+
+def globalization_state(state: dict) -> tuple:
+    """The discrete watchdog / soft-restoration state of an iterate record."""
+    return tuple(int(state.get(k, 0)) for k in ("wd_short", "wd_active", "wd_trials", "soft_active", "soft_iters",
+                                                 "mu_free")) + (len(state.get("mu_refs", [])),)
 
 
 def e_v(v, v_ref) -> float:

@@ -177,3 +177,21 @@ def test_cost_and_constraint_values_by_hand():
     assert np.isclose(nlp.f(w), expect, rtol=1e-14)
     cen, rad = nlp.sph[0, 0:3].numpy(), float(nlp.sph[0, 3])
     assert np.allclose(s.numpy(), np.sum((p0 - cen) ** 2) - rad ** 2)
+
+
+@pytest.mark.parametrize("case", ["nav1", "track", "pairs_cyl"])
+def test_stage_assembled_derivatives_equal_whole_vector_autograd(case):
+    """The oracle assembles the constraint Jacobian and the Lagrangian Hessian
+    from per-stage autograd; differentiating the whole decision vector at once
+    must give the same matrices (sparsity placement, signs of the dynamics rows,
+    multiplier indexing, the objective factor)."""
+    desc = None if case != "pairs_cyl" else ProblemDesc(nq=3, horizon=4, dt=0.05, n_sph=1, n_cyl=2, pair_dist=0.4)
+    name = "multi4" if case == "pairs_cyl" else case
+    d, th = make_batch(name, 1, desc=desc)
+    nlp = Q.QuadNLP(d, th[0])
+    rng = np.random.default_rng(7)
+    x = nlp.default_start() + 0.1 * rng.standard_normal(nlp.n)
+    y = rng.standard_normal(nlp.m)
+    assert np.allclose(nlp.jac_c(x), nlp.jac_c_whole(x), rtol=0, atol=1e-12)
+    for of in (1.0, 0.0, 2.5):
+        assert np.allclose(nlp.hess_lag(x, y, of), nlp.hess_lag_whole(x, y, of), rtol=0, atol=1e-11)

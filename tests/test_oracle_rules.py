@@ -521,3 +521,71 @@ def test_soft_restoration_step_reduces_the_primal_dual_error():
             checked += 1
             assert e_t <= (1 - opt.kappa_soft) * L["e_current"]
     assert tried >= 1
+
+
+# ------------------------------------------ adaptive barrier update (row 7) --
+
+def test_loqo_centrality_rule():
+    """xi = min / average; sigma = 0.1 min(0.05 (1 - xi) / xi, 2)^3; mu = sigma * average.
+    avg = 1, min = 0.5: xi = 0.5, 0.05 * 0.5 / 0.5 = 0.05, sigma = 0.1 * 1.25e-4 = 1.25e-5.
+    avg = 2, min = 0.02: xi = 0.01, 0.05 * 0.99 / 0.01 = 4.95 -> 2, sigma = 0.8, mu = 1.6.
+    Perfect centrality (min = avg) gives mu = 0."""
+    assert ipm.loqo_mu(1.0, 0.5) == rel(1.25e-5, 1e-12)
+    assert ipm.loqo_mu(2.0, 0.02) == rel(1.6, 1e-14)
+    assert ipm.loqo_mu(3.0, 3.0) == 0.0
+    assert ipm.loqo_mu(1.0, 0.0) == rel(0.8, 1e-15)
+
+
+def test_complementarity_statistics():
+    """x0 in [0, 2] at 0.5 with z_L = 2, z_U = 1; x1 >= 0 at 3 with z_L = 0.1: products
+    1.0, 1.5 and 0.3 -> average 0.9333, minimum 0.3."""
+    nlp = TorchNLP(lambda x: x.sum(), None, 2, 0, xl=[0.0, 0.0], xu=[2.0, np.inf])
+    avg, mn = ipm.complementarity_stats(nlp, np.array([0.5, 3.0]), np.array([2.0, 0.1]), np.array([1.0, 0.0]))
+    assert avg == rel(2.8 / 3.0, 1e-15) and mn == rel(0.3, 1e-15)
+
+
+def test_progress_test_and_references():
+    """Progress: E_0 <= 0.9999 max(refs); empty refs always progress; at most four kept."""
+    refs = []
+    assert ipm.sufficient_progress(5.0, refs, OPT)
+    for e in (4.0, 3.0, 2.0, 1.0, 0.5):
+        ipm.remember_reference(refs, e, OPT)
+    assert refs == [3.0, 2.0, 1.0, 0.5]
+    assert ipm.sufficient_progress(2.9997, refs, OPT)
+    assert not ipm.sufficient_progress(2.9998, refs, OPT)
+
+
+def test_adaptive_barrier_update_modes():
+    """Free mode with progress: mu = LOQO, clipped to [1e-11, mu_max]; without progress
+    (or after a tiny step) the fixed mode starts at 0.8 * average complementarity;
+    fixed mode returns to free mode once the barrier problem is solved with progress,
+    and otherwise follows the monotone rule."""
+    opt = ipm.Options(mu_strategy="adaptive")
+    ph = _phase()
+    ph.mu, ph.mu_max = 0.1, 10.0
+    mu, changed, stall = ipm.adaptive_barrier_update(ph, 1.0, lambda m: 0.0, 2.0, 0.02, False, opt)
+    assert (mu, ph.mu_free, ph.mu_refs) == (pytest.approx(1.6), True, [1.0]) and changed and not stall
+    ph.mu = mu
+    ph.mu_max = 1.0  # the cap applies
+    mu, _, _ = ipm.adaptive_barrier_update(ph, 0.5, lambda m: 0.0, 2.0, 0.02, False, opt)
+    assert mu == 1.0 and ph.mu_refs == [1.0, 0.5]
+    ph.mu = mu
+    # no progress (0.99995 > 0.9999 * 1.0): fixed mode at 0.8 * average
+    mu, changed, _ = ipm.adaptive_barrier_update(ph, 0.99995, lambda m: 0.0, 0.5, 0.1, False, opt)
+    assert not ph.mu_free and mu == rel(0.4, 1e-15) and changed
+    ph.mu = mu
+    # fixed mode, barrier problem not solved (E_mu > 10 mu): unchanged
+    mu, changed, _ = ipm.adaptive_barrier_update(ph, 0.1, lambda m: 100.0, 0.5, 0.1, False, opt)
+    assert mu == 0.4 and not changed and not ph.mu_free
+    # solved, but no progress against the references: the monotone rule, whose fast
+    # decrease (E_mu = 0 at every mu) runs down to the floor tol / 10
+    mu, changed, _ = ipm.adaptive_barrier_update(ph, 5.0, lambda m: 0.0, 0.5, 0.1, False, opt)
+    assert changed and not ph.mu_free and mu == 1e-7
+    ph.mu = mu
+    # solved with progress: free mode again, references restart from E_0
+    mu, changed, _ = ipm.adaptive_barrier_update(ph, 0.1, lambda m: 0.0, 2.0, 0.02, False, opt)
+    assert ph.mu_free and ph.mu_refs == [0.1] and mu == rel(1.0, 1e-15)  # LOQO 1.6 capped at 1.0
+    # a tiny step in free mode switches to the fixed mode
+    ph.mu = mu
+    ipm.adaptive_barrier_update(ph, 0.01, lambda m: 0.0, 0.5, 0.1, True, opt)
+    assert not ph.mu_free
