@@ -18,13 +18,15 @@
  * Layouts (one problem; double precision):
  *   theta : xbar (12 nq) | reference circles (6 nq: cx, cy, cz, radius, rate,
  *           phase; radius 0 = fixed goal) | spheres (4 n_spheres: cx, cy, cz, r) |
- *           cylinders (3 n_cylinders: cx, cy, r)
+ *           cylinders (3 n_cylinders: cx, cy, r) | moving spheres (7 n_moving:
+ *           cx, cy, cz, r, vx, vy, vz; centre at time t: c + v t)
  *   x     : for k = 0..N: x_k (12 nq), then u_k (4 nq) if k < N, then s_k (ni)
  *           if k >= 1; n = 12nq(N+1) + (4nq + ni) N
  *   y     : x_0 - xbar (12 nq), then for k = 0..N-1: dynamics rows
  *           x_{k+1} - F(x_k, u_k) (12 nq), then stage-(k+1) inequality rows
  *           (ni); m = 12nq(N+1) + ni N
- *   ni    : nq * n_spheres + nq * n_cylinders + (pair_dist > 0 ? nq(nq-1)/2 : 0)
+ *   ni    : nq * (n_spheres + n_cylinders + n_moving) + (pair_dist > 0 ? nq(nq-1)/2 : 0),
+ *           in that order (obstacle rows quadrotor-major, pairs last)
  *
  * Ownership: the batch owns all device memory it uses; caller buffers are
  * only read or written during the call.  `on_device` = 1 means the pointer is
@@ -87,6 +89,9 @@ typedef struct {
   int n_spheres;      /* spherical obstacles (applied to every quadrotor) */
   int n_cylinders;    /* vertical cylinders (applied to every quadrotor) */
   double pair_dist;   /* minimum pairwise distance; 0 disables the pair rows */
+  int n_moving;       /* moving spherical obstacles (applied to every quadrotor):
+                         centre c + v t at the stage time t = k dt, known in
+                         advance (the time-varying obstacles of Sec. VI) */
 } bipm_problem_desc;
 
 /* Algorithm options (Sec. IV; the constants the paper defers to IPOPT are

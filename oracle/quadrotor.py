@@ -16,8 +16,10 @@ leaves open are fixed by these readings:
   Q = diag(10 I3, I3, I3, 0.1 I3), R = 0.1 I4, Q_N = 10 Q (no factor 1/2);
 * inequalities at stages 1..N, squared-distance form g(x) - s = 0, s >= 0:
   spheres |p_i - c|^2 - r^2, cylinders (p_ix - cx)^2 + (p_iy - cy)^2 - r^2,
-  pairs |p_i - p_j|^2 - d^2; order: spheres (quad-major), cylinders
-  (quad-major), then pairs (i < j, lexicographic);
+  moving spheres |p_i - (c + v k dt)|^2 - r^2 at stage k (time-varying
+  obstacles with known trajectories, Sec. VI), pairs |p_i - p_j|^2 - d^2;
+  order: spheres, cylinders, moving spheres (each quad-major), then pairs
+  (i < j, lexicographic);
 * variable order: for k = 0..N: x_k, then u_k (k < N), then s_k (k >= 1);
   equality order: x_0 - xbar, then for k = 0..N-1 the dynamics rows
   x_{k+1} - F(x_k, u_k) followed by the stage-(k+1) inequality rows.
@@ -98,6 +100,7 @@ class QuadNLP:
         self.ref = th[lay["ref"]:lay["ref"] + 6 * self.nq].reshape(self.nq, 6)
         self.sph = th[lay["sph"]:lay["sph"] + 4 * d.n_sph].reshape(d.n_sph, 4)
         self.cyl = th[lay["cyl"]:lay["cyl"] + 3 * d.n_cyl].reshape(d.n_cyl, 3)
+        self.mov = th[lay["mov"]:lay["mov"] + 7 * d.n_mov].reshape(d.n_mov, 7)
         self.pairs = [(i, j) for i in range(self.nq) for j in range(i + 1, self.nq)] \
             if d.pair_dist > 0 else []
 
@@ -142,9 +145,14 @@ class QuadNLP:
     def split(self, w):
         return w[self.xi], w[self.ui], w[self.si]
 
-    def ineq(self, xs):
-        """Inequality values g(x_k) for the given stacked states (K, nx) -> (K, ni)."""
+    def ineq(self, xs, ks=None):
+        """Inequality values g(x_k) for the given stacked states (K, nx) -> (K, ni);
+        ks are the stage indices of the rows (default 1..K: the states x_1..x_N),
+        which place the moving spheres at time k dt."""
         p = xs.reshape(xs.shape[0], self.nq, 12)[..., 0:3]
+        if ks is None:
+            ks = torch.arange(1, xs.shape[0] + 1, dtype=F64)
+        t = torch.as_tensor(ks, dtype=F64).reshape(-1) * self.dt
         out = []
         for i in range(self.nq):
             for j in range(self.sph.shape[0]):
@@ -154,6 +162,11 @@ class QuadNLP:
             for j in range(self.cyl.shape[0]):
                 cx, cy, rad = self.cyl[j]
                 out.append((p[:, i, 0] - cx) ** 2 + (p[:, i, 1] - cy) ** 2 - rad ** 2)
+        for i in range(self.nq):
+            for j in range(self.mov.shape[0]):
+                c0, rad, v = self.mov[j, 0:3], self.mov[j, 3], self.mov[j, 4:7]
+                cen = c0 + t.reshape(-1, 1) * v          # centre at each row's stage time
+                out.append(((p[:, i] - cen) ** 2).sum(-1) - rad ** 2)
         dd = self.desc.pair_dist
         for (i, j) in self.pairs:
             out.append(((p[:, i] - p[:, j]) ** 2).sum(-1) - dd ** 2)
@@ -208,8 +221,8 @@ class QuadNLP:
         u = z[self.nx:].reshape(self.nq, 4)
         return rk4(x, u, self.dt).reshape(self.nx)
 
-    def _ineq1(self, xk):
-        return self.ineq(xk.reshape(1, -1))[0]
+    def _ineq1(self, xk, k):
+        return self.ineq(xk.reshape(1, -1), k.reshape(1))[0]
 
     def _stage_cost(self, z, r):
         """Cost of interval k < N from z = (x_k, u_k) and the reference r = x^ref_k."""
@@ -230,7 +243,8 @@ class QuadNLP:
         J[np.arange(nx), xi[0]] = 1.0
         Z = torch.cat([x[:-1], u], dim=1)
         Jd = torch.func.vmap(torch.func.jacfwd(self._dyn))(Z).numpy()
-        Jg = torch.func.vmap(torch.func.jacfwd(self._ineq1))(x[1:]).numpy() if ni else None
+        ks = torch.arange(1, N + 1, dtype=F64)
+        Jg = torch.func.vmap(torch.func.jacfwd(self._ineq1))(x[1:], ks).numpy() if ni else None
         row = nx
         for k in range(N):
             J[row:row + nx][:, np.concatenate([xi[k], ui[k]])] = -Jd[k]
@@ -267,8 +281,9 @@ class QuadNLP:
             H[np.ix_(xi[N], xi[N])] += obj_factor * Ht
         if ni:
             yin = torch.stack([yt[nx + k * blk + nx: nx + (k + 1) * blk] for k in range(N)])
-            Hg = torch.func.vmap(torch.func.hessian(lambda xk, lam: (lam * self._ineq1(xk)).sum()))(
-                x[1:], yin).numpy()
+            ks = torch.arange(1, N + 1, dtype=F64)
+            Hg = torch.func.vmap(torch.func.hessian(lambda xk, lam, k: (lam * self._ineq1(xk, k)).sum()))(
+                x[1:], yin, ks).numpy()
             for k in range(N):
                 H[np.ix_(xi[k + 1], xi[k + 1])] += Hg[k]
         return H
@@ -290,6 +305,6 @@ class QuadNLP:
         w[self.xi] = self.xbar
         w[self.ui] = self.uh
         if self.ni > 0:
-            g = self.ineq(self.xbar.reshape(1, -1))[0]
-            w[self.si] = g
+            # g(xbar) at every stage (moving spheres sit at each stage's time)
+            w[self.si] = self.ineq(self.xbar.reshape(1, -1).repeat(self.N, 1))
         return w.numpy()

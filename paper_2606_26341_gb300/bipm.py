@@ -26,7 +26,13 @@ FILTER_CAP = 64
 class ProblemDescC(ctypes.Structure):
     _fields_ = [("n_quads", ctypes.c_int), ("horizon", ctypes.c_int), ("dt", ctypes.c_double),
                 ("n_spheres", ctypes.c_int), ("n_cylinders", ctypes.c_int),
-                ("pair_dist", ctypes.c_double)]
+                ("pair_dist", ctypes.c_double), ("n_moving", ctypes.c_int)]
+
+
+def desc_c(desc):
+    """The C record of a workloads.ProblemDesc."""
+    return ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist,
+                        getattr(desc, "n_mov", 0))
 
 
 class OptionsC(ctypes.Structure):
@@ -173,7 +179,7 @@ def solve_static(desc, theta_dev, x_out=None, results=None, options: "Options | 
     x_out: optional CUDA float64 tensor (count x n); results: CUDA uint8 tensor of
     count * RESULT_DTYPE.itemsize bytes (read back with results_from_bytes)."""
     lib = load_library()
-    d = ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist)
+    d = desc_c(desc)
     o = options or Options()
     oc = o.to_c()
     sp = _stream_ptr(stream)
@@ -242,7 +248,7 @@ class Batch:
 
     def __init__(self, desc, capacity: int, options: Options | None = None, stream=None):
         self.lib = load_library()
-        d = ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist)
+        d = desc_c(desc)
         o = options or Options()
         oc = o.to_c()
         h = ctypes.c_void_p()
@@ -413,7 +419,7 @@ class Batch:
 
 # ------------------------------------------------------------------ warm start
 def _desc_c(desc):
-    return ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist)
+    return desc_c(desc)
 
 
 def _dev_ptr(t, dtype_name):
@@ -555,8 +561,7 @@ def solve_mixed(classes, cls, theta, n_slots: int, options: "Options | None" = N
     x_out: packed solution rows or None.  Host mode returns the result records
     as a dict of arrays; device mode fills `results` (CUDA uint8 tensor)."""
     lib = load_library()
-    arr = (ProblemDescC * len(classes))(*[ProblemDescC(c.nq, c.horizon, c.dt, c.n_sph, c.n_cyl, c.pair_dist)
-                                           for c in classes])
+    arr = (ProblemDescC * len(classes))(*[desc_c(c) for c in classes])
     oc = (options or Options()).to_c()
     cls = np.ascontiguousarray(cls, dtype=np.int32)
     nq = int(cls.shape[0])

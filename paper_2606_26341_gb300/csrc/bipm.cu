@@ -60,6 +60,7 @@ int dims_from_desc(const bipm_problem_desc* desc, Dims* out) {
   if (desc->n_spheres < 0 || desc->n_cylinders < 0 || desc->n_spheres > 256 || desc->n_cylinders > 256)
     return fail(BIPM_EINVAL, "obstacle counts must be 0..256");
   if (!(desc->pair_dist >= 0.0)) return fail(BIPM_EINVAL, "pair_dist must be >= 0");
+  if (desc->n_moving < 0 || desc->n_moving > 256) return fail(BIPM_EINVAL, "n_moving must be 0..256");
   Dims d;
   std::memset(&d, 0, sizeof(d));
   d.nq = desc->n_quads;
@@ -68,8 +69,9 @@ int dims_from_desc(const bipm_problem_desc* desc, Dims* out) {
   d.nu = 4 * d.nq;
   d.n_sph = desc->n_spheres;
   d.n_cyl = desc->n_cylinders;
+  d.n_mov = desc->n_moving;
   d.n_pairs = desc->pair_dist > 0.0 ? d.nq * (d.nq - 1) / 2 : 0;
-  d.ni = d.nq * d.n_sph + d.nq * d.n_cyl + d.n_pairs;
+  d.ni = d.nq * (d.n_sph + d.n_cyl + d.n_mov) + d.n_pairs;
   d.n = d.nx * (d.N + 1) + (d.nu + d.ni) * d.N;
   d.m = d.nx * (d.N + 1) + d.ni * d.N;
   d.dt = desc->dt;
@@ -78,7 +80,8 @@ int dims_from_desc(const bipm_problem_desc* desc, Dims* out) {
   d.th_ref = 12 * d.nq;
   d.th_sph = d.th_ref + 6 * d.nq;
   d.th_cyl = d.th_sph + 4 * d.n_sph;
-  d.n_theta = d.th_cyl + 3 * d.n_cyl;
+  d.th_mov = d.th_cyl + 3 * d.n_cyl;
+  d.n_theta = d.th_mov + 7 * d.n_mov;
   *out = d;
   return 0;
 }

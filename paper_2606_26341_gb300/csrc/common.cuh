@@ -138,11 +138,11 @@ enum VarKind : int { VK_FREE = 0, VK_BOX = 1, VK_LOWER = 2 };
 // ------------------------------------------------------------ problem layout
 struct Dims {
   int nq, N, nx, nu, ni, n, m;
-  int n_sph, n_cyl, n_pairs;
+  int n_sph, n_cyl, n_pairs, n_mov;
   int n_theta;
   double dt, pair_d;
   // offsets inside theta
-  int th_x, th_ref, th_sph, th_cyl;
+  int th_x, th_ref, th_sph, th_cyl, th_mov;
 };
 
 // Dims with the per-quadrotor sizes fixed at compile time: NQ quadrotors per

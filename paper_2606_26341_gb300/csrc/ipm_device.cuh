@@ -205,14 +205,40 @@ struct IneqRow {
   double hdiag;    // Hessian of g: hdiag * (I on involved components); pairs: +-hdiag
 };
 
+// Centre of moving sphere o at stage k (time k dt): c + v k dt.
+template <class D>
+__device__ __forceinline__ void moving_centre(const D& d, const double* th, int o, int k, double* cen) {
+  const double* s = th + d.th_mov + 7 * o;
+  const double t = k * d.dt;
+  cen[0] = s[0] + s[4] * t;
+  cen[1] = s[1] + s[5] * t;
+  cen[2] = s[2] + s[6] * t;
+}
+
 template <class D>
 __device__ __forceinline__ IneqRow ineq_row(const D& d, const double* th, const double* xk,
-                                            int j) {
+                                            int j, int k) {
   IneqRow r;
   r.q1 = -1;
   r.hdiag = 2.0;
   int nsq = d.nq * d.n_sph;
   int ncq = d.nq * d.n_cyl;
+  int nmq = d.nq * d.n_mov;
+  if (j >= nsq + ncq && j < nsq + ncq + nmq) {
+    const int jj = j - nsq - ncq;
+    const int q = jj / d.n_mov, o = jj - q * d.n_mov;
+    double cen[3];
+    moving_centre(d, th, o, k, cen);
+    const double* p = xk + 12 * q;
+    const double rad = th[d.th_mov + 7 * o + 3];
+    double dx = p[0] - cen[0], dy = p[1] - cen[1], dz = p[2] - cen[2];
+    r.q0 = q;
+    r.ncomp = 3;
+    r.gval = dx * dx + dy * dy + dz * dz - rad * rad;
+    r.grad[0] = 2 * dx; r.grad[1] = 2 * dy; r.grad[2] = 2 * dz;
+    return r;
+  }
+  if (j >= nsq + ncq) j -= nmq;  // pair rows follow the moving spheres
   if (j < nsq) {
     int q = j / d.n_sph, o = j - (j / d.n_sph) * d.n_sph;
     const double* s = th + d.th_sph + 4 * o;
@@ -257,10 +283,22 @@ struct IneqGrad {
   double g[3];
 };
 template <class D>
-__device__ __forceinline__ IneqGrad ineq_grad(const D& d, const double* th, const double* xk, int j) {
+__device__ __forceinline__ IneqGrad ineq_grad(const D& d, const double* th, const double* xk, int j, int k) {
   IneqGrad r;
   r.q1 = -1;
-  const int nsq = d.nq * d.n_sph, ncq = d.nq * d.n_cyl;
+  const int nsq = d.nq * d.n_sph, ncq = d.nq * d.n_cyl, nmq = d.nq * d.n_mov;
+  if (j >= nsq + ncq && j < nsq + ncq + nmq) {
+    const int jj = j - nsq - ncq;
+    const int q = jj / d.n_mov, o = jj - q * d.n_mov;
+    double cen[3];
+    moving_centre(d, th, o, k, cen);
+    const double* p = xk + 12 * q;
+    r.q0 = q;
+    r.ncomp = 3;
+    r.g[0] = 2 * (p[0] - cen[0]); r.g[1] = 2 * (p[1] - cen[1]); r.g[2] = 2 * (p[2] - cen[2]);
+    return r;
+  }
+  if (j >= nsq + ncq) j -= nmq;
   if (j < nsq) {
     const int q = j / d.n_sph, o = j - q * d.n_sph;
     const double* s = th + d.th_sph + 4 * o;
@@ -296,7 +334,17 @@ template <class D>
 __device__ __forceinline__ IneqGrad ineq_grad_tab(const D& d, const double* igr, int t, int j) {
   IneqGrad r;
   r.q1 = -1;
-  const int nsq = d.nq * d.n_sph, ncq = d.nq * d.n_cyl;
+  const int nsq = d.nq * d.n_sph, ncq = d.nq * d.n_cyl, nmq = d.nq * d.n_mov;
+  if (j >= nsq + ncq && j < nsq + ncq + nmq) {
+    r.q0 = (j - nsq - ncq) / d.n_mov;
+    r.ncomp = 3;
+    const double* g = igr + 3LL * t;
+    r.g[0] = g[0];
+    r.g[1] = g[1];
+    r.g[2] = g[2];
+    return r;
+  }
+  if (j >= nsq + ncq) j -= nmq;
   if (j < nsq) {
     r.q0 = j / d.n_sph;
     r.ncomp = 3;
@@ -359,7 +407,7 @@ __device__ __noinline__ double eval_values(Ctx<TB, TF, NQ>& c, const double* x, 
   }
   for (int t = lane; t < d.N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, j = t - (t / d.ni) * d.ni;
-    IneqRow r = ineq_row(d, c.th, x + off_x(d, k), j);
+    IneqRow r = ineq_row(d, c.th, x + off_x(d, k), j, k);
     cout[row_ineq(d, k) + j] = r.gval - x[off_s(d, k) + j];
   }
   double fs = 0.0;
@@ -530,7 +578,7 @@ __device__ __noinline__ void eval_jty(Ctx<TB, TF, NQ>& c, const double* x, const
     const double* xk = x + off_x(d, k);
     const double* yi = y + row_ineq(d, k);
     double acc = 0.0;
-    for (int r = 0; r < d.ni; ++r) acc += grad_pos(ineq_grad(d, c.th, xk, r), q, comp) * yi[r];
+    for (int r = 0; r < d.ni; ++r) acc += grad_pos(ineq_grad(d, c.th, xk, r, k), q, comp) * yi[r];
     jty[off_x(d, k) + i] += acc;
   }
   for (int t = lane; t < d.N * d.ni; t += c.T) {
@@ -599,7 +647,7 @@ __device__ __noinline__ void fill_ineq_grad(Ctx<TB, TF, NQ>& c, const double* x)
   double* igr = c.f + c.L.igr;
   for (int t = c.lane; t < d.N * d.ni; t += c.T) {
     const int k = 1 + t / d.ni, j = t - (k - 1) * d.ni;
-    const IneqGrad g = ineq_grad(d, c.th, x + off_x(d, k), j);
+    const IneqGrad g = ineq_grad(d, c.th, x + off_x(d, k), j, k);
     igr[3 * t] = g.g[0];
     igr[3 * t + 1] = g.g[1];
     igr[3 * t + 2] = g.g[2];

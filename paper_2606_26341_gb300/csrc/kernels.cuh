@@ -197,7 +197,7 @@ __device__ __forceinline__ SlotState init_slot(const Params* P, int slot, int la
       v = kHover;
     } else {
       int r = vi.loc - d.nx - (vi.k < d.N ? d.nu : 0);
-      IneqRow row = ineq_row(d, th, th + d.th_x, r);
+      IneqRow row = ineq_row(d, th, th + d.th_x, r, vi.k);
       v = row.gval;
     }
     if (warm) {

@@ -39,9 +39,9 @@ int fail(int code, const std::string& msg) {
 
 int warm_dims(const bipm_problem_desc* desc, Dims* d) {
   if (!desc) return fail(BIPM_EINVAL, "null problem description");
-  if (desc->n_quads != 1 || desc->n_spheres != 0 || desc->pair_dist > 0.0)
+  if (desc->n_quads != 1 || desc->n_spheres != 0 || desc->pair_dist > 0.0 || desc->n_moving != 0)
     return fail(BIPM_EINVAL, "the warm start is defined for one quadrotor among cylinders "
-                             "(n_quads = 1, n_spheres = 0, pair_dist = 0)");
+                             "(n_quads = 1, n_spheres = 0, n_moving = 0, pair_dist = 0)");
   if (desc->horizon < 1 || desc->horizon > 1000 || desc->n_cylinders < 0 || desc->n_cylinders > 256)
     return fail(BIPM_EINVAL, "horizon must be 1..1000 and n_cylinders 0..256");
   Dims& r = *d;
@@ -52,6 +52,7 @@ int warm_dims(const bipm_problem_desc* desc, Dims* d) {
   r.n_sph = 0;
   r.n_cyl = desc->n_cylinders;
   r.n_pairs = 0;
+  r.n_mov = 0;
   r.ni = r.n_cyl;
   r.n = r.nx * (r.N + 1) + (r.nu + r.ni) * r.N;
   r.m = r.nx * (r.N + 1) + r.ni * r.N;
@@ -61,6 +62,7 @@ int warm_dims(const bipm_problem_desc* desc, Dims* d) {
   r.th_ref = 12;
   r.th_sph = 18;
   r.th_cyl = 18;
+  r.th_mov = 18 + 3 * r.n_cyl;
   r.n_theta = 18 + 3 * r.n_cyl;
   return 0;
 }

@@ -195,3 +195,23 @@ def test_stage_assembled_derivatives_equal_whole_vector_autograd(case):
     assert np.allclose(nlp.jac_c(x), nlp.jac_c_whole(x), rtol=0, atol=1e-12)
     for of in (1.0, 0.0, 2.5):
         assert np.allclose(nlp.hess_lag(x, y, of), nlp.hess_lag_whole(x, y, of), rtol=0, atol=1e-11)
+
+
+def test_moving_sphere_rows_by_hand():
+    """A moving sphere (c + v t, radius r) at stage k enters as |p_k - (c + v k dt)|^2 - r^2
+    - s = 0.  c = (1, 2, 3), v = (0.5, -1, 2), r = 0.5, dt = 0.05: at k = 4 (t = 0.2) the
+    centre is (1.1, 1.8, 3.4); with p_4 = (2, 2, 2): 0.81 + 0.04 + 1.96 - 0.25 = 2.56.
+    The default start puts every slack at g(xbar) of its own stage, so those rows are 0."""
+    desc = ProblemDesc(nq=1, horizon=5, dt=0.05, n_mov=1)
+    th = np.zeros(18 + 7)
+    th[0:3] = [0.2, -0.3, 1.0]
+    th[18:25] = [1.0, 2.0, 3.0, 0.5, 0.5, -1.0, 2.0]
+    nlp = Q.QuadNLP(desc, th)
+    w = nlp.default_start()
+    c = nlp.c(w)
+    ineq_rows = [12 + k * 13 + 12 for k in range(5)]   # after each stage's dynamics rows
+    assert np.allclose(c[ineq_rows], 0.0, atol=1e-14)
+    x4 = np.zeros(12)
+    x4[0:3] = [2.0, 2.0, 2.0]
+    g = nlp.ineq(torch.as_tensor(x4).reshape(1, -1), torch.tensor([4.0])).numpy()[0]
+    assert g[0] == pytest.approx(2.56, rel=1e-14)

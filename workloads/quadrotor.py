@@ -11,6 +11,8 @@ Parameter vector theta of one problem (float64), in this order:
                     radius 0 means a fixed goal at (cx, cy, cz)
     spheres  4*n_sph  (cx, cy, cz, r) of every spherical obstacle
     cyls     3*n_cyl  (cx, cy, r) of every vertical cylinder
+    moving   7*n_mov  (cx, cy, cz, r, vx, vy, vz) of every moving sphere: its centre
+                      at time t is c + v t (the time-varying obstacles of Sec. VI)
 Shared (not per problem): nq, horizon N, dt, n_sph, n_cyl and the pairwise
 minimum distance d (0 disables the pairwise constraints).
 """
@@ -63,6 +65,7 @@ class ProblemDesc:
     n_sph: int = 0
     n_cyl: int = 0
     pair_dist: float = 0.0
+    n_mov: int = 0  # moving spheres (centre c + v t at stage time t = k dt)
 
     @property
     def nx(self) -> int:
@@ -78,7 +81,7 @@ class ProblemDesc:
 
     @property
     def ni(self) -> int:
-        return self.nq * self.n_sph + self.nq * self.n_cyl + self.n_pairs
+        return self.nq * (self.n_sph + self.n_cyl + self.n_mov) + self.n_pairs
 
     @property
     def n(self) -> int:
@@ -95,8 +98,9 @@ def theta_layout(desc: ProblemDesc) -> dict:
     o_ref = o_x + 12 * desc.nq
     o_sph = o_ref + 6 * desc.nq
     o_cyl = o_sph + 4 * desc.n_sph
-    end = o_cyl + 3 * desc.n_cyl
-    return {"xbar": o_x, "ref": o_ref, "sph": o_sph, "cyl": o_cyl, "end": end}
+    o_mov = o_cyl + 3 * desc.n_cyl
+    end = o_mov + 7 * desc.n_mov
+    return {"xbar": o_x, "ref": o_ref, "sph": o_sph, "cyl": o_cyl, "mov": o_mov, "end": end}
 
 
 def n_theta(desc: ProblemDesc) -> int:
@@ -152,6 +156,33 @@ def _track(rng: SplitMix64, desc: ProblemDesc) -> np.ndarray:
             if np.linalg.norm(p0 - c) >= r + 0.1:
                 break
         th[lay["sph"] + 4 * j:lay["sph"] + 4 * j + 4] = [c[0], c[1], c[2], r]
+    return th
+
+
+def _track_moving(rng: SplitMix64, desc: ProblemDesc) -> np.ndarray:
+    """Reference tracking with time-varying obstacles (the scaling-difficulty task of
+    Sec. VI): the tracking workload's circle (speed U[1, 2] m/s, the paper's range of
+    the reference velocity) with spheres that move at constant velocity
+    U[-0.5, 0.5]^3 m/s and pass near the reference: sphere j is at p_ref(t_j) +
+    U[-0.3, 0.3]^3 at t_j ~ U[0, N dt], radius U[0.3, 0.6]; redrawn until it stays
+    0.1 m clear of the start at t = 0."""
+    th = _track(rng, dataclasses.replace(desc, n_sph=0, n_mov=0))
+    th = np.concatenate([th, np.zeros(n_theta(desc) - th.size)])
+    lay = theta_layout(desc)
+    ref = th[lay["ref"]:lay["ref"] + 6]
+    p0 = th[lay["xbar"]:lay["xbar"] + 3]
+    t_end = desc.horizon * desc.dt
+    for j in range(desc.n_mov):
+        while True:
+            r = rng.uniform(0.3, 0.6)
+            tj = rng.uniform(0, t_end)
+            pj, _ = _circle_point(ref, tj)
+            v = np.array([rng.uniform(-0.5, 0.5) for _ in range(3)])
+            cj = pj + np.array([rng.uniform(-0.3, 0.3) for _ in range(3)])
+            c0 = cj - v * tj
+            if np.linalg.norm(p0 - c0) >= r + 0.1:
+                break
+        th[lay["mov"] + 7 * j:lay["mov"] + 7 * j + 7] = [c0[0], c0[1], c0[2], r, v[0], v[1], v[2]]
     return th
 
 
@@ -214,12 +245,38 @@ def _cyl(rng: SplitMix64, desc: ProblemDesc) -> np.ndarray:
     return th
 
 
+def _swap(rng: SplitMix64, desc: ProblemDesc) -> np.ndarray:
+    """The multi-quadrotor swap (consensus) task of the paper's dimension-scaling
+    experiment: nq quadrotors start evenly spaced on a horizontal circle (radius
+    U[1.5, 2.5] m, height U[1, 2] m, rotated by a random angle, each start
+    perturbed by U[-0.1, 0.1]^3) and each must reach the antipodal start, so every
+    path crosses the centre and the pairwise minimum-distance rows are active."""
+    th = np.zeros(n_theta(desc))
+    lay = theta_layout(desc)
+    rad, h, rot = rng.uniform(1.5, 2.5), rng.uniform(1.0, 2.0), rng.uniform(0, 2 * math.pi)
+    pts = []
+    for i in range(desc.nq):
+        a = rot + 2 * math.pi * i / desc.nq
+        pts.append(np.array([rad * math.cos(a), rad * math.sin(a), h]))
+    for i in range(desc.nq):
+        p0 = pts[i] + np.array([rng.uniform(-0.1, 0.1) for _ in range(3)])
+        goal = pts[(i + desc.nq // 2) % desc.nq] if desc.nq % 2 == 0 else -pts[i] + np.array([0, 0, 2 * h])
+        th[lay["xbar"] + 12 * i:lay["xbar"] + 12 * i + 3] = p0
+        th[lay["ref"] + 6 * i:lay["ref"] + 6 * i + 3] = goal
+    return th
+
+
 WORKLOADS = {
     # name: (seed, desc, drawer, default batch)
     "nav1": (1001, ProblemDesc(nq=1, horizon=10, dt=0.05, n_sph=1), _nav1, 64),
     "track": (1002, ProblemDesc(nq=1, horizon=30, dt=0.05, n_sph=3), _track, 4096),
     "multi4": (1003, ProblemDesc(nq=4, horizon=25, dt=0.05, pair_dist=0.4), _multi, 1024),
     "cyl": (1005, ProblemDesc(nq=1, horizon=40, dt=0.05, n_cyl=50), _cyl, 16384),
+    # the paper's swap task (Sec. VI, dimension scaling) with 2 and 4 quadrotors, horizon 30
+    "swap2": (1006, ProblemDesc(nq=2, horizon=30, dt=0.05, pair_dist=0.4), _swap, 1024),
+    "swap4": (1007, ProblemDesc(nq=4, horizon=30, dt=0.05, pair_dist=0.4), _swap, 1024),
+    # reference tracking with three time-varying (moving) spherical obstacles
+    "track_moving": (1008, ProblemDesc(nq=1, horizon=30, dt=0.05, n_mov=3), _track_moving, 4096),
 }
 
 
