@@ -262,10 +262,12 @@ def run_ours(args):
         return ms, rec, clk, [r[0] for r in runs]
 
     ms_mixed, r_mixed, clk, ms_all = timed_queue(best, slots, args.repeats)
+    # the plain FP64 form with the chosen barrier update (the pair isolates the precision form)
+    opt64 = bipm.Options(precision=0, mu_strategy=best.mu_strategy)
     if args.only_mixed:
         ms_fp64, r_fp64, ms_all64 = ms_mixed, r_mixed, ms_all
     else:
-        ms_fp64, r_fp64, _, ms_all64 = timed_queue(bipm.Options(precision=0), B, args.repeats)
+        ms_fp64, r_fp64, _, ms_all64 = timed_queue(opt64, B, args.repeats)
     conv_mixed = int(np.sum(r_mixed["status"] == bipm.CONVERGED))
     conv_fp64 = int(np.sum(r_fp64["status"] == bipm.CONVERGED))
 
@@ -325,6 +327,7 @@ def run_ours(args):
 
     if rank == 0:
         opt_desc = {"precision": best.precision, "fp32_switch": best.fp32_switch,
+                    "mu_strategy": "adaptive" if best.mu_strategy else "monotone",
                     "visit_cap": best.visit_cap or 96, "warps_per_sm": best.warps_per_sm or 24,
                     "team_threads": best.team_threads or 256, "slots": slots}
         line = {
@@ -360,8 +363,9 @@ def run_ours(args):
         if mixed is not None:
             line["uneven_queue"] = mixed
         if ws == 1 and not args.no_cpu_baseline:
-            forms = {"chosen": best, "fp64": bipm.Options(precision=0)}
-            line["cpu_baseline"] = cpu_baseline(desc, theta, forms, stream, budget_s=args.cpu_budget)
+            forms = {"chosen": best, "fp64": opt64}
+            line["cpu_baseline"] = cpu_baseline(desc, theta, forms, stream, budget_s=args.cpu_budget,
+                                                mu_strategy=best.mu_strategy)
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -597,7 +601,8 @@ def desc_theta_len(desc):
 
 # ------------------------------------------------------------ CPU oracle
 def _oracle_one(args):
-    desc, theta = args
+    desc, theta = args[0], args[1]
+    mu_strategy = args[2] if len(args) > 2 else 0
     sys.path.insert(0, ROOT)
     import torch
 
@@ -605,7 +610,8 @@ def _oracle_one(args):
     from oracle import ipm
     from oracle.quadrotor import QuadNLP
     t0 = time.perf_counter()
-    st, _ = ipm.solve(QuadNLP(desc, theta))
+    opt = ipm.Options(mu_strategy="adaptive" if mu_strategy else "monotone")
+    st, _ = ipm.solve(QuadNLP(desc, theta), opt=opt)
     return {"ok": st.status == ipm.CONVERGED, "s": time.perf_counter() - t0, "status": int(st.status),
             "iters": int(st.iter), "x": st.normal.x}
 
@@ -615,12 +621,12 @@ def single_thread_env():
         os.environ[var] = "1"  # one thread per worker process: cores = processes
 
 
-def oracle_rate(desc, theta, n_problems, processes):
+def oracle_rate(desc, theta, n_problems, processes, mu_strategy=0):
     """Converged count, wall time and per-problem records of the oracle on the
     first n_problems rows, one problem per process."""
     single_thread_env()
     ctx = mp.get_context("spawn")
-    jobs = [(desc, theta[j]) for j in range(n_problems)]
+    jobs = [(desc, theta[j], mu_strategy) for j in range(n_problems)]
     with ctx.Pool(processes=processes) as pool:
         pool.map(_oracle_one, jobs[:processes])  # warm the workers (imports)
         t0 = time.perf_counter()
@@ -671,18 +677,20 @@ def gpu_error_vs_oracle(desc, theta, oracle_res, options, stream, processes):
             "same_iters": int(sum(st["iters"][j] == o["iters"] for j, o in enumerate(oracle_res)))}
 
 
-def cpu_baseline(desc, theta, forms, stream, budget_s=20.0):
-    """The oracle as it stands on the host cores: all cores (one problem per
-    process, two problems per core) and one core (two problems); then each GPU
-    form's error against the oracle's solutions of the same problems."""
+def cpu_baseline(desc, theta, forms, stream, budget_s=20.0, mu_strategy=0):
+    """The oracle as it stands on the host cores, with the chosen form's barrier
+    update: all cores (one problem per process, two problems per core) and one core
+    (two problems); then each GPU form's error against the oracle's solutions of
+    the same problems."""
     cores = os.cpu_count() or 1
     n_prob = 2 * cores
-    conv, wall, res = oracle_rate(desc, theta, n_prob, cores)
-    conv1, wall1, _ = oracle_rate(desc, theta, 2, 1)
+    conv, wall, res = oracle_rate(desc, theta, n_prob, cores, mu_strategy)
+    conv1, wall1, _ = oracle_rate(desc, theta, 2, 1, mu_strategy)
     errors = {name: gpu_error_vs_oracle(desc, theta, res, opt, stream, cores) for name, opt in forms.items()}
     return {"value": conv / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_prob} problems of the {WORKLOAD} workload (the first of the timed set), one per "
-                      f"process on {cores} cores, {wall:.1f} s wall",
+                      f"process on {cores} cores, {wall:.1f} s wall, "
+                      f"{'adaptive' if mu_strategy else 'monotone'} barrier update",
             "single_core": {"value": conv1 / wall1, "unit": UNIT, "cores": 1,
                             "sample": f"2 problems, {wall1:.1f} s"},
             "oracle_iters_mean": float(np.mean([r["iters"] for r in res])),

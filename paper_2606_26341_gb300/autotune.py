@@ -1,13 +1,16 @@
 """Measured selection of the solver's execution options for one workload.
 
 The library exposes the choices that decide throughput on a given problem
-family, none of which changes a result beyond the order of floating-point
-sums:
+family.  The precision form and the barrier update change the iteration path
+but not the accuracy a converged problem is held to (E_0 <= tol in FP64); the
+schedule changes no result beyond the order of floating-point sums:
 
 * the precision form: FP32 derivative blocks with an FP64 factorisation
   (``precision=1, fp32_switch<0``), FP32 factorisation with FP64 refinement
   (``precision=1``, FP64 above the barrier scale ``fp32_switch``), or the
-  double-float factorisation (``precision=2``);
+  double-float factorisation (``precision=2``), each with the monotone or the
+  adaptive barrier update (``mu_strategy``; this changes the iteration path,
+  not the accuracy a converged problem is held to);
 * the schedule of the persistent queue (iteration-level batching, Sec. V):
   the visit cap after which a straggler is parked for the block teams, the
   resident warps per SM, the block-team size, and the number of slots (every
@@ -36,6 +39,10 @@ DEFAULT_CANDIDATES = (
     bipm.Options(precision=2),
     bipm.Options(precision=1, fp32_switch=-1.0),
     bipm.Options(precision=1, fp32_switch=1e2),
+    # the adaptive barrier update (Table I row 7) changes the path, not the accuracy
+    # (converged = E_0 <= tol either way)
+    bipm.Options(precision=1, fp32_switch=-1.0, mu_strategy=1),
+    bipm.Options(precision=0, mu_strategy=1),
 )
 
 # schedule knobs and the values tried for each (the first is the library default)
@@ -74,6 +81,7 @@ def measure(desc, theta_dev, options, capacity, stream=None):
 
 def _row(options, slots, rate, stage):
     return {"stage": stage, "precision": options.precision, "fp32_switch": options.fp32_switch,
+            "mu_strategy": "adaptive" if options.mu_strategy else "monotone",
             "visit_cap": options.visit_cap or 96, "warps_per_sm": options.warps_per_sm or 24,
             "team_threads": options.team_threads or 256, "slots": slots, "solves_per_s": rate}
 

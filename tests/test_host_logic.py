@@ -33,10 +33,10 @@ def test_result_records_round_trip_through_bytes():
 
 def test_autotuner_picks_the_fastest_candidate(monkeypatch):
     """Precision forms first, then one schedule knob at a time from the best so far."""
-    rates = {(2, 0.0): 10.0, (1, -1.0): 30.0, (1, 100.0): 20.0}
+    rates = {(2, 0.0, 0): 10.0, (1, -1.0, 0): 30.0, (1, 100.0, 0): 20.0, (1, -1.0, 1): 25.0, (0, 0.0, 1): 5.0}
 
     def fake(desc, th, o, cap, stream=None):
-        r = rates[(o.precision, o.fp32_switch)]
+        r = rates[(o.precision, o.fp32_switch, o.mu_strategy)]
         # a faster schedule: visit cap 160 and 128-thread teams, 1.25x the slots
         r += 2.0 * (o.visit_cap == 160) + 1.0 * (o.team_threads == 128) + 0.5 * (cap == 125)
         r -= 3.0 * (o.warps_per_sm in (16, 20))
@@ -47,14 +47,14 @@ def test_autotuner_picks_the_fastest_candidate(monkeypatch):
     o = best.options
     assert (o.precision, o.fp32_switch) == (1, -1.0)
     assert (o.visit_cap, o.team_threads, o.warps_per_sm or 24, best.slots) == (160, 128, 24, 125)
-    assert [row["solves_per_s"] for row in table[:3]] == [10.0, 30.0, 20.0]
-    # 3 forms + 2 visit caps + 2 warp counts + 1 team size + 1 slot count
-    assert len(table) == 9
+    assert [row["solves_per_s"] for row in table[:5]] == [10.0, 30.0, 20.0, 25.0, 5.0]
+    # 5 forms + 2 visit caps + 2 warp counts + 1 team size + 1 slot count
+    assert len(table) == 11
     assert {row["stage"] for row in table} == {"precision", "visit_cap", "warps_per_sm", "team_threads",
                                                 "slot_factor"}
     # without the schedule search only the forms are measured
     best, table = autotune.autotune(None, None, 100, schedule=False)
-    assert len(table) == 3 and best.slots == 100
+    assert len(table) == 5 and best.slots == 100
 
 
 def test_warm_start_network_shape_follows_the_family():
