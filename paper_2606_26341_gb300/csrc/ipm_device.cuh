@@ -22,7 +22,11 @@
 
 namespace bipm {
 
-#define LANE_LOOP(i, n) for (int i = lane; i < (n); i += c.T)
+// Loops that stride over a team's lanes are never unrolled ("unroll 1" here
+// and on every such loop below): many warps of one SM run different parts of
+// this code at once, and the smaller instruction footprint measured faster
+// than the unrolled copies.
+#define LANE_LOOP(i, n) _Pragma("unroll 1") for (int i = lane; i < (n); i += c.T)
 
 template <class T>
 struct Fac {  // factor arrays of one slot in precision T
@@ -44,13 +48,24 @@ __device__ __forceinline__ Fac<T> make_fac(T* base, const Layout& L) {
 
 enum FactorFlags : int { FF_IDENT = 1, FF_RESTO = 2 };
 
-template <class TB, class TF, int NQ>
-struct Ctx {
+// Team size of a kernel: TM = 32 fixes a one-warp team at compile time (the
+// block-team branches of the team primitives fold away); TM = 0 keeps it a
+// run-time field (block teams, T = blockDim.x).
+template <int TM>
+struct TeamSize {
+  static constexpr int T = TM;
+};
+template <>
+struct TeamSize<0> {
+  int T;
+};
+
+template <class TB, class TF, int NQ, int TM>
+struct Ctx : TeamSize<TM> {
   const Params* P;
   DimsT<NQ> d;         // problem sizes (nq, nx, nu compile-time when NQ > 0)
   Layout L;
   int lane;            // thread index within the team
-  int T;               // team size: 32 (warp) or the block size
   double* red;         // shared reduction buffer (block teams)
   int slot;
   double* f;           // this slot's FP64 arrays
@@ -76,6 +91,53 @@ struct Ctx {
 
 __device__ __forceinline__ double sq(double a) { return a * a; }
 
+// 1 / sqrt(x) for x > 0 in FP64 without the FP64 square root and division:
+// an FP32 estimate y refined by one step of the second-order Newton iteration
+// for the reciprocal square root (Householder's method of order 2).  With
+// e = 1 - x y^2, 1 / sqrt(x) = y (1 - e)^(-1/2) = y (1 + e/2 + 3 e^2/8 + O(e^3)).
+// The FP32 estimate is within a few FP32 ulp (|e| < 2^-20), so the truncated
+// series is exact to about 2^-60 and the result lies within about one FP64
+// ulp of 1 / sqrt(x).  Outside the normal FP32 range the plain expression.
+__device__ __forceinline__ double rsqrt_fp64(double x) {
+  if (!(x >= 1e-36 && x <= 1e36)) return 1.0 / sqrt(x);
+  const double y = (double)rsqrtf((float)x);
+  const double e = fma(-(x * y), y, 1.0);
+  return fma(y * e, fma(e, 0.375, 0.5), y);
+}
+
+// (i, j), j <= i, of entry e of a row-major lower triangle (e = i (i + 1) / 2 + j)
+__device__ __forceinline__ void tri_index(int e, int& i, int& j) {
+  int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (r * (r + 1) / 2 > e) --r;
+  while ((r + 1) * (r + 2) / 2 <= e) ++r;
+  i = r;
+  j = e - r * (r + 1) / 2;
+}
+
+// Lower-triangle entries (i, j), j <= i, of the rows 12 q + r0 .. 12 q + r0 + 5
+// of every quadrotor block q of an nx x nx matrix: their count, and entry f in
+// row-major order
+template <class D>
+__device__ __forceinline__ int tri_rows_count(const D& d, int r0) {
+  int n = 0;
+  for (int q = 0; q < d.nq; ++q) {
+    const int a = 12 * q + r0;
+    n += (a + 6) * (a + 7) / 2 - a * (a + 1) / 2;
+  }
+  return n;
+}
+template <class D>
+__device__ __forceinline__ void tri_rows_entry(const D& d, int f, int r0, int& i, int& j) {
+  int q = 0;
+  for (; q + 1 < d.nq; ++q) {
+    const int a = 12 * q + r0, cnt = (a + 6) * (a + 7) / 2 - a * (a + 1) / 2;
+    if (f < cnt) break;
+    f -= cnt;
+  }
+  const int a = 12 * q + r0;
+  tri_index(a * (a + 1) / 2 + f, i, j);
+}
+
 // 12-term dot product a[r*sa] * b[r*sb] with three independent partial sums
 // (shorter dependency chains for the latency-bound stage products)
 template <class TX>
@@ -96,7 +158,7 @@ __device__ __forceinline__ TX dot12(const TX* a, int sa, const TX* b, int sb) {
   {                                                  \
     const int C_ = (C), RC_ = (R) * (C);             \
     int i = lane / C_, j = lane - (lane / C_) * C_;  \
-    for (int e = lane; e < RC_; e += c.T) {
+    _Pragma("unroll 1") for (int e = lane; e < RC_; e += c.T) {
 #define MAT_LOOP_END(i, j)     \
   j += c.T;                    \
   while (j >= C_) {            \
@@ -384,12 +446,13 @@ __device__ __forceinline__ double hess_pos(const IneqGrad& r, int qa, int ca, in
 
 // ---------------------------------------------------------------- evaluation
 // Constraint values c(x) (original problem) into cout and the objective f(x).
-template <class TB, class TF, int NQ>
-__device__ __noinline__ double eval_values(Ctx<TB, TF, NQ>& c, const double* x, double* cout,
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ double eval_values(Ctx<TB, TF, NQ, TM>& c, const double* x, double* cout,
                               bool dynamics = true) {
   const auto& d = c.d;
   const int lane = c.lane;
   LANE_LOOP(i, d.nx) cout[i] = x[i] - c.th[d.th_x + i];
+  #pragma unroll 1
   for (int t = lane; t < (dynamics ? d.N * d.nq : 0); t += c.T) {
     int k = t / d.nq, q = t - (t / d.nq) * d.nq;
     double xx[12], uu[4], F[12];
@@ -405,12 +468,14 @@ __device__ __noinline__ double eval_values(Ctx<TB, TF, NQ>& c, const double* x, 
 #pragma unroll
     for (int i = 0; i < 12; ++i) cr[i] = xn[i] - F[i];
   }
+  #pragma unroll 1
   for (int t = lane; t < d.N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, j = t - (t / d.ni) * d.ni;
     IneqRow r = ineq_row(d, c.th, x + off_x(d, k), j, k);
     cout[row_ineq(d, k) + j] = r.gval - x[off_s(d, k) + j];
   }
   double fs = 0.0;
+  #pragma unroll 1
   for (int t = lane; t < (d.N + 1) * d.nx; t += c.T) {
     int k = t / d.nx, i = t - (t / d.nx) * d.nx;
     int q = i / 12, j = i - 12 * (i / 12);
@@ -418,6 +483,7 @@ __device__ __noinline__ double eval_values(Ctx<TB, TF, NQ>& c, const double* x, 
     (void)q;
     fs += cost_weight(d, k, j) * e * e;
   }
+  #pragma unroll 1
   for (int t = lane; t < d.N * d.nu; t += c.T) {
     int k = t / d.nu, i = t - (t / d.nu) * d.nu;
     double e = x[off_u(d, k) + i] - kHover;
@@ -428,8 +494,8 @@ __device__ __noinline__ double eval_values(Ctx<TB, TF, NQ>& c, const double* x, 
 }
 
 // Gradient of the objective of the current phase into g (W-sized).
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void eval_grad(Ctx<TB, TF, NQ>& c, const double* x, double* g) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void eval_grad(Ctx<TB, TF, NQ, TM>& c, const double* x, double* g) {
   const auto& d = c.d;
   const int lane = c.lane;
   const double* xr = c.f + c.L.xr;
@@ -458,8 +524,8 @@ __device__ __noinline__ void eval_grad(Ctx<TB, TF, NQ>& c, const double* x, doub
 }
 
 // Objective of the restoration problem: rho sum(p + n) + zeta/2 |D_R (x - x_R)|^2.
-template <class TB, class TF, int NQ>
-__device__ __noinline__ double resto_objective(Ctx<TB, TF, NQ>& c, const double* w) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ double resto_objective(Ctx<TB, TF, NQ, TM>& c, const double* w) {
   const auto& d = c.d;
   const int lane = c.lane;
   const double* xr = c.f + c.L.xr;
@@ -480,12 +546,13 @@ __device__ __noinline__ double resto_objective(Ctx<TB, TF, NQ>& c, const double*
 // at stage k.  The columns of A for p and v are constant (F is affine in p, v)
 // and the Hessian of lam^T F vanishes in those rows, so only ten directions
 // carry derivatives.  lam = -y_dyn (the Lagrangian term is +y^T (x_{k+1} - F)).
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void eval_blocks(Ctx<TB, TF, NQ>& c, const double* x, const double* y, bool hess) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void eval_blocks(Ctx<TB, TF, NQ, TM>& c, const double* x, const double* y, bool hess) {
   const auto& d = c.d;
   const int lane = c.lane;
   typedef Dual<TB> DT;
   const int ntask = d.N * d.nq * 10;
+  #pragma unroll 1
   for (int t = lane; t < ntask; t += c.T) {
     int j = t - (t / 10) * 10;
     int kq = t / 10;
@@ -535,11 +602,12 @@ __device__ __noinline__ void eval_blocks(Ctx<TB, TF, NQ>& c, const double* x, co
 
 // J^T y of the original constraints (x-part, n entries) in FP64, plus the
 // elastic parts (-y, +y) in restoration.
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void eval_jty(Ctx<TB, TF, NQ>& c, const double* x, const double* y, double* jty,
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void eval_jty(Ctx<TB, TF, NQ, TM>& c, const double* x, const double* y, double* jty,
                          double* cout = nullptr) {
   const auto& d = c.d;
   const int lane = c.lane;
+  #pragma unroll 1
   for (int t = lane; t < d.N * d.nq; t += c.T) {
     int k = t / d.nq, q = t - (t / d.nq) * d.nq;
     double xx[12], uu[4], F[12], gx[12], gu[4], lam[12];
@@ -570,6 +638,7 @@ __device__ __noinline__ void eval_jty(Ctx<TB, TF, NQ>& c, const double* x, const
   LANE_LOOP(i, d.nx) jty[off_x(d, d.N) + i] = y[row_dyn(d, d.N - 1) + i];
   team_sync(c);
   // inequality rows: + G_k^T y_ineq on the positions, - y_ineq on the slacks
+  #pragma unroll 1
   for (int t = lane; t < d.N * 3 * d.nq; t += c.T) {
     int k = 1 + t / (3 * d.nq);
     int pc = t - (t / (3 * d.nq)) * (3 * d.nq);
@@ -581,6 +650,7 @@ __device__ __noinline__ void eval_jty(Ctx<TB, TF, NQ>& c, const double* x, const
     for (int r = 0; r < d.ni; ++r) acc += grad_pos(ineq_grad(d, c.th, xk, r, k), q, comp) * yi[r];
     jty[off_x(d, k) + i] += acc;
   }
+  #pragma unroll 1
   for (int t = lane; t < d.N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
     jty[off_s(d, k) + r] = -y[row_ineq(d, k) + r];
@@ -597,20 +667,22 @@ __device__ __noinline__ void eval_jty(Ctx<TB, TF, NQ>& c, const double* x, const
 // ------------------------------------------------- barrier quantities (FP64)
 // Sigma_i = z_L/s_L + z_U/s_U of W-entry i, from the array fill_sigma wrote
 // for the current iterate.
-template <class TB, class TF, int NQ>
-__device__ __forceinline__ double sigma_of(Ctx<TB, TF, NQ>& c, int i) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __forceinline__ double sigma_of(Ctx<TB, TF, NQ, TM>& c, int i) {
   return c.f[c.L.sig + i];
 }
 
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void fill_sigma(Ctx<TB, TF, NQ>& c) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void fill_sigma(Ctx<TB, TF, NQ, TM>& c) {
   const double* x = c.f + c.L.x;
   const double* zl = c.f + c.L.zl;
   const double* zu = c.f + c.L.zu;
   double* sg = c.f + c.L.sig;
+  #pragma unroll 1
   for (int i = c.lane; i < c.nw; i += c.T) sg[i] = 0.0;
   team_sync(c);
   const int nb = n_bounded(c.d, c.nw);
+  #pragma unroll 1
   for (int b = c.lane; b < nb; b += c.T) {
     int kind;
     const int i = bnd_index(c.d, b, kind);
@@ -623,8 +695,8 @@ __device__ __noinline__ void fill_sigma(Ctx<TB, TF, NQ>& c) {
 
 // Diagonal Hessian of the objective on W-entry i (cost weights, or zeta D_R^2
 // in restoration, or 1 for the least-squares multiplier system).
-template <class TB, class TF, int NQ>
-__device__ __forceinline__ double obj_hdiag(Ctx<TB, TF, NQ>& c, int i, int flags) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __forceinline__ double obj_hdiag(Ctx<TB, TF, NQ, TM>& c, int i, int flags) {
   if (flags & FF_IDENT) return 1.0;
   const auto& d = c.d;
   if (i >= d.n) return 0.0;
@@ -641,10 +713,11 @@ __device__ __forceinline__ double obj_hdiag(Ctx<TB, TF, NQ>& c, int i, int flags
 
 // Position gradients of every inequality row at the point x (the iterate),
 // one pass over all rows; factorisation, solves and the KKT mat-vec read them.
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void fill_ineq_grad(Ctx<TB, TF, NQ>& c, const double* x) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void fill_ineq_grad(Ctx<TB, TF, NQ, TM>& c, const double* x) {
   const auto& d = c.d;
   double* igr = c.f + c.L.igr;
+  #pragma unroll 1
   for (int t = c.lane; t < d.N * d.ni; t += c.T) {
     const int k = 1 + t / d.ni, j = t - (k - 1) * d.ni;
     const IneqGrad g = ineq_grad(d, c.th, x + off_x(d, k), j, k);
@@ -658,8 +731,8 @@ __device__ __noinline__ void fill_ineq_grad(Ctx<TB, TF, NQ>& c, const double* x)
 // Condensation diagonals for regularisation dw:
 //   slack (k, r):  D_s = H_ss + Sigma_s + dw,  E = D_s / (1 + D_s D_g)
 //   row i (restoration): 1/(Sigma_p + dw), 1/(Sigma_n + dw), D = their sum
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void compute_diag(Ctx<TB, TF, NQ>& c, double dw, int flags) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void compute_diag(Ctx<TB, TF, NQ, TM>& c, double dw, int flags) {
   const auto& d = c.d;
   const int lane = c.lane;
   double* dsv = c.f + c.L.dsv;
@@ -685,6 +758,7 @@ __device__ __noinline__ void compute_diag(Ctx<TB, TF, NQ>& c, double dw, int fla
     }
   }
   team_sync(c);
+  #pragma unroll 1
   for (int t = lane; t < d.N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
     int vi = off_s(d, k) + r;
@@ -711,8 +785,8 @@ __device__ __noinline__ void compute_diag(Ctx<TB, TF, NQ>& c, double dw, int fla
 //   qpos_k(a, b) = sum_r E_r g_r(a) g_r(b) + y_r H_r(a, b),
 // a, b over the 3 nq position components of stage k (no Hessian term in the
 // least-squares multiplier system).
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void ineq_blocks(Ctx<TB, TF, NQ>& c, int flags) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void ineq_blocks(Ctx<TB, TF, NQ, TM>& c, int flags) {
   const auto& d = c.d;
   const int lane = c.lane;
   const double* ev = c.f + c.L.ev;
@@ -720,6 +794,7 @@ __device__ __noinline__ void ineq_blocks(Ctx<TB, TF, NQ>& c, int flags) {
   const double* igr = c.f + c.L.igr;
   const double* y = c.f + c.L.y;
   double* qpos = c.f + c.L.qpos;
+  #pragma unroll 1
   for (int e = lane; e < d.N * npp; e += c.T) {
     const int k = 1 + e / npp, ab = e - (k - 1) * npp;
     const int a = ab / np, b = ab - a * np;
@@ -780,70 +855,77 @@ __host__ __device__ inline size_t scratch_bytes(int nq, int nx, int nu, int elem
 
 // shared memory when the scratch of precision TX fits, else the slot's
 // global scratch region
-template <class TX, class TB, class TF, int NQ>
-__device__ __forceinline__ char* scratch_base(const Ctx<TB, TF, NQ>& c) {
+template <class TX, class TB, class TF, int NQ, int TM>
+__device__ __forceinline__ char* scratch_base(const Ctx<TB, TF, NQ, TM>& c) {
   return scratch_bytes(c.d.nq, c.d.nx, c.d.nu, (int)sizeof(TX)) <= (size_t)c.smem_bytes ? c.smem
                                                                                         : c.gscratch;
 }
 
-// Q~_k (state block, written to Pb as TX), including the inequality terms.
-template <class TB, class TF, int NQ, class TX>
-__device__ __noinline__ void add_state_block(Ctx<TB, TF, NQ>& c, int k, TX* Q, double dw, int flags,
-                                const double* y, bool accumulate, const TX* xdg = nullptr) {
+// v + entry (i, j) of Q~_k, the state block of the stage Hessian including the
+// inequality terms (xdg: its diagonal, precomputed in TX, or null); the terms
+// are added to v one at a time.
+template <class TB, class TF, int NQ, int TM, class TX>
+__device__ __forceinline__ TX state_term(Ctx<TB, TF, NQ, TM>& c, int k, int i, int j, double dw, int flags,
+                                         const TX* xdg, TX v) {
   const auto& d = c.d;
-  const int lane = c.lane;
-  const int nx = d.nx;
-  const double* qpos = c.f + c.L.qpos;
   const bool ident = flags & FF_IDENT;
-  (void)y;
+  if (i == j) {
+    if (xdg)
+      v += xdg[k * d.nx + i];
+    else
+      v += (TX)(obj_hdiag(c, off_x(d, k) + i, flags) + (ident ? 0.0 : dw));
+  }
+  const int qi = i / 12, qj = j / 12;
+  const int ci = i - 12 * qi, cj = j - 12 * qj;
+  if (!ident && k < d.N && qi == qj && ci >= 6 && cj >= 6) {
+    const TB* H = c.blk + c.L.H + ((long long)k * d.nq + qi) * 100;
+    v += (TX)H[(cj - 6) * 10 + (ci - 6)];
+  }
+  if (k >= 1 && ci < 3 && cj < 3 && d.ni > 0) {
+    const int np = 3 * d.nq;
+    v += (TX)c.f[c.L.qpos + (long long)(k - 1) * np * np + (3 * qi + ci) * np + 3 * qj + cj];
+  }
+  return v;
+}
+
+// Q~_k written to the full nx x nx block Q.
+template <class TB, class TF, int NQ, int TM, class TX>
+__device__ __noinline__ void add_state_block(Ctx<TB, TF, NQ, TM>& c, int k, TX* Q, double dw, int flags,
+                                             const TX* xdg = nullptr) {
+  const int lane = c.lane;
+  const int nx = c.d.nx;
   MAT_LOOP_BEGIN(i, j, nx, nx)
-    TX v = accumulate ? Q[e] : (TX)0;
-    if (i == j) {
-      if (xdg)
-        v += xdg[k * nx + i];
-      else
-        v += (TX)(obj_hdiag(c, off_x(d, k) + i, flags) + (ident ? 0.0 : dw));
-    }
-    int qi = i / 12, qj = j / 12;
-    int ci = i - 12 * qi, cj = j - 12 * qj;
-    if (!ident && k < d.N && qi == qj && ci >= 6 && cj >= 6) {
-      const TB* H = c.blk + c.L.H + ((long long)k * d.nq + qi) * 100;
-      v += (TX)H[(cj - 6) * 10 + (ci - 6)];
-    }
-    if (k >= 1 && ci < 3 && cj < 3 && d.ni > 0) {
-      const int np = 3 * d.nq;
-      v += (TX)qpos[(long long)(k - 1) * np * np + (3 * qi + ci) * np + 3 * qj + cj];
-    }
-    Q[e] = v;
+    Q[e] = state_term<TB, TF, NQ, TM, TX>(c, k, i, j, dw, flags, xdg, (TX)0);
   MAT_LOOP_END(i, j)
 }
 
-// Cholesky of the nxn symmetric matrix in `a` (row-major, double) in place;
-// lower triangle holds L.  Returns min pivot ratio L_jj^2 / a_jj, or -1 if a
-// pivot is not positive.
+// Cholesky of the n x n symmetric matrix in `a` (row-major, double) in place
+// by the team: the lower triangle holds L below the diagonal and 1 / L_jj on
+// it.  Returns false if a pivot is not positive and finite (every thread reads
+// the same pivot, so the return is uniform).
 template <class C>
-__device__ inline double warp_cholesky(const C& c, double* a, int n) {
+__device__ inline bool warp_cholesky_rdiag(const C& c, double* a, int n) {
   const int lane = c.lane;
-  double ratio = 1.0;
   for (int j = 0; j < n; ++j) {
     team_sync(c);
-    double diag0 = a[j * n + j];
     // a_jj already holds the Schur complement pivot
-    double piv = diag0;
-    if (!(piv > 0.0) || !isfinite(piv)) return -1.0;
-    double l = sqrt(piv);
+    const double piv = a[j * n + j];
+    if (!(piv > 0.0) || !isfinite(piv)) return false;
+    const double il = rsqrt_fp64(piv);
     team_sync(c);
-    if (lane == 0) a[j * n + j] = l;
-    for (int i = j + 1 + lane; i < n; i += c.T) a[i * n + j] /= l;
+    if (lane == 0) a[j * n + j] = il;
+    #pragma unroll 1
+    for (int i = j + 1 + lane; i < n; i += c.T) a[i * n + j] *= il;
     team_sync(c);
-    int rem = n - j - 1;
+    const int rem = n - j - 1;
+    #pragma unroll 1
     for (int e = lane; e < rem * rem; e += c.T) {
-      int i = j + 1 + e / rem, t = j + 1 + (e - (e / rem) * rem);
+      const int i = j + 1 + e / rem, t = j + 1 + (e - (e / rem) * rem);
       if (t <= i) a[i * n + t] -= a[i * n + j] * a[t * n + j];
     }
   }
   team_sync(c);
-  return ratio;
+  return true;
 }
 
 // Cholesky of the nxn matrix in `a` (row-major, precision TX) in place by
@@ -860,9 +942,11 @@ __device__ inline bool team_cholesky(const C& c, TX* a, int n) {
     const TX il = (TX)1 / l;
     team_sync(c);
     if (lane == 0) a[j * n + j] = l;
+    #pragma unroll 1
     for (int i = j + 1 + lane; i < n; i += c.T) a[i * n + j] *= il;
     team_sync(c);
     const int rem = n - j - 1;
+    #pragma unroll 1
     for (int e = lane; e < rem * rem; e += c.T) {
       const int i = j + 1 + e / rem, t = j + 1 + (e - (e / rem) * rem);
       if (t <= i) a[i * n + t] -= a[i * n + j] * a[t * n + j];
@@ -882,6 +966,7 @@ __device__ inline int stage_pivot_check(const C& c, const TX* R, double* a64, in
   int bad = 0;
   double rmin = 1.0;
   const int nn = nu * nu;
+  #pragma unroll 1
   for (int k = k0 + c.lane; k < N; k += c.T) {
     double* a = a64 + (long long)k * nn;
     const TX* r = R + (long long)k * nn;
@@ -910,8 +995,8 @@ __device__ inline int stage_pivot_check(const C& c, const TX* R, double* a64, in
 }
 
 // Restoration: P~ = P - Y^T Y with Y = L_M^{-1} D^1/2 P, M = I + D^1/2 P D^1/2 = L_M L_M^T.
-template <class TB, class TF, int NQ, class TX>
-__device__ __noinline__ bool resto_transform(Ctx<TB, TF, NQ>& c, TX* Pb, const double* D, TX* LM, TX* Y) {
+template <class TB, class TF, int NQ, int TM, class TX>
+__device__ __noinline__ bool resto_transform(Ctx<TB, TF, NQ, TM>& c, TX* Pb, const double* D, TX* LM, TX* Y) {
   const auto& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx;
@@ -929,9 +1014,11 @@ __device__ __noinline__ bool resto_transform(Ctx<TB, TF, NQ>& c, TX* Pb, const d
     double l = sqrt(piv);
     team_sync(c);
     if (lane == 0) LM[j * nx + j] = (TX)l;
+    #pragma unroll 1
     for (int i = j + 1 + lane; i < nx; i += c.T) LM[i * nx + j] = (TX)((double)LM[i * nx + j] / l);
     team_sync(c);
     int rem = nx - j - 1;
+    #pragma unroll 1
     for (int e = lane; e < rem * rem; e += c.T) {
       int i = j + 1 + e / rem, t = j + 1 + (e - (e / rem) * rem);
       if (t <= i) LM[i * nx + t] = (TX)((double)LM[i * nx + t] - (double)LM[i * nx + j] * (double)LM[t * nx + j]);
@@ -939,6 +1026,7 @@ __device__ __noinline__ bool resto_transform(Ctx<TB, TF, NQ>& c, TX* Pb, const d
   }
   team_sync(c);
   // Y = L^{-1} (D^1/2 P): forward substitution, one column per lane
+  #pragma unroll 1
   for (int col = lane; col < nx; col += c.T) {
     for (int i = 0; i < nx; ++i) {
       double acc = sqrt(D[i]) * (double)Pb[i * nx + col];
@@ -957,8 +1045,8 @@ __device__ __noinline__ bool resto_transform(Ctx<TB, TF, NQ>& c, TX* Pb, const d
   return true;
 }
 
-template <class TB, class TF, int NQ, class TX>
-__device__ __noinline__ int factor(Ctx<TB, TF, NQ>& c, Fac<TX> F, double dw, int flags, const double* y) {
+template <class TB, class TF, int NQ, int TM, class TX>
+__device__ __noinline__ int factor(Ctx<TB, TF, NQ, TM>& c, Fac<TX> F, double dw, int flags, const double* y) {
   const auto& d = c.d;
   const int lane = c.lane;
   const int nx = d.nx, nu = d.nu, nq = d.nq, N = d.N;
@@ -1003,10 +1091,10 @@ __device__ __noinline__ int factor(Ctx<TB, TF, NQ>& c, Fac<TX> F, double dw, int
   }
 
   // terminal block P_N = Q~_N
-  add_state_block<TB, TF, NQ, TX>(c, N, s.Pb, dw, flags, y, false, xdg);
+  add_state_block<TB, TF, NQ, TM, TX>(c, N, s.Pb, dw, flags, xdg);
   team_sync(c);
   if (resto) {
-    if (!resto_transform<TB, TF, NQ, TX>(c, s.Pb, dv + row_dyn(d, N - 1), F.LM + (long long)N * nx * nx,
+    if (!resto_transform<TB, TF, NQ, TM, TX>(c, s.Pb, dv + row_dyn(d, N - 1), F.LM + (long long)N * nx * nx,
                                      F.Yr + (long long)N * nx * nx))
       return 0;
   }
@@ -1024,72 +1112,111 @@ __device__ __noinline__ int factor(Ctx<TB, TF, NQ>& c, Fac<TX> F, double dw, int
     // first six columns of each A block are constant (p and v enter F
     // affinely): column c < 3 is e_c, column c in 3..5 is e_c + dt e_(c-3),
     // with dt read from the stored block.  They cost a copy or one FMA; the
-    // twelve-term products run over the other six columns only, in passes of
-    // their own.
+    // twelve-term products of the other six columns and those of PB share one
+    // pass (an FP64 instruction costs the same whatever the active lanes).
     const int n6 = 6 * nq;
-    for (int e = lane; e < nx * n6; e += c.T) {
+    const int nPA = nx * n6, nPB = nx * nu;
+    #pragma unroll 1
+    for (int e = lane; e < nPA; e += c.T) {
       const int i = e / n6, r6 = e - i * n6, q = r6 / 6, cc = r6 - 6 * q;
       const TX* prow = s.Pb + i * nx + 12 * q;
       s.PA[i * nx + 12 * q + cc] = cc < 3 ? prow[cc] : prow[cc - 3] * s.Ab[q * 144 + cc * 12 + cc - 3] + prow[cc];
     }
-    for (int e = lane; e < nx * n6; e += c.T) {
-      const int i = e / n6, r6 = e - i * n6, q = r6 / 6, cc = 6 + r6 - 6 * q;
-      s.PA[i * nx + 12 * q + cc] = dot12(s.Pb + i * nx + 12 * q, 1, s.Ab + q * 144 + cc * 12, 1);
-    }
-    MAT_LOOP_BEGIN(i, col, nx, nu)
-      int q = col >> 2, cc = col & 3;
-      s.PB[e] = dot12(s.Pb + i * nx + 12 * q, 1, s.Bb + q * 48 + cc * 12, 1);
-    MAT_LOOP_END(i, col)
-    team_sync(c);
-    // R^ = R~ + B^T P~ B ; S^ = S + B^T P~ A
-    MAT_LOOP_BEGIN(a, b, nu, nu)
-      int qa = a >> 2, ca = a & 3;
-      TX acc = dot12(s.Bb + qa * 48 + ca * 12, 1, s.PB + (12 * qa) * nu + b, nu);
-      if (a == b) {
-        if constexpr (pre_diag) {
-          acc += udg[k * nu + a];
-        } else {
-          const int ui = off_u(d, k) + a;
-          acc += (TX)(obj_hdiag(c, ui, flags) + (ident ? 0.0 : sigma_of(c, ui) + dw));
-        }
-      }
-      int qb = b >> 2;
-      if (!ident && qa == qb) {
-        const TB* H = c.blk + c.L.H + ((long long)k * nq + qa) * 100;
-        acc += (TX)H[(6 + (b & 3)) * 10 + (6 + ca)];
-      }
-      if constexpr (f32) {
-        s.Rh[e] = acc;
-        F.LM[(long long)k * nu * nu + e] = acc;
+    #pragma unroll 1
+    for (int e = lane; e < nPA + nPB; e += c.T) {
+      const TX* col;
+      TX* dst;
+      int i, q;
+      if (e < nPA) {
+        i = e / n6;
+        const int r6 = e - i * n6;
+        q = r6 / 6;
+        const int cc = 6 + r6 - 6 * q;
+        col = s.Ab + q * 144 + cc * 12;
+        dst = s.PA + i * nx + 12 * q + cc;
       } else {
-        s.R64[e] = (double)acc;
+        const int e2 = e - nPA;
+        i = e2 / nu;
+        const int cu = e2 - i * nu;
+        q = cu >> 2;
+        col = s.Bb + q * 48 + (cu & 3) * 12;
+        dst = s.PB + e2;
       }
-    MAT_LOOP_END(a, b)
-    MAT_LOOP_BEGIN(a, col, nu, nx)
-      int qa = a >> 2, ca = a & 3;
-      TX acc = dot12(s.Bb + qa * 48 + ca * 12, 1, s.PA + (12 * qa) * nx + col, nx);
-      int qc = col / 12, cc = col - 12 * qc;
-      if (!ident && qc == qa && cc >= 6) {
-        const TB* H = c.blk + c.L.H + ((long long)k * nq + qa) * 100;
-        acc += (TX)H[(cc - 6) * 10 + (6 + ca)];
-      }
-      s.Sh[e] = acc;
-    MAT_LOOP_END(a, col)
-    team_sync(c);
-    // Q^ = A^T P~ A + Q~_k (overwrites Pb); rows of the constant columns of A
-    // are a copy or one FMA, the others twelve-term products
-    for (int e = lane; e < n6 * nx; e += c.T) {
-      const int r6 = e / nx, col = e - r6 * nx, q = r6 / 6, ci = r6 - 6 * q;
-      const TX* pa = s.PA + (12 * q) * nx + col;
-      s.Pb[(12 * q + ci) * nx + col] =
-          ci < 3 ? pa[ci * nx] : pa[(ci - 3) * nx] * s.Ab[q * 144 + ci * 12 + ci - 3] + pa[ci * nx];
-    }
-    for (int e = lane; e < n6 * nx; e += c.T) {
-      const int r6 = e / nx, col = e - r6 * nx, q = r6 / 6, ci = 6 + r6 - 6 * q;
-      s.Pb[(12 * q + ci) * nx + col] = dot12(s.Ab + q * 144 + ci * 12, 1, s.PA + (12 * q) * nx + col, nx);
+      *dst = dot12(s.Pb + i * nx + 12 * q, 1, col, 1);
     }
     team_sync(c);
-    add_state_block<TB, TF, NQ, TX>(c, k, s.Pb, dw, flags, y, true, xdg);
+    // R^ = R~ + B^T P~ B and S^ = S + B^T (P~ A), in one pass.  S^ and Q^ below
+    // are both products with the same PA (entry (i, j) of Q^ from column j of
+    // PA): in P_k = Q^ - S^T R^-1 S^ the rounding errors of PA then enter both
+    // terms alike and partly cancel, which keeps ill-conditioned stages as
+    // accurate as the plain recursion.  (Forming the constant columns of S^
+    // from PB, or mirroring Q^ from its upper triangle, is cheaper but breaks
+    // this pairing.)
+    const int nR = nu * nu;
+    #pragma unroll 1
+    for (int e = lane; e < nR + nu * nx; e += c.T) {
+      int a, colx, sb;
+      const TX* v;
+      if (e < nR) {
+        a = e / nu;
+        colx = e - a * nu;
+        v = s.PB + (12 * (a >> 2)) * nu + colx;
+        sb = nu;
+      } else {
+        const int e2 = e - nR;
+        a = e2 / nx;
+        colx = e2 - a * nx;
+        v = s.PA + (12 * (a >> 2)) * nx + colx;
+        sb = nx;
+      }
+      const int qa = a >> 2, ca = a & 3;
+      TX acc = dot12(s.Bb + qa * 48 + ca * 12, 1, v, sb);
+      const TB* H = c.blk + c.L.H + ((long long)k * nq + qa) * 100;
+      if (e < nR) {
+        const int b = colx;
+        if (a == b) {
+          if constexpr (pre_diag) {
+            acc += udg[k * nu + a];
+          } else {
+            const int ui = off_u(d, k) + a;
+            acc += (TX)(obj_hdiag(c, ui, flags) + (ident ? 0.0 : sigma_of(c, ui) + dw));
+          }
+        }
+        if (!ident && qa == (b >> 2)) acc += (TX)H[(6 + (b & 3)) * 10 + (6 + ca)];
+        if constexpr (f32) {
+          s.Rh[e] = acc;
+          F.LM[(long long)k * nu * nu + e] = acc;
+        } else if constexpr (std::is_same<TX, double>::value) {
+          s.Rh[e] = acc;
+        } else {
+          s.R64[e] = (double)acc;
+        }
+      } else {
+        const int qc = colx / 12, cc = colx - 12 * qc;
+        if (!ident && qc == qa && cc >= 6) acc += (TX)H[(cc - 6) * 10 + (6 + ca)];
+        s.Sh[a * nx + colx] = acc;
+      }
+    }
+    // Q^ = A^T P~ A + Q~_k on the lower triangle only (overwrites Pb; the
+    // update of P_k below reads no other entry).  Rows at the constant columns
+    // of A are a copy or one FMA of PA, the others twelve-term products.
+    #pragma unroll 1
+    for (int e = lane; e < tri_rows_count(d, 6); e += c.T) {
+      int i, j;
+      tri_rows_entry(d, e, 6, i, j);
+      const int qi = i / 12;
+      const TX q = dot12(s.Ab + qi * 144 + (i - 12 * qi) * 12, 1, s.PA + (12 * qi) * nx + j, nx);
+      s.Pb[i * nx + j] = state_term<TB, TF, NQ, TM, TX>(c, k, i, j, dw, flags, xdg, q);
+    }
+    #pragma unroll 1
+    for (int e = lane; e < tri_rows_count(d, 0); e += c.T) {
+      int i, j;
+      tri_rows_entry(d, e, 0, i, j);
+      const int qi = i / 12, ci = i - 12 * qi;
+      TX q = s.PA[i * nx + j];
+      if (ci >= 3) q += s.PA[(i - 3) * nx + j] * s.Ab[qi * 144 + ci * 12 + ci - 3];
+      s.Pb[i * nx + j] = state_term<TB, TF, NQ, TM, TX>(c, k, i, j, dw, flags, xdg, q);
+    }
     if constexpr (f32) {
       // FP32 Cholesky of R^ for the gains; the FP64 inertia test follows the
       // recursion.  A pivot FP32 cannot factor ends the recursion here.
@@ -1099,17 +1226,21 @@ __device__ __noinline__ int factor(Ctx<TB, TF, NQ>& c, Fac<TX> F, double dw, int
       }
       LANE_LOOP(e, nu * nu) if (e % (nu + 1) == 0) s.Rh[e] = (TX)1 / s.Rh[e];
       team_sync(c);
-    } else {
-      // Cholesky of R^ in FP64: the inertia test
-      double* R64 = s.R64;
+    } else if constexpr (std::is_same<TX, double>::value) {
+      // Cholesky of R^ in FP64 (the inertia test), in place; the diagonal is
+      // left as the reciprocals of L_ii, the form every use of it takes
       team_sync(c);
-      if (warp_cholesky(c, R64, nu) < 0.0) return 0;
-      // Cholesky factor in the factorisation precision (stored, and used for K);
-      // the diagonal is stored as its reciprocal: every use of L_ii divides by it
-      LANE_LOOP(e, nu * nu) s.Rh[e] = (TX)(e % (nu + 1) == 0 ? 1.0 / R64[e] : R64[e]);
+      if (!warp_cholesky_rdiag(c, s.Rh, nu)) return 0;
+    } else {
+      // Cholesky of R^ in FP64 (the inertia test), then the factor in the
+      // factorisation precision with the reciprocal diagonal
+      team_sync(c);
+      if (!warp_cholesky_rdiag(c, s.R64, nu)) return 0;
+      LANE_LOOP(e, nu * nu) s.Rh[e] = (TX)s.R64[e];
       team_sync(c);
     }
     // K = -R^{-1} S^: one column per lane
+    #pragma unroll 1
     for (int col = lane; col < nx; col += c.T) {
       TX z[32];
       for (int i = 0; i < nu; ++i) {
@@ -1129,11 +1260,10 @@ __device__ __noinline__ int factor(Ctx<TB, TF, NQ>& c, Fac<TX> F, double dw, int
     // in place: each thread reads lower entries and writes their mirror images
     {
       const int ntri = nx * (nx + 1) / 2;
+      #pragma unroll 1
       for (int e = lane; e < ntri; e += c.T) {
-        int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        while (i * (i + 1) / 2 > e) --i;
-        while ((i + 1) * (i + 2) / 2 <= e) ++i;
-        const int j = e - i * (i + 1) / 2;
+        int i, j;
+        tri_index(e, i, j);
         TX a0 = 0, a1 = 0;
         int a = 0;
         for (; a + 1 < nu; a += 2) {
@@ -1153,7 +1283,7 @@ __device__ __noinline__ int factor(Ctx<TB, TF, NQ>& c, Fac<TX> F, double dw, int
     team_sync(c);
     if (resto) {
       const double* D = dv + (k == 0 ? 0 : row_dyn(d, k - 1));
-      if (!resto_transform<TB, TF, NQ, TX>(c, s.Pb, D, F.LM + (long long)k * nx * nx,
+      if (!resto_transform<TB, TF, NQ, TM, TX>(c, s.Pb, D, F.LM + (long long)k * nx * nx,
                                        F.Yr + (long long)k * nx * nx))
         return 0;
     }
@@ -1175,8 +1305,8 @@ __device__ __noinline__ int factor(Ctx<TB, TF, NQ>& c, Fac<TX> F, double dw, int
 // is the augmented matrix of Eq. 7 (restoration: with the elastic variables)
 // and r is K-sized: [r_x (n) | r_p (m) | r_n (m) | r_c (m)] (r_p, r_n only in
 // restoration; the layout always reserves them).  out has the same layout.
-template <class TB, class TF, int NQ, class TX>
-__device__ __noinline__ void solve(Ctx<TB, TF, NQ>& c, Fac<TX> F, const double* r, double* out, int flags,
+template <class TB, class TF, int NQ, int TM, class TX>
+__device__ __noinline__ void solve(Ctx<TB, TF, NQ, TM>& c, Fac<TX> F, const double* r, double* out, int flags,
                       const double* y) {
   const auto& d = c.d;
   const int lane = c.lane;
@@ -1212,11 +1342,13 @@ __device__ __noinline__ void solve(Ctx<TB, TF, NQ>& c, Fac<TX> F, const double* 
   double* qin = c.f + c.L.qin;
   const double* igr = c.f + c.L.igr;
   if (d.ni > 0) {
+    #pragma unroll 1
     for (int t = lane; t < N * d.ni; t += c.T) {
       const int k = 1 + t / d.ni, rr = t - (k - 1) * d.ni;
       wrow[t] = evr[t] * rx[off_s(d, k) + rr] + ev[t] * rct[row_ineq(d, k) + rr];
     }
     team_sync(c);
+    #pragma unroll 1
     for (int e = lane; e < N * np; e += c.T) {
       const int k = 1 + e / np, a = e - (k - 1) * np;
       const int q = a / 3, comp = a - 3 * q;
@@ -1405,6 +1537,7 @@ __device__ __noinline__ void solve(Ctx<TB, TF, NQ>& c, Fac<TX> F, const double* 
     team_sync(c);
   }
   // inequality multipliers and slacks
+  #pragma unroll 1
   for (int t = lane; t < N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, rr = t - (t / d.ni) * d.ni;
     const IneqGrad g = ineq_grad_tab(d, igr, t, rr);
@@ -1433,8 +1566,8 @@ __device__ __noinline__ void solve(Ctx<TB, TF, NQ>& c, Fac<TX> F, const double* 
 // ---------------------------------------------------- KKT mat-vec (FP64)
 // out = K v for the matrix that `factor` condensed (same dw, same phase),
 // K-sized layout as in `solve`.  Used for iterative refinement.
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void kkt_matvec(Ctx<TB, TF, NQ>& c, const double* v, double* out, double dw,
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void kkt_matvec(Ctx<TB, TF, NQ, TM>& c, const double* v, double* out, double dw,
                            const double* y) {
   const auto& d = c.d;
   const int lane = c.lane;
@@ -1453,6 +1586,7 @@ __device__ __noinline__ void kkt_matvec(Ctx<TB, TF, NQ>& c, const double* v, dou
     out[i] = acc;
   }
   team_sync(c);
+  #pragma unroll 1
   for (int t = lane; t < N * d.nq; t += c.T) {
     int k = t / d.nq, q = t - (t / d.nq) * d.nq;
     const TB* A = c.blk + c.L.A + ((long long)k * d.nq + q) * 144;
@@ -1482,6 +1616,7 @@ __device__ __noinline__ void kkt_matvec(Ctx<TB, TF, NQ>& c, const double* v, dou
   LANE_LOOP(i, nx) out[off_x(d, N) + i] += vy[row_dyn(d, N - 1) + i];
   team_sync(c);
   // inequality Hessian and G^T v_y on positions; -v_y on slacks
+  #pragma unroll 1
   for (int t = lane; t < N * 3 * d.nq; t += c.T) {
     int k = 1 + t / (3 * d.nq);
     int pc = t - (t / (3 * d.nq)) * (3 * d.nq);
@@ -1503,6 +1638,7 @@ __device__ __noinline__ void kkt_matvec(Ctx<TB, TF, NQ>& c, const double* v, dou
     }
     out[off_x(d, k) + i] += acc;
   }
+  #pragma unroll 1
   for (int t = lane; t < N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
     out[off_s(d, k) + r] -= vy[row_ineq(d, k) + r];
@@ -1516,6 +1652,7 @@ __device__ __noinline__ void kkt_matvec(Ctx<TB, TF, NQ>& c, const double* v, dou
   team_sync(c);
   // constraint part: J v_w (- v_p + v_n in restoration)
   LANE_LOOP(i, nx) oy[i] = v[i];
+  #pragma unroll 1
   for (int t = lane; t < N * d.nq; t += c.T) {
     int k = t / d.nq, q = t - (t / d.nq) * d.nq;
     const TB* A = c.blk + c.L.A + ((long long)k * d.nq + q) * 144;
@@ -1530,6 +1667,7 @@ __device__ __noinline__ void kkt_matvec(Ctx<TB, TF, NQ>& c, const double* v, dou
       oy[row_dyn(d, k) + 12 * q + r] = acc;
     }
   }
+  #pragma unroll 1
   for (int t = lane; t < N * d.ni; t += c.T) {
     int k = 1 + t / d.ni, r = t - (t / d.ni) * d.ni;
     const IneqGrad g = ineq_grad_tab(d, igr, t, r);

@@ -18,32 +18,36 @@ namespace bipm {
 enum Outcome : int { OUT_ACCEPTED = 0, OUT_LS_FAILED = 1 };
 
 // ------------------------------------------------------------- reductions
-template <class TB, class TF, int NQ>
-__device__ double l1_norm(Ctx<TB, TF, NQ>& c, const double* v, int len) {
+template <class TB, class TF, int NQ, int TM>
+__device__ double l1_norm(Ctx<TB, TF, NQ, TM>& c, const double* v, int len) {
   double a = 0.0;
+  #pragma unroll 1
   for (int i = c.lane; i < len; i += c.T) a += fabs(v[i]);
   return team_sum(c, a);
 }
-template <class TB, class TF, int NQ>
-__device__ double inf_norm(Ctx<TB, TF, NQ>& c, const double* v, int len) {
+template <class TB, class TF, int NQ, int TM>
+__device__ double inf_norm(Ctx<TB, TF, NQ, TM>& c, const double* v, int len) {
   double a = 0.0;
+  #pragma unroll 1
   for (int i = c.lane; i < len; i += c.T) a = fmax(a, fabs(v[i]));
   return team_max(c, a);
 }
-template <class TB, class TF, int NQ>
-__device__ bool all_finite(Ctx<TB, TF, NQ>& c, const double* v, int len) {
+template <class TB, class TF, int NQ, int TM>
+__device__ bool all_finite(Ctx<TB, TF, NQ, TM>& c, const double* v, int len) {
   int bad = 0;
+  #pragma unroll 1
   for (int i = c.lane; i < len; i += c.T) bad |= !isfinite(v[i]);
   return !team_or(c, bad);
 }
 
 // barrier objective phi_mu (Eq. 3) with the one-sided damping term, over the
 // first `len` entries of a W-sized point w; +inf outside the bounds
-template <class TB, class TF, int NQ>
-__device__ __noinline__ double barrier_phi(Ctx<TB, TF, NQ>& c, const double* w, double f, double mu, int len) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ double barrier_phi(Ctx<TB, TF, NQ, TM>& c, const double* w, double f, double mu, int len) {
   double acc = 0.0;
   int bad = 0;
   const int nb = n_bounded(c.d, len);
+  #pragma unroll 1
   for (int b = c.lane; b < nb; b += c.T) {
     int kind;
     const int i = bnd_index(c.d, b, kind);
@@ -67,8 +71,8 @@ struct ErrParts {
   double dual, prim, y1, z1, nb;
 };
 
-template <class TB, class TF, int NQ>
-__device__ __noinline__ ErrParts err_parts(Ctx<TB, TF, NQ>& c) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ ErrParts err_parts(Ctx<TB, TF, NQ, TM>& c) {
   const double* gf = c.f + c.L.gf;
   const double* jty = c.f + c.L.jty;
   const double* zl = c.f + c.L.zl;
@@ -76,6 +80,7 @@ __device__ __noinline__ ErrParts err_parts(Ctx<TB, TF, NQ>& c) {
   const double* y = c.f + c.L.y;
   const double* cv = c.f + c.L.c;
   double du = 0.0, z1 = 0.0, nb = 0.0;
+  #pragma unroll 1
   for (int i = c.lane; i < c.nw; i += c.T) {
     int kind = wkind(c.d, i);
     double zli = has_lower(kind) ? zl[i] : 0.0;
@@ -85,6 +90,7 @@ __device__ __noinline__ ErrParts err_parts(Ctx<TB, TF, NQ>& c) {
     nb += (has_lower(kind) ? 1.0 : 0.0) + (has_upper(kind) ? 1.0 : 0.0);
   }
   double pr = 0.0, y1 = 0.0;
+  #pragma unroll 1
   for (int i = c.lane; i < c.d.m; i += c.T) {
     pr = fmax(pr, fabs(cv[i]));
     y1 += fabs(y[i]);
@@ -98,13 +104,14 @@ __device__ __noinline__ ErrParts err_parts(Ctx<TB, TF, NQ>& c) {
   return e;
 }
 
-template <class TB, class TF, int NQ>
-__device__ __noinline__ double opt_error(Ctx<TB, TF, NQ>& c, const ErrParts& e, double mu) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ double opt_error(Ctx<TB, TF, NQ, TM>& c, const ErrParts& e, double mu) {
   const double* w = c.f + c.L.x;
   const double* zl = c.f + c.L.zl;
   const double* zu = c.f + c.L.zu;
   double comp = 0.0;
   const int nbnd = n_bounded(c.d, c.nw);
+  #pragma unroll 1
   for (int b = c.lane; b < nbnd; b += c.T) {
     int kind;
     const int i = bnd_index(c.d, b, kind);
@@ -120,10 +127,11 @@ __device__ __noinline__ double opt_error(Ctx<TB, TF, NQ>& c, const ErrParts& e, 
 
 // largest alpha in (0, 1] keeping the bounded entries of w + alpha dw at least
 // the fraction 1 - tau of their distance to the bounds
-template <class TB, class TF, int NQ>
-__device__ __noinline__ double ftb_primal(Ctx<TB, TF, NQ>& c, const double* w, const double* dw, double tau) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ double ftb_primal(Ctx<TB, TF, NQ, TM>& c, const double* w, const double* dw, double tau) {
   double a = 1.0;
   const int nb = n_bounded(c.d, c.nw);
+  #pragma unroll 1
   for (int b = c.lane; b < nb; b += c.T) {
     int kind;
     const int i = bnd_index(c.d, b, kind);
@@ -148,6 +156,7 @@ __device__ __forceinline__ bool in_filter(const C& c, const double* filt, int nf
                                           double phi, double theta_max) {
   if (!(theta < theta_max)) return true;
   int hit = 0;
+  #pragma unroll 1
   for (int j = c.lane; j < nf; j += c.T) hit |= (theta >= filt[2 * j] && phi >= filt[2 * j + 1]);
   return team_or(c, hit);
 }
@@ -187,13 +196,15 @@ __device__ __forceinline__ void filter_add(const C& c, double* filt, int& nf, do
 // the condensation weight E of the slacks.  Relative to the O(1) Hessian
 // blocks it measures how much of FP32's 24-bit mantissa the factorisation
 // loses in the position and input blocks.
-template <class TB, class TF, int NQ>
-__device__ __noinline__ double barrier_scale(Ctx<TB, TF, NQ>& c) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ double barrier_scale(Ctx<TB, TF, NQ, TM>& c) {
   const auto& d = c.d;
   const double* ev = c.f + c.L.ev;
   const double* sg = c.f + c.L.sig;
   double b = 0.0;
+  #pragma unroll 1
   for (int t = c.lane; t < d.N * d.ni; t += c.T) b = fmax(b, ev[t]);
+  #pragma unroll 1
   for (int t = c.lane; t < d.N * d.nu; t += c.T) {
     int k = t / d.nu, a = t - (t / d.nu) * d.nu;
     b = fmax(b, sg[off_u(d, k) + a]);
@@ -201,14 +212,14 @@ __device__ __noinline__ double barrier_scale(Ctx<TB, TF, NQ>& c) {
   return team_max(c, b);
 }
 
-template <class TB, class TF, int NQ>
-__device__ __noinline__ bool factor_any(Ctx<TB, TF, NQ>& c, double dw, bool force64) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ bool factor_any(Ctx<TB, TF, NQ, TM>& c, double dw, bool force64) {
   const int flags = c.resto ? FF_RESTO : 0;
   const double* y = c.f + c.L.y;
   if (HighPrecision<TF>::value && !std::is_same<TF, double>::value && !c.resto && !force64) {
     // double-float factorisation: accurate enough to need no refinement
     c.use64 = 0;
-    return factor<TB, TF, NQ, TF>(c, c.fac, dw, flags, y) != 0;
+    return factor<TB, TF, NQ, TM, TF>(c, c.fac, dw, flags, y) != 0;
   }
   if (sizeof(TF) == 4 && !c.resto && !force64) {
     // per-problem precision choice: FP32 only while the barrier terms leave
@@ -221,14 +232,14 @@ __device__ __noinline__ bool factor_any(Ctx<TB, TF, NQ>& c, double dw, bool forc
   }
   if (HighPrecision<TF>::value || c.resto || force64) {
     c.use64 = 1;
-    return factor<TB, TF, NQ, double>(c, c.fac64, dw, flags, y) != 0;
+    return factor<TB, TF, NQ, TM, double>(c, c.fac64, dw, flags, y) != 0;
   }
-  int r = factor<TB, TF, NQ, TF>(c, c.fac, dw, flags, y);
+  int r = factor<TB, TF, NQ, TM, TF>(c, c.fac, dw, flags, y);
   if (r == 0) return false;
   if (r == 2) {
     c.n_esc++;
     c.use64 = 1;
-    return factor<TB, TF, NQ, double>(c, c.fac64, dw, flags, y) != 0;
+    return factor<TB, TF, NQ, TM, double>(c, c.fac64, dw, flags, y) != 0;
   }
   c.use64 = 0;
   return true;
@@ -241,16 +252,16 @@ __device__ __noinline__ bool factor_any(Ctx<TB, TF, NQ>& c, double dw, bool forc
 // residual ratio |K out + r| / (min(|out|, 1e6 |r|) + |r|) drops below 1e-10;
 // if that fails within the restarts the matrix is refactorised in FP64.
 // Returns false only if that FP64 refactorisation reports wrong inertia.
-template <class TB, class TF, int NQ>
-__device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ>& c, const double* r, double* out) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ, TM>& c, const double* r, double* out) {
   const int flags = c.resto ? FF_RESTO : 0;
   const double* y = c.f + c.L.y;
   if (c.use64) {
-    solve<TB, TF, NQ, double>(c, c.fac64, r, out, flags, y);
+    solve<TB, TF, NQ, TM, double>(c, c.fac64, r, out, flags, y);
     return true;
   }
   if (HighPrecision<TF>::value) {  // double-float factors: no refinement needed
-    solve<TB, TF, NQ, TF>(c, c.fac, r, out, flags, y);
+    solve<TB, TF, NQ, TM, TF>(c, c.fac, r, out, flags, y);
     return true;
   }
   const int lane = c.lane;
@@ -264,6 +275,7 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ>& c, const double* r, 
   auto at = [&](int i) { return i < nused ? i : nwk + (i - nused); };
   auto norm2 = [&](const double* v) {
     double a = 0.0;
+    #pragma unroll 1
     for (int i = lane; i < len; i += c.T) {
       double t = v[at(i)];
       a += t * t;
@@ -272,21 +284,24 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ>& c, const double* r, 
   };
   auto norm_inf = [&](const double* v) {
     double a = 0.0;
+    #pragma unroll 1
     for (int i = lane; i < len; i += c.T) a = fmax(a, fabs(v[at(i)]));
     return team_max(c, a);
   };
   // preconditioner: z = M^{-1} v  (solve(r') returns K z = -r', so r' = -v)
   auto precond = [&](const double* v, double* z) {
+    #pragma unroll 1
     for (int i = lane; i < len; i += c.T) corr[at(i)] = -v[at(i)];
     team_sync(c);
-    solve<TB, TF, NQ, TF>(c, c.fac, corr, z, flags, y);
+    solve<TB, TF, NQ, TM, TF>(c, c.fac, corr, z, flags, y);
   };
-  solve<TB, TF, NQ, TF>(c, c.fac, r, out, flags, y);
+  solve<TB, TF, NQ, TM, TF>(c, c.fac, r, out, flags, y);
   const double rnorm = norm_inf(r);
   if (rnorm == 0.0) return true;
   for (int rs = 0; rs <= kGmresRestarts; ++rs) {
     // residual of K out = -r
     kkt_matvec(c, out, res, c.dw, y);
+    #pragma unroll 1
     for (int i = lane; i < len; i += c.T) res[at(i)] = -r[at(i)] - res[at(i)];
     team_sync(c);
     double ratio = norm_inf(res) / (fmin(norm_inf(out), 1e6 * rnorm) + rnorm);
@@ -295,6 +310,7 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ>& c, const double* r, 
     double beta = norm2(res);
     double H[kGmresM + 1][kGmresM], cs[kGmresM], sn[kGmresM], g[kGmresM + 1];
     const double ibeta = 1.0 / beta;
+    #pragma unroll 1
     for (int i = lane; i < len; i += c.T) V[at(i)] = res[at(i)] * ibeta;
     g[0] = beta;
     team_sync(c);
@@ -308,8 +324,10 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ>& c, const double* r, 
       for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
         const double* vi = V + (long long)i * nk;
         double h = 0.0;
+        #pragma unroll 1
         for (int t = lane; t < len; t += c.T) h += vn[at(t)] * vi[at(t)];
         h = team_sum(c, h);
+        #pragma unroll 1
         for (int t = lane; t < len; t += c.T) vn[at(t)] -= h * vi[at(t)];
         team_sync(c);
         H[i][j] = h;
@@ -318,6 +336,7 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ>& c, const double* r, 
       H[j + 1][j] = hn;
       if (hn > 0.0) {
         const double ihn = 1.0 / hn;
+        #pragma unroll 1
         for (int t = lane; t < len; t += c.T) vn[at(t)] *= ihn;
         team_sync(c);
       }
@@ -344,6 +363,7 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ>& c, const double* r, 
       for (int t = i + 1; t < jm; ++t) acc -= H[i][t] * yv[t];
       yv[i] = H[i][i] != 0.0 ? acc / H[i][i] : 0.0;
     }
+    #pragma unroll 1
     for (int t = lane; t < len; t += c.T) {
       double acc = 0.0;
       for (int i = 0; i < jm; ++i) acc += yv[i] * V[(long long)i * nk + at(t)];
@@ -351,14 +371,15 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ>& c, const double* r, 
     }
     team_sync(c);
     precond(res, res);
+    #pragma unroll 1
     for (int t = lane; t < len; t += c.T) out[at(t)] += res[at(t)];
     team_sync(c);
   }
   // refinement did not converge: refactorise in FP64
   c.n_esc++;
-  if (factor<TB, TF, NQ, double>(c, c.fac64, c.dw, flags, y) == 0) return false;
+  if (factor<TB, TF, NQ, TM, double>(c, c.fac64, c.dw, flags, y) == 0) return false;
   c.use64 = 1;
-  solve<TB, TF, NQ, double>(c, c.fac64, r, out, flags, y);
+  solve<TB, TF, NQ, TM, double>(c, c.fac64, r, out, flags, y);
   // an FP64 step that is not finite cannot be used: the problem stops
   if (!all_finite(c, out, nused) || !all_finite(c, out + nwk, c.d.m)) c.esc_failed = 1;
   return true;
@@ -366,8 +387,8 @@ __device__ __noinline__ bool solve_refined(Ctx<TB, TF, NQ>& c, const double* r, 
 
 // Least-squares multipliers: [[I, J^T], [J, 0]] (w, y) = (-(grad f - z_L + z_U), 0);
 // y = 0 if |y|_inf > y_max.
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void ls_multipliers(Ctx<TB, TF, NQ>& c) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void ls_multipliers(Ctx<TB, TF, NQ, TM>& c) {
   const auto& d = c.d;
   const int lane = c.lane;
   double* w = c.f + c.L.x;
@@ -384,20 +405,21 @@ __device__ __noinline__ void ls_multipliers(Ctx<TB, TF, NQ>& c) {
   }
   LANE_LOOP(i, d.m) rhs[c.L.nw + i] = 0.0;
   team_sync(c);
-  factor<TB, TF, NQ, double>(c, c.fac64, 0.0, FF_IDENT, y);
-  solve<TB, TF, NQ, double>(c, c.fac64, rhs, sol, FF_IDENT, y);
+  factor<TB, TF, NQ, TM, double>(c, c.fac64, 0.0, FF_IDENT, y);
+  solve<TB, TF, NQ, TM, double>(c, c.fac64, rhs, sol, FF_IDENT, y);
   double ymax = inf_norm(c, sol + c.L.nw, d.m);
   LANE_LOOP(i, d.m) y[i] = ymax > kYmax ? 0.0 : sol[c.L.nw + i];
   team_sync(c);
 }
 
 // z <- max(min(z, kappa_Sigma mu / s), mu / (kappa_Sigma s)) over the first len entries
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void kappa_sigma_reset(Ctx<TB, TF, NQ>& c, int len, double mu) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void kappa_sigma_reset(Ctx<TB, TF, NQ, TM>& c, int len, double mu) {
   double* w = c.f + c.L.x;
   double* zl = c.f + c.L.zl;
   double* zu = c.f + c.L.zu;
   const int nb = n_bounded(c.d, len);
+  #pragma unroll 1
   for (int b = c.lane; b < nb; b += c.T) {
     int kind;
     const int i = bnd_index(c.d, b, kind);
@@ -423,14 +445,15 @@ __device__ __forceinline__ void end_globalization(SlotState& S) {
 
 // Average and minimum of the complementarity products s_i z_i over all bounds
 // of the original problem.
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void complementarity_stats(Ctx<TB, TF, NQ>& c, double& avg, double& mn) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void complementarity_stats(Ctx<TB, TF, NQ, TM>& c, double& avg, double& mn) {
   const auto& d = c.d;
   const double* w = c.f + c.L.x;
   const double* zl = c.f + c.L.zl;
   const double* zu = c.f + c.L.zu;
   double sum = 0.0, lo = INFINITY, cnt = 0.0;
   const int nb = n_bounded(d, d.n);
+  #pragma unroll 1
   for (int b = c.lane; b < nb; b += c.T) {
     int kind;
     const int i = bnd_index(d, b, kind);
@@ -463,17 +486,20 @@ __device__ __forceinline__ double loqo_mu(double avg, double mn) {
 
 // 1-norm primal-dual error of the barrier problem at mu (original problem):
 // |grad f + J^T y - z_L + z_U|_1 + |c|_1 + |S_L z_L - mu e|_1 + |S_U z_U - mu e|_1
-template <class TB, class TF, int NQ>
-__device__ __noinline__ double pd_error(Ctx<TB, TF, NQ>& c, const double* w, const double* zl, const double* zu,
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ double pd_error(Ctx<TB, TF, NQ, TM>& c, const double* w, const double* zl, const double* zu,
                                         const double* gf, const double* jty, const double* cv, double mu) {
   const auto& d = c.d;
   double a = 0.0;
+  #pragma unroll 1
   for (int i = c.lane; i < d.n; i += c.T) {
     const int kind = wkind(d, i);
     a += fabs(gf[i] + jty[i] - (has_lower(kind) ? zl[i] : 0.0) + (has_upper(kind) ? zu[i] : 0.0));
   }
+  #pragma unroll 1
   for (int i = c.lane; i < d.m; i += c.T) a += fabs(cv[i]);
   const int nb = n_bounded(d, d.n);
+  #pragma unroll 1
   for (int b = c.lane; b < nb; b += c.T) {
     int kind;
     const int i = bnd_index(d, b, kind);
@@ -491,8 +517,8 @@ struct TrialVal {
 
 // trial point w + alpha * dir: constraint violation and barrier objective of
 // the current phase; the phase constraint vector goes to ct
-template <class TB, class TF, int NQ>
-__device__ __noinline__ TrialVal trial_point(Ctx<TB, TF, NQ>& c, double alpha, const double* dir) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ TrialVal trial_point(Ctx<TB, TF, NQ, TM>& c, double alpha, const double* dir) {
   const auto& d = c.d;
   const int lane = c.lane;
   const double* w = c.f + c.L.x;
@@ -515,8 +541,8 @@ __device__ __noinline__ TrialVal trial_point(Ctx<TB, TF, NQ>& c, double alpha, c
   return tv;
 }
 
-template <class TB, class TF, int NQ>
-__device__ __noinline__ void iterate(Ctx<TB, TF, NQ>& c, SlotState& S) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __noinline__ void iterate(Ctx<TB, TF, NQ, TM>& c, SlotState& S) {
   const auto& d = c.d;
   const int lane = c.lane;
   const Options& opt = c.P->opt;
@@ -689,6 +715,7 @@ __device__ __noinline__ void iterate(Ctx<TB, TF, NQ>& c, SlotState& S) {
   team_sync(c);
   {
     const int nb = n_bounded(d, c.nw);
+    #pragma unroll 1
     for (int b = lane; b < nb; b += c.T) {
       int kind;
       const int i = bnd_index(d, b, kind);
@@ -774,6 +801,7 @@ __device__ __noinline__ void iterate(Ctx<TB, TF, NQ>& c, SlotState& S) {
     auto dual_max = [&](const double* ddx) {
       double az = 1.0;
       const int nb = n_bounded(d, c.nw);
+      #pragma unroll 1
       for (int b = lane; b < nb; b += c.T) {
         int kind;
         const int i = bnd_index(d, b, kind);
@@ -794,6 +822,7 @@ __device__ __noinline__ void iterate(Ctx<TB, TF, NQ>& c, SlotState& S) {
       const double az = az_fixed >= 0.0 ? az_fixed : dual_max(ddx);
       const int nb = n_bounded(d, c.nw);
       // bound multipliers from the step at the current point, then the primal step
+      #pragma unroll 1
       for (int b = lane; b < nb; b += c.T) {
         int kind;
         const int i = bnd_index(d, b, kind);
@@ -812,6 +841,7 @@ __device__ __noinline__ void iterate(Ctx<TB, TF, NQ>& c, SlotState& S) {
     // tiny step (Table I row 4)
     // max_i |dx_i| / (1 + |w_i|) < 10 eps, tested without a division per entry
     int big = 0;
+    #pragma unroll 1
     for (int i = lane; i < c.nw; i += c.T) big |= fabs(dx[i]) >= 10.0 * kEpsMach * (1.0 + fabs(w[i]));
     if (!team_or(c, big)) {
       accept(a_max, sol, false);
@@ -823,6 +853,7 @@ __device__ __noinline__ void iterate(Ctx<TB, TF, NQ>& c, SlotState& S) {
       tiny = 0;
       phi0 = barrier_phi(c, w, fph, mu, c.nw);
       double gd = 0.0;
+      #pragma unroll 1
       for (int i = lane; i < c.nw; i += c.T) gd += gphi[i] * dx[i];
       gdx = team_sum(c, gd);
       double a_min;
@@ -876,6 +907,7 @@ __device__ __noinline__ void iterate(Ctx<TB, TF, NQ>& c, SlotState& S) {
         team_sync(c);
         {
           const int nb = n_bounded(d, n);
+          #pragma unroll 1
           for (int b = lane; b < nb; b += c.T) {
             int kind;
             const int i = bnd_index(d, b, kind);

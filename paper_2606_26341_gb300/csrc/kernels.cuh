@@ -14,14 +14,17 @@ constexpr int kBulkVisit = 64;     // iterations per problem in the warp kernel
 constexpr int kQueueVisit = 96;    // iterations before a queue problem is parked for block teams
 constexpr int kMaxClasses = 64;    // structure classes of one mixed queue
 
-template <class TB, class TF, int NQ>
-__device__ void make_ctx(Ctx<TB, TF, NQ>& c, const Params* P, int slot, int lane, int T, double* red,
+template <class TB, class TF, int NQ, int TM>
+__device__ void make_ctx(Ctx<TB, TF, NQ, TM>& c, const Params* P, int slot, int lane, int T, double* red,
                          char* smem) {
   c.P = P;
   static_cast<Dims&>(c.d) = P->d;
   c.L = P->L;
   c.lane = lane;
-  c.T = T;
+  if constexpr (TM == 0)
+    c.T = T;
+  else
+    (void)T;
   c.red = red;
   c.slot = slot;
   c.f = P->f64 + (long long)slot * P->L.slot_f64;
@@ -53,8 +56,8 @@ __device__ void make_ctx(Ctx<TB, TF, NQ>& c, const Params* P, int slot, int lane
 }
 
 // final objective, scaled KKT error and infeasibility of the original problem
-template <class TB, class TF, int NQ>
-__device__ void slot_metrics(Ctx<TB, TF, NQ>& c, SlotState& S) {
+template <class TB, class TF, int NQ, int TM>
+__device__ void slot_metrics(Ctx<TB, TF, NQ, TM>& c, SlotState& S) {
   c.resto = 0;
   c.nw = c.d.n;
   double* w = c.f + c.L.x;
@@ -70,8 +73,8 @@ __device__ void slot_metrics(Ctx<TB, TF, NQ>& c, SlotState& S) {
 }
 
 // true (in every thread of the team) once the call's time budget has run out
-template <class TB, class TF, int NQ>
-__device__ __forceinline__ bool team_budget_spent(Ctx<TB, TF, NQ>& c) {
+template <class TB, class TF, int NQ, int TM>
+__device__ __forceinline__ bool team_budget_spent(Ctx<TB, TF, NQ, TM>& c) {
   if (c.P->time_limit_ns == 0) return false;
   int v = 0;
   if (c.lane == 0) v = budget_spent(c.P) ? 1 : 0;
@@ -82,8 +85,8 @@ __device__ __forceinline__ bool team_budget_spent(Ctx<TB, TF, NQ>& c) {
 // terminates, or (visit_cap > 0) for at most visit_cap iterations in this visit.
 // Before every iteration the call's time budget is checked; returns true if the
 // slot stopped because it ran out (the problem is left running, resumable).
-template <class TB, class TF, int NQ>
-__device__ bool run_slot(Ctx<TB, TF, NQ>& c, SlotState& S, int n_iter, int visit_cap) {
+template <class TB, class TF, int NQ, int TM>
+__device__ bool run_slot(Ctx<TB, TF, NQ, TM>& c, SlotState& S, int n_iter, int visit_cap) {
   int done = 0;
   bool spent = false;
   if (n_iter > 0) {
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     if (slot >= P->n_slots) break;
     SlotState S = P->st[slot];
     if (S.status != BIPM_RUNNING) continue;
-    Ctx<TB, TF, NQ> c;
+    Ctx<TB, TF, NQ, 32> c;
     make_ctx(c, P, slot, lane, 32, nullptr, smem);
     run_slot(c, S, n_iter, visit_cap);
     __syncwarp();
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(kBlockTeam)
     if (slot >= P->n_slots) break;
     SlotState S = P->st[slot];
     if (S.status != BIPM_RUNNING) continue;
-    Ctx<TB, TF, NQ> c;
+    Ctx<TB, TF, NQ, 0> c;
     make_ctx(c, P, slot, (int)threadIdx.x, (int)blockDim.x, red, smem);
     run_slot(c, S, n_iter, 0);
     __syncthreads();
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     const double* gq = x_guess ? x_guess + (long long)id * d.n : nullptr;
     SlotState S = init_slot(P, slot, lane, gq, nullptr, gq != nullptr);
     S.problem_id = id;
-    Ctx<TB, TF, NQ> c;
+    Ctx<TB, TF, NQ, 32> c;
     make_ctx(c, P, slot, lane, 32, nullptr, smem);
     int warm = gq ? 1 : 0, warm_iters = 0;
     bool done = false, spent = false;
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 6)
     SlotState S = init_slot(P, slot, lane, nullptr, nullptr, 0);
     S.problem_id = id;
     S.cls = k;
-    Ctx<TB, TF, NQ> c;
+    Ctx<TB, TF, NQ, 32> c;
     make_ctx(c, P, slot, lane, 32, nullptr, smem);
     const bool spent = run_slot(c, S, 0, P->visit_cap);
     if (S.status == BIPM_RUNNING && !spent) {
@@ -457,7 +460,7 @@ __global__ void __launch_bounds__(kBlockTeam)
     SlotState S = P0->st[slot];
     if (S.status != BIPM_RUNNING) continue;
     const Params* P = Pc + S.cls;
-    Ctx<TB, TF, NQ> c;
+    Ctx<TB, TF, NQ, 0> c;
     make_ctx(c, P, slot, (int)threadIdx.x, (int)blockDim.x, red, smem);
     run_slot(c, S, 0, 0);
     __syncthreads();
