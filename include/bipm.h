@@ -489,6 +489,15 @@ int bipm_get_stats(const bipm_batch* b, bipm_stats* out, int first_slot, int cou
 int bipm_get_iterate(const bipm_batch* b, int slot, bipm_iterate* out);
 int bipm_set_iterate(bipm_batch* b, int slot, const bipm_iterate* in);
 
+/* Self-check of the FP64 reciprocal square root used by the pivot-block
+ * Cholesky of the Riccati recursion (Sec. IV, the factorisation of Eq. 7; the
+ * paper has no counterpart of the routine itself): writes to *max_ulp (host)
+ * the largest distance, in FP64 units in the last place, between it and
+ * CUDA's correctly rounded 1.0 / sqrt(x) over n log-spaced x in [1e-40, 1e40],
+ * computed on the current device with the default stream.  BIPM_EINVAL for
+ * n < 1 or a null pointer, BIPM_ECUDA on a CUDA error. */
+int bipm_check_rsqrt(int n, double* max_ulp);
+
 /* Thread-local message of the last failed call ("" if none); the pointer
  * stays valid until the thread's next failing call.  The paper has no
  * counterpart; it cannot fail. */

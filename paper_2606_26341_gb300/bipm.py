@@ -102,7 +102,7 @@ EXPORTS = ["bipm_create_batch", "bipm_dims", "bipm_set_problems", "bipm_set_init
            "bipm_solve_static", "bipm_warm_features", "bipm_warm_encode", "bipm_warm_decode",
            "bipm_mlp_create", "bipm_mlp_param_count", "bipm_mlp_set_params", "bipm_mlp_get_params",
            "bipm_mlp_forward", "bipm_mlp_loss_grad", "bipm_mlp_train_step", "bipm_mlp_destroy",
-           "bipm_last_error", "bipm_destroy"]
+           "bipm_check_rsqrt", "bipm_last_error", "bipm_destroy"]
 PHASES = ["eval", "derivs", "factor", "solve", "line_search", "other", "lsq_mult", "total"]
 
 _LIB = None
@@ -153,6 +153,7 @@ def load_library(build_if_missing: bool = True):
     lib.bipm_mlp_train_step.argtypes = [vp, vp, vp, i, vp, i, ctypes.c_float, vp]
     lib.bipm_mlp_destroy.argtypes = [vp]
     lib.bipm_mlp_destroy.restype = None
+    lib.bipm_check_rsqrt.argtypes = [i, ctypes.POINTER(ctypes.c_double)]
     lib.bipm_last_error.restype = ctypes.c_char_p
     lib.bipm_destroy.argtypes = [vp]
     lib.bipm_destroy.restype = None
@@ -169,6 +170,14 @@ class BipmError(RuntimeError):
     def __init__(self, msg, code=0):
         super().__init__(msg)
         self.code = code
+
+
+def check_rsqrt(n: int) -> float:
+    """Largest ulp distance of the factorisation's FP64 reciprocal square root
+    from CUDA's 1.0 / sqrt(x) over n log-spaced x (bipm_check_rsqrt)."""
+    out = ctypes.c_double()
+    _check(load_library().bipm_check_rsqrt(int(n), ctypes.byref(out)))
+    return out.value
 
 
 def solve_static(desc, theta_dev, x_out=None, results=None, options: "Options | None" = None,

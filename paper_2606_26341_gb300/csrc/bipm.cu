@@ -331,6 +331,19 @@ int run_iterations(bipm_batch* b, int n_iter) {
   return end_call(b->counter, b->time_limit_ms, b->stream);
 }
 
+// ulp distance of the factorisation's reciprocal square root from CUDA's
+// 1.0 / sqrt(x) over n log-spaced x in [1e-40, 1e40] (both sides of its FP32
+// range tests); positive doubles order as their bit patterns
+__global__ void rsqrt_check_kernel(int n, unsigned long long* worst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double t = n > 1 ? (double)i / (double)(n - 1) : 0.0;
+    const double x = exp10(-40.0 + 80.0 * t);
+    const long long a = __double_as_longlong(rsqrt_fp64(x));
+    const long long r = __double_as_longlong(1.0 / sqrt(x));
+    atomicMax(worst, (unsigned long long)(a > r ? a - r : r - a));
+  }
+}
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -790,6 +803,23 @@ int bipm_solve_mixed(const bipm_problem_desc* classes, int n_classes, const bipm
     CUDA_TRY(cudaMemcpyAsync(results, r_dev, n_queue * sizeof(bipm_result), cudaMemcpyDeviceToHost, stream));
   }
   return end_call(counter, o.time_limit_ms, stream);
+}
+
+int bipm_check_rsqrt(int n, double* max_ulp) {
+  if (n <= 0 || !max_ulp) return fail(BIPM_EINVAL, "n must be >= 1 and max_ulp non-null");
+  unsigned long long* w = nullptr;
+  CUDA_TRY(cudaMalloc(&w, sizeof(*w)));
+  unsigned long long h = 0;
+  cudaError_t e = cudaMemset(w, 0, sizeof(*w));
+  if (e == cudaSuccess) {
+    rsqrt_check_kernel<<<152, 256>>>(n, w);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&h, w, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(w);
+  if (e != cudaSuccess) return fail(BIPM_ECUDA, cudaGetErrorString(e));
+  *max_ulp = (double)h;
+  return 0;
 }
 
 int bipm_step(bipm_batch* b, int n_iterations) {

@@ -91,20 +91,6 @@ struct Ctx : TeamSize<TM> {
 
 __device__ __forceinline__ double sq(double a) { return a * a; }
 
-// 1 / sqrt(x) for x > 0 in FP64 without the FP64 square root and division:
-// an FP32 estimate y refined by one step of the second-order Newton iteration
-// for the reciprocal square root (Householder's method of order 2).  With
-// e = 1 - x y^2, 1 / sqrt(x) = y (1 - e)^(-1/2) = y (1 + e/2 + 3 e^2/8 + O(e^3)).
-// The FP32 estimate is within a few FP32 ulp (|e| < 2^-20), so the truncated
-// series is exact to about 2^-60 and the result lies within about one FP64
-// ulp of 1 / sqrt(x).  Outside the normal FP32 range the plain expression.
-__device__ __forceinline__ double rsqrt_fp64(double x) {
-  if (!(x >= 1e-36 && x <= 1e36)) return 1.0 / sqrt(x);
-  const double y = (double)rsqrtf((float)x);
-  const double e = fma(-(x * y), y, 1.0);
-  return fma(y * e, fma(e, 0.375, 0.5), y);
-}
-
 // (i, j), j <= i, of entry e of a row-major lower triangle (e = i (i + 1) / 2 + j)
 __device__ __forceinline__ void tri_index(int e, int& i, int& j) {
   int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
