@@ -1416,39 +1416,40 @@ __device__ __noinline__ void solve(Ctx<TB, TF, NQ, TM>& c, Fac<TX> F, const doub
       tv[i] = acc;
     }
     team_sync(c);
-    // g^ = r_u + B^T t
-    LANE_LOOP(a, nu) {
-      int q = a / 4, ca = a - 4 * q;
-      const TX* b = Bb + q * 48 + ca * 12;
-      TX acc = (TX)rx[off_u(d, k) + a];
-      for (int rr = 0; rr < 12; ++rr) acc += b[rr] * tv[12 * q + rr];
-      gv[a] = acc;
+    // A^T t (the first part of p_k, lanes e < nx) and g^ = r_u + B^T t (lanes
+    // nx.. nx + nu) in one pass: both are twelve-term products of t, so the
+    // two kinds of lane share one instruction stream.  g^ is kept in kff; the
+    // feed-forward terms k_k = -R^-1 g^ of all stages are formed after the
+    // sweep, one stage per lane.
+    const TX* Kg = F.K + (long long)k * nu * nx;
+    TX* gk = F.kff + (long long)k * nu;
+    LANE_LOOP(e, nx + nu) {
+      const TX* col;
+      const TX* tq;
+      TX acc;
+      if (e < nx) {
+        const int q = e / 12;
+        col = Ab + q * 144 + (e - 12 * q) * 12;
+        tq = tv + 12 * q;
+        acc = 0;
+      } else {
+        const int a = e - nx, q = a >> 2;
+        col = Bb + q * 48 + (a & 3) * 12;
+        tq = tv + 12 * q;
+        acc = (TX)rx[off_u(d, k) + a];
+      }
+      for (int rr = 0; rr < 12; ++rr) acc += col[rr] * tq[rr];
+      if (e < nx) {
+        wv[e] = acc;
+      } else {
+        gv[e - nx] = acc;
+        gk[e - nx] = acc;
+      }
     }
     team_sync(c);
-    // k_k = -R^{-1} g^ (lane 0; the stored factor holds 1 / L_ii on its diagonal)
-    const TX* Lr = F.Lr + (long long)k * nu * nu;
-    TX* kf = F.kff + (long long)k * nu;
-    if (lane == 0) {
-      TX z[32];
-      for (int i = 0; i < nu; ++i) {
-        TX acc = gv[i];
-        for (int t = 0; t < i; ++t) acc -= Lr[i * nu + t] * z[t];
-        z[i] = acc * Lr[i * nu + i];
-      }
-      for (int i = nu - 1; i >= 0; --i) {
-        TX acc = z[i];
-        for (int t = i + 1; t < nu; ++t) acc -= Lr[t * nu + i] * z[t];
-        z[i] = acc * Lr[i * nu + i];
-      }
-      for (int i = 0; i < nu; ++i) kf[i] = -z[i];
-    }
     // p_k = q~_k + A^T t + K^T g^
-    const TX* Kg = F.K + (long long)k * nu * nx;
     LANE_LOOP(i, nx) {
-      int q = i / 12, ci = i - 12 * q;
-      const TX* a = Ab + q * 144 + ci * 12;
-      TX acc = 0;
-      for (int rr = 0; rr < 12; ++rr) acc += a[rr] * tv[12 * q + rr];
+      TX acc = wv[i];
       for (int aa = 0; aa < nu; ++aa) acc += Kg[aa * nx + i] * gv[aa];
       wv[i] = acc;
     }
@@ -1460,6 +1461,27 @@ __device__ __noinline__ void solve(Ctx<TB, TF, NQ, TM>& c, Fac<TX> F, const doub
     LANE_LOOP(i, nx) F.ptv[(long long)k * nx + i] = pv[i];
     team_sync(c);
   }
+
+  // feed-forward terms k_k = -R^_k^-1 g^_k of every stage, one stage per lane,
+  // in place in kff (the stored factor holds 1 / L_ii on its diagonal)
+  #pragma unroll 1
+  for (int k = lane; k < N; k += c.T) {
+    const TX* Lr = F.Lr + (long long)k * nu * nu;
+    TX* kf = F.kff + (long long)k * nu;
+    TX z[32];
+    for (int i = 0; i < nu; ++i) {
+      TX acc = kf[i];
+      for (int t = 0; t < i; ++t) acc -= Lr[i * nu + t] * z[t];
+      z[i] = acc * Lr[i * nu + i];
+    }
+    for (int i = nu - 1; i >= 0; --i) {
+      TX acc = z[i];
+      for (int t = i + 1; t < nu; ++t) acc -= Lr[t * nu + i] * z[t];
+      z[i] = acc * Lr[i * nu + i];
+    }
+    for (int i = 0; i < nu; ++i) kf[i] = -z[i];
+  }
+  team_sync(c);
 
   // ---- forward sweep; pv = Delta x_k, tv = xi / lambda scratch
   {
@@ -1489,18 +1511,40 @@ __device__ __noinline__ void solve(Ctx<TB, TF, NQ, TM>& c, Fac<TX> F, const doub
     stage_blocks(k, Ab, Bb);
     const TX* Kg = F.K + (long long)k * nu * nx;
     const TX* kf = F.kff + (long long)k * nu;
-    LANE_LOOP(a, nu) {
-      TX acc = kf[a];
-      for (int j = 0; j < nx; ++j) acc += Kg[a * nx + j] * pv[j];
-      gv[a] = acc;
-      ox[off_u(d, k) + a] = (double)acc;
+    // d~_k + A dx_k (the first part of xi, lanes e < nx) and du_k = k_k + K dx_k
+    // (lanes nx .. nx + nu) in one pass over one instruction stream
+    LANE_LOOP(e, nx + nu) {
+      const TX* row;
+      const TX* vq;
+      int sr, len;
+      TX acc;
+      if (e < nx) {
+        const int q = e / 12;
+        row = Ab + q * 144 + (e - 12 * q);
+        sr = 12;
+        vq = pv + 12 * q;
+        len = 12;
+        acc = (TX)(-rct[row_dyn(d, k) + e]);
+      } else {
+        row = Kg + (e - nx) * nx;
+        sr = 1;
+        vq = pv;
+        len = nx;
+        acc = kf[e - nx];
+      }
+      for (int j = 0; j < len; ++j) acc += row[j * sr] * vq[j];
+      if (e < nx) {
+        wv[e] = acc;
+      } else {
+        gv[e - nx] = acc;
+        ox[off_u(d, k) + e - nx] = (double)acc;
+      }
     }
     team_sync(c);
     // xi = A dx + B du + d~
     LANE_LOOP(i, nx) {
       int q = i / 12, ri = i - 12 * q;
-      TX acc = (TX)(-rct[row_dyn(d, k) + i]);
-      for (int j = 0; j < 12; ++j) acc += Ab[q * 144 + j * 12 + ri] * pv[12 * q + j];
+      TX acc = wv[i];
       for (int j = 0; j < 4; ++j) acc += Bb[q * 48 + j * 12 + ri] * gv[4 * q + j];
       wv[i] = acc;
     }
