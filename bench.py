@@ -141,9 +141,9 @@ RK4_DUAL_FLOPS = 1122 + 1596 + 8           # forward-over-reverse, one direction
 
 # DRAM traffic per problem-iteration of the queue kernel, measured by ncu on one
 # timed launch of 4096 tracking problems (dram__bytes_read.sum +
-# dram__bytes_write.sum = 41.71e9 + 33.15e9 B at 30.45 iterations each); scaled
+# dram__bytes_write.sum = 41.35e9 + 33.20e9 B at 30.45 iterations each); scaled
 # to a launch by its iterations.
-TRAFFIC_PER_PROBLEM_ITER = (41.71e9 + 33.15e9) / (4096 * 30.45)
+TRAFFIC_PER_PROBLEM_ITER = (41.35e9 + 33.20e9) / (4096 * 30.45)
 
 
 def unit_flops(desc):
