@@ -17,12 +17,15 @@ one problem at a time:
   Newton system Eq. 6 reduced to the augmented system Eq. 7, inertia
   correction, and the branches of Table I: backtracking filter line search,
   second-order correction, watchdog and soft feasibility restoration (both
-  optional, off by default), tiny step, hard feasibility restoration and the
-  monotone barrier update).  The details the paper defers to the IPOPT paper
+  optional, off by default), tiny step, hard feasibility restoration, and the
+  monotone or the adaptive barrier update).  The details the paper defers to the IPOPT paper
   (Wachter & Biegler 2006) follow that paper's algorithm as read in the design
   notes.  Linear algebra is the dense full-space augmented matrix factorised
   by LAPACK's Bunch-Kaufman LDL^T (scipy.linalg.ldl); inertia is read off D.
 
+* ``quat13``     - the 13-state quaternion quadrotor of Sec. VI (position,
+  attitude quaternion, body velocities; rotor speeds as inputs) on the same
+  NLP transcription; it has no CUDA counterpart yet (parity unpinned).
 * ``mlp``        - the learned warm start's network in FP64 (forward pass,
   chain-rule gradient, Adam), optionally rounding product operands to
   bfloat16 at the CUDA kernels' rounding points.

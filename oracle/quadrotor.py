@@ -75,17 +75,25 @@ def quad_rhs(x, u):
                         phid, thd, psid, w1d, w2d, w3d], dim=-1)
 
 
-def rk4(x, u, dt):
-    """One classical fourth-order Runge-Kutta step."""
-    k1 = quad_rhs(x, u)
-    k2 = quad_rhs(x + 0.5 * dt * k1, u)
-    k3 = quad_rhs(x + 0.5 * dt * k2, u)
-    k4 = quad_rhs(x + dt * k3, u)
+def rk4(x, u, dt, rhs=quad_rhs):
+    """One classical fourth-order Runge-Kutta step of x' = rhs(x, u)."""
+    k1 = rhs(x, u)
+    k2 = rhs(x + 0.5 * dt * k1, u)
+    k3 = rhs(x + 0.5 * dt * k2, u)
+    k4 = rhs(x + dt * k3, u)
     return x + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
 
 
 class QuadNLP:
     """One quadrotor NMPC instance as a plain NLP (n variables, m equalities)."""
+
+    # per-quadrotor state size, continuous dynamics and input bounds of the model
+    NXQ = 12
+    U_LO, U_HI = 0.0, U_MAX
+
+    @staticmethod
+    def rhs(x, u):
+        return quad_rhs(x, u)
 
     def __init__(self, desc: ProblemDesc, theta: np.ndarray):
         self.desc = desc
@@ -120,26 +128,44 @@ class QuadNLP:
 
         self.xl = np.full(self.n, -np.inf)
         self.xu = np.full(self.n, np.inf)
-        self.xl[self.ui.numpy().ravel()] = 0.0
-        self.xu[self.ui.numpy().ravel()] = U_MAX
+        self.xl[self.ui.numpy().ravel()] = self.U_LO
+        self.xu[self.ui.numpy().ravel()] = self.U_HI
         if self.ni > 0:
             self.xl[self.si.numpy().ravel()] = 0.0
 
-        # reference trajectory per stage: position and velocity of each circle
+        self.xref = self.reference().reshape(self.N + 1, self.nx)
+        self.qw, self.rw, self.uh = self.weights()
+
+    def reference_circles(self):
+        """Position and velocity (N + 1, nq, 3) of every quadrotor's reference circle
+        at the stage times."""
         t = torch.arange(self.N + 1, dtype=torch.float64) * self.dt
-        r = torch.zeros(self.N + 1, self.nq, 12, dtype=F64)
+        p = torch.zeros(self.N + 1, self.nq, 3, dtype=F64)
+        v = torch.zeros(self.N + 1, self.nq, 3, dtype=F64)
         for i in range(self.nq):
             cx, cy, cz, rad, rate, ph = self.ref[i]
             a = rate * t + ph
-            r[:, i, 0] = cx + rad * torch.cos(a)
-            r[:, i, 1] = cy + rad * torch.sin(a)
-            r[:, i, 2] = cz
-            r[:, i, 3] = -rad * rate * torch.sin(a)
-            r[:, i, 4] = rad * rate * torch.cos(a)
-        self.xref = r.reshape(self.N + 1, self.nx)
-        self.qw = torch.tensor(Q_DIAG, dtype=F64).repeat(self.nq)
-        self.rw = torch.tensor(R_DIAG, dtype=F64).repeat(self.nq)
-        self.uh = torch.full((self.nu,), HOVER, dtype=F64)
+            p[:, i, 0] = cx + rad * torch.cos(a)
+            p[:, i, 1] = cy + rad * torch.sin(a)
+            p[:, i, 2] = cz
+            v[:, i, 0] = -rad * rate * torch.sin(a)
+            v[:, i, 1] = rad * rate * torch.cos(a)
+        return p, v
+
+    def reference(self):
+        """Reference states (N + 1, nq, 12): the circle's position and velocity, zero
+        attitude and rates."""
+        p, v = self.reference_circles()
+        r = torch.zeros(self.N + 1, self.nq, 12, dtype=F64)
+        r[..., 0:3] = p
+        r[..., 3:6] = v
+        return r
+
+    def weights(self):
+        """State weights (nx), input weights (nu) and the input reference (nu)."""
+        return (torch.tensor(Q_DIAG, dtype=F64).repeat(self.nq),
+                torch.tensor(R_DIAG, dtype=F64).repeat(self.nq),
+                torch.full((self.nu,), HOVER, dtype=F64))
 
     # ------------------------------------------------------------ functions
     def split(self, w):
@@ -149,7 +175,7 @@ class QuadNLP:
         """Inequality values g(x_k) for the given stacked states (K, nx) -> (K, ni);
         ks are the stage indices of the rows (default 1..K: the states x_1..x_N),
         which place the moving spheres at time k dt."""
-        p = xs.reshape(xs.shape[0], self.nq, 12)[..., 0:3]
+        p = xs.reshape(xs.shape[0], self.nq, self.NXQ)[..., 0:3]
         if ks is None:
             ks = torch.arange(1, xs.shape[0] + 1, dtype=F64)
         t = torch.as_tensor(ks, dtype=F64).reshape(-1) * self.dt
@@ -184,9 +210,9 @@ class QuadNLP:
 
     def step_t(self, x, u):
         """Discrete dynamics F(x_k, u_k) for stacked (K, nx), (K, nu)."""
-        xq = x.reshape(x.shape[0], self.nq, 12)
+        xq = x.reshape(x.shape[0], self.nq, self.NXQ)
         uq = u.reshape(u.shape[0], self.nq, 4)
-        return rk4(xq, uq, self.dt).reshape(x.shape[0], self.nx)
+        return rk4(xq, uq, self.dt, self.rhs).reshape(x.shape[0], self.nx)
 
     def c_t(self, w):
         x, u, s = self.split(w)
@@ -217,9 +243,9 @@ class QuadNLP:
     # once and serve as the check of the assembly.
     def _dyn(self, z):
         """F(x_k, u_k) of one interval from z = (x_k, u_k)."""
-        x = z[:self.nx].reshape(self.nq, 12)
+        x = z[:self.nx].reshape(self.nq, self.NXQ)
         u = z[self.nx:].reshape(self.nq, 4)
-        return rk4(x, u, self.dt).reshape(self.nx)
+        return rk4(x, u, self.dt, self.rhs).reshape(self.nx)
 
     def _ineq1(self, xk, k):
         return self.ineq(xk.reshape(1, -1), k.reshape(1))[0]
@@ -300,7 +326,8 @@ class QuadNLP:
         return torch.func.hessian(lag)(torch.as_tensor(w)).numpy()
 
     def default_start(self):
-        """Default primal guess: every state at xbar, hover thrust, slacks at g(xbar)."""
+        """Default primal guess: every state at xbar, inputs at their reference (hover),
+        slacks at g(xbar)."""
         w = torch.zeros(self.n, dtype=F64)
         w[self.xi] = self.xbar
         w[self.ui] = self.uh

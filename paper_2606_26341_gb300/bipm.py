@@ -30,7 +30,11 @@ class ProblemDescC(ctypes.Structure):
 
 
 def desc_c(desc):
-    """The C record of a workloads.ProblemDesc."""
+    """The C record of a workloads.ProblemDesc (the 12-state model; any other model
+    is rejected, the library has no kernel for it)."""
+    model = getattr(desc, "model", "euler12")
+    if model != "euler12":
+        raise ValueError(f"problem model {model!r}: the library solves the 12-state quadrotor model only")
     return ProblemDescC(desc.nq, desc.horizon, desc.dt, desc.n_sph, desc.n_cyl, desc.pair_dist,
                         getattr(desc, "n_mov", 0))
 

@@ -14,6 +14,7 @@ from .mlp_init import mlp_init  # noqa: F401
 from .quadrotor import (  # noqa: F401
     WORKLOADS,
     ProblemDesc,
+    QuatProblemDesc,
     SplitMix64,
     make_batch,
     make_mixed,

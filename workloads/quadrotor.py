@@ -6,7 +6,9 @@ multi-quadrotor swaps).  No dataset exists, so the workloads below stand in for
 them with seeded synthetic draws of the same shape.
 
 Parameter vector theta of one problem (float64), in this order:
-    xbar    12*nq   initial state of every quadrotor (p, v, eta, omega)
+    xbar    nx      initial state of every quadrotor: (p, v, eta, omega), 12 per
+                    quadrotor; (p, q, v, omega), 13 per quadrotor, for the
+                    quaternion model of QuatProblemDesc
     ref      6*nq   per quadrotor reference circle (cx, cy, cz, radius, rate, phase);
                     radius 0 means a fixed goal at (cx, cy, cz)
     spheres  4*n_sph  (cx, cy, cz, r) of every spherical obstacle
@@ -75,6 +77,10 @@ class ProblemDesc:
     def nu(self) -> int:
         return 4 * self.nq
 
+    # the model of the problem class: the 12-state Euler-angle quadrotor (the one
+    # the CUDA path solves) or the 13-state quaternion one (QuatProblemDesc)
+    model = "euler12"
+
     @property
     def n_pairs(self) -> int:
         return self.nq * (self.nq - 1) // 2 if self.pair_dist > 0 else 0
@@ -92,10 +98,23 @@ class ProblemDesc:
         return self.nx * (self.horizon + 1) + self.ni * self.horizon
 
 
+@dataclasses.dataclass(frozen=True)
+class QuatProblemDesc(ProblemDesc):
+    """ProblemDesc of the 13-state quaternion quadrotor model of Sec. VI (state
+    (p, q, v, omega) per quadrotor, four rotor speeds as inputs); the same
+    fields, 13 states per quadrotor."""
+
+    model = "quat13"
+
+    @property
+    def nx(self) -> int:
+        return 13 * self.nq
+
+
 def theta_layout(desc: ProblemDesc) -> dict:
     """Offsets of the parameter groups inside theta."""
     o_x = 0
-    o_ref = o_x + 12 * desc.nq
+    o_ref = o_x + desc.nx
     o_sph = o_ref + 6 * desc.nq
     o_cyl = o_sph + 4 * desc.n_sph
     o_mov = o_cyl + 3 * desc.n_cyl
@@ -183,6 +202,23 @@ def _track_moving(rng: SplitMix64, desc: ProblemDesc) -> np.ndarray:
             if np.linalg.norm(p0 - c0) >= r + 0.1:
                 break
         th[lay["mov"] + 7 * j:lay["mov"] + 7 * j + 7] = [c0[0], c0[1], c0[2], r, v[0], v[1], v[2]]
+    return th
+
+
+def _track_quat(rng: SplitMix64, desc: ProblemDesc) -> np.ndarray:
+    """The tracking workload for the 13-state quaternion model: the same draws as
+    _track (reference circle, start, spheres), the start state written as
+    (p, q = (1, 0, 0, 0), v, omega = 0): level attitude at zero yaw, where the body
+    frame's velocity equals the world frame's."""
+    d12 = dataclasses.replace(ProblemDesc(), nq=desc.nq, horizon=desc.horizon, dt=desc.dt, n_sph=desc.n_sph)
+    t12 = _track(rng, d12)
+    l12, lay = theta_layout(d12), theta_layout(desc)
+    th = np.zeros(n_theta(desc))
+    x12 = t12[l12["xbar"]:l12["xbar"] + 12]
+    th[lay["xbar"]:lay["xbar"] + 3] = x12[0:3]
+    th[lay["xbar"] + 3] = 1.0
+    th[lay["xbar"] + 7:lay["xbar"] + 10] = x12[3:6]
+    th[lay["ref"]:] = t12[l12["ref"]:]
     return th
 
 
@@ -277,6 +313,9 @@ WORKLOADS = {
     "swap4": (1007, ProblemDesc(nq=4, horizon=30, dt=0.05, pair_dist=0.4), _swap, 1024),
     # reference tracking with three time-varying (moving) spherical obstacles
     "track_moving": (1008, ProblemDesc(nq=1, horizon=30, dt=0.05, n_mov=3), _track_moving, 4096),
+    # the tracking workload on the paper's 13-state quaternion model at its dt = 0.1 s and
+    # horizon 30 (oracle side only: the CUDA path solves the 12-state model)
+    "track_quat": (1009, QuatProblemDesc(nq=1, horizon=30, dt=0.1, n_sph=3), _track_quat, 4096),
 }
 
 
