@@ -40,3 +40,15 @@ def test_unit_flops_are_positive_and_scale_with_the_horizon():
     for k in a:
         assert a[k] > 0
         assert 1.8 < b[k] / a[k] < 2.2
+
+
+def test_lower_triangle_index_arithmetic_covers_every_entry_once():
+    """The factorisation's lower-triangle index helpers (csrc/tri_index.cuh, the
+    same source the kernels compile), built for the host and checked exhaustively
+    for 1..8 quadrotors."""
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "tri_index_check")
+        subprocess.run(["g++", "-O1", "-std=c++17", "-I", CSRC, os.path.join(HERE, "tri_index_check.cpp"),
+                        "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout
