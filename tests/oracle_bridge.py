@@ -14,6 +14,7 @@ import numpy as np
 
 from oracle import ipm
 from oracle.quadrotor import QuadNLP
+from oracle.quat13 import QuatNLP
 
 
 def oracle_to_iterate(nlp, st: ipm.SolverState) -> dict:
@@ -82,10 +83,16 @@ def _single_thread():
     torch.set_num_threads(1)
 
 
+def nlp_of(desc, theta):
+    """The oracle NLP of a problem: the 12-state model, or the 13-state one for a
+    QuatProblemDesc."""
+    return QuatNLP(desc, theta) if getattr(desc, "model", "euler12") == "quat13" else QuadNLP(desc, theta)
+
+
 def _solve_one(args):
     desc, theta, record, opt_kw = args
     _single_thread()
-    nlp = QuadNLP(desc, theta)
+    nlp = nlp_of(desc, theta)
     opt = ipm.Options(**opt_kw)
     st, hist = ipm.solve(nlp, opt=opt, record=record)
     res = {

@@ -224,3 +224,22 @@ def test_the_library_rejects_the_quaternion_model():
 
     with pytest.raises(ValueError, match="12-state"):
         desc_c(make_batch("track_quat", 1)[0])
+
+
+def test_stored_quaternion_outcomes_are_reproduced():
+    """tests/golden/track_quat_oracle.json (written by make_track_quat.py, the
+    oracle only): the oracle reproduces the stored status and iteration count of
+    the first two problems, and their solutions to 1e-9."""
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "track_quat_oracle.json")
+    with open(path) as fh:
+        golden = json.load(fh)
+    desc, theta = make_batch("track_quat", 2)
+    for j in range(2):
+        nlp = QuatNLP(desc, theta[j])
+        st, _ = ipm.solve(nlp)
+        assert st.status == golden["status"][j] and st.iter == golden["iters"][j]
+        x = np.asarray(golden["x"][j])
+        assert np.abs(st.normal.x - x).max() <= 1e-9 * max(1.0, np.abs(x).max())
