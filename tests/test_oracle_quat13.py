@@ -243,3 +243,63 @@ def test_stored_quaternion_outcomes_are_reproduced():
         assert st.status == golden["status"][j] and st.iter == golden["iters"][j]
         x = np.asarray(golden["x"][j])
         assert np.abs(st.normal.x - x).max() <= 1e-9 * max(1.0, np.abs(x).max())
+
+
+def _lqr_rollout(A, B, Q, R, QN, x0, N):
+    """Finite-horizon discrete LQR (textbook backward Riccati recursion) and its rollout."""
+    P = QN
+    Ks = []
+    for _ in range(N):
+        K = -np.linalg.solve(R + B.T @ P @ B, B.T @ P @ A)
+        P = Q + A.T @ P @ A + A.T @ P @ B @ K
+        Ks.append(K)
+    Ks = Ks[::-1]
+    xs, us = [x0], []
+    for k in range(N):
+        us.append(Ks[k] @ xs[-1])
+        xs.append(A @ xs[-1] + B @ us[-1])
+    return np.array(xs), np.array(us)
+
+
+def test_small_offsets_from_hover_follow_the_lqr_of_the_linearisation():
+    """Starting delta away from hover at the goal (no obstacles), the NMPC solution
+    approaches the textbook LQR rollout of the RK4 step linearised at hover (its
+    Jacobians by central differences) to second order in delta."""
+    N, dt = 6, 0.1
+    desc = QuatProblemDesc(nq=1, horizon=N, dt=dt)
+    lay = theta_layout(desc)
+    xh = np.zeros(13)
+    xh[3] = 1.0
+    uh = np.full(4, OMEGA_H)
+
+    def step(x, u):
+        return rk4(torch.as_tensor(x), torch.as_tensor(u), dt, quat13_rhs).numpy()
+
+    h = 1e-6
+    A = np.stack([(step(xh + h * e, uh) - step(xh - h * e, uh)) / (2 * h) for e in np.eye(13)], axis=1)
+    B = np.stack([(step(xh, uh + h * e) - step(xh, uh - h * e)) / (2 * h) for e in np.eye(4)], axis=1)
+    # the weights of the reading, restated: Q = diag(10 I3 (p), I4 (q), I3 (v), 0.1 I3 (w)),
+    # R = 0.1 (dT/dOmega at hover)^2 with thrust m g / 4 = K_F Omega_h^2 per rotor
+    Q = np.diag([10.0] * 3 + [1.0] * 4 + [1.0] * 3 + [0.1] * 3)
+    kf = 0.5 * 9.81 / 4.0 / 400.0 ** 2
+    R = 0.1 * (2.0 * kf * 400.0) ** 2 * np.eye(4)
+    d = np.random.default_rng(17).standard_normal(13)
+
+    def deviation(delta):
+        x0 = xh + delta * d
+        x0[3:7] /= np.linalg.norm(x0[3:7])
+        th = np.zeros(lay["end"])
+        th[lay["xbar"]:lay["xbar"] + 13] = x0
+        nlp = QuatNLP(desc, th)
+        st, _ = ipm.solve(nlp, opt=ipm.Options(tol=1e-11))
+        assert st.status == ipm.CONVERGED
+        w = st.normal.x
+        xs_l, us_l = _lqr_rollout(A, B, Q, R, 10 * Q, x0 - xh, N)
+        xs = w[nlp.xi.numpy()] - xh
+        us = w[nlp.ui.numpy()] - uh
+        dev = max(np.abs(xs - xs_l).max(), np.abs(us - us_l).max() / OMEGA_H)
+        return dev, np.abs(xs_l).max()
+
+    (e1, s1), (e2, _) = deviation(1e-3), deviation(2e-3)
+    assert e1 < 0.01 * s1            # far below the size of the trajectory itself
+    assert 3.5 < e2 / e1 < 4.5       # second order in the offset
